@@ -1,0 +1,17 @@
+"""Plain FP64 CPU oracle for the projection method of Palitta & Simoncini.
+
+TEST INFRASTRUCTURE ONLY.  This package is a deliberately slow, direct
+restatement of the paper's algorithms in NumPy/SciPy, used to check the CUDA
+path.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import it; the library itself never calls it and has no CPU
+fallback.  It shares no code with the CUDA path: the only common module is
+``workloads`` (seeded problem generators, which hold none of the method).
+
+Modules
+-------
+lyap       block Lanczos (Alg. 2), cheap residual (Prop. 3.1 / Alg. 3),
+           truncated factor (eq. 2.5, Sec. 3.2) and the two-pass device (Sec. 3.3)
+sylvester  two-sided variant for A X + X B + C1 C2^T = 0 (Sec. 4.1, Alg. 4)
+explicit   explicit residual norms used as pins (dense and exact low-rank form)
+"""
+from . import lyap, sylvester, explicit  # noqa: F401
