@@ -1,0 +1,152 @@
+/*
+ * lyap.h -- C ABI of the GB300 projection solver for large symmetric Lyapunov
+ * and Sylvester equations (Palitta & Simoncini, "Computationally enhanced
+ * projection methods for symmetric Sylvester and Lyapunov matrix equations").
+ *
+ *   Lyapunov : A X + X A + C C^T = 0            (eq. 1.1 with B = A, C1 = C2 = C)
+ *   Sylvester: A X + X B + C1 C2^T = 0          (eq. 4.1)
+ *
+ * A and B are sparse, symmetric negative definite; C1 (n1 x s) and C2 (n2 x s)
+ * are tall.  The solution is returned as low-rank factors: X ~= Z Z^T
+ * (Lyapunov) or X ~= Z1 Z2^T (Sylvester).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: every function returns an int status (lyap_status below) and never
+ *    throws or aborts.  lyap_status_string() gives a static description.
+ *  - Memory: the library never allocates device memory.  The caller provides one
+ *    device workspace of the size lyap_workspace_size() reports; the handle
+ *    lives in host memory (malloc) and owns two CUDA streams and a few events.
+ *  - Dense blocks (C, V, Z) are row-major: row i of an n x s block holds its s
+ *    values contiguously (leading dimension s, or the ld argument).
+ *  - Pointers flagged LYAP_MEM_HOST are host memory (pinned or pageable); the
+ *    library copies them to or from the workspace inside the call.
+ *  - Streams are passed as void* holding a cudaStream_t (NULL = legacy stream).
+ *    All work is ordered on the caller's stream; lyap_solve returns once the
+ *    convergence decision is known on the host.
+ *  - Calling order: create -> solve -> (residual_norm)* -> factor -> destroy.
+ *    factor may be called once per solve.
+ */
+#ifndef LYAP_H
+#define LYAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LYAP_OK = 0,
+  LYAP_NOT_CONVERGED = 1,  /* maxit reached; history and factor are still valid    */
+  LYAP_ERR_ARG = 2,        /* invalid argument, size or calling order              */
+  LYAP_ERR_NONFINITE = 3,  /* NaN/Inf met in the data or in a coefficient          */
+  LYAP_ERR_BREAKDOWN = 4,  /* CholQR2 pivot <= 0: rank-deficient block (the paper
+                              assumes full rank, Sec. 2; deflation not implemented) */
+  LYAP_ERR_NOT_NEGDEF = 5, /* lambda_i + lambda_j >= 0 met: A is not negative definite */
+  LYAP_ERR_TCAP = 6,       /* the factor needs more than tcap columns              */
+  LYAP_ERR_TIMEOUT = 7,    /* a bounded device wait gave up                        */
+  LYAP_ERR_CUDA = 8,       /* a CUDA runtime call failed                           */
+  LYAP_ERR_WORKSPACE = 9   /* workspace too small or misaligned (256 B)            */
+} lyap_status;
+
+enum { LYAP_F64 = 0, LYAP_F32 = 1 };            /* element types              */
+enum { LYAP_MEM_DEVICE = 0, LYAP_MEM_HOST = 1 }; /* where a pointer lives       */
+enum { LYAP_PREC_F64 = 0, LYAP_PREC_MIXED = 1 }; /* bulk precision of the basis */
+
+/* Sparse matrix in CSR form, read only during lyap_workspace_size and lyap_create.
+ * Column indices of each row need not be sorted; the matrix must be symmetric
+ * (the method relies on it, Sec. 2) -- symmetry is not checked. */
+typedef struct {
+  int64_t n;              /* rows = columns                                  */
+  int64_t nnz;            /* stored entries                                  */
+  const int64_t* rowptr;  /* n + 1 offsets                                   */
+  const int32_t* col;     /* nnz column indices in [0, n)                    */
+  const void* val;        /* nnz values of type val_dtype                    */
+  int val_dtype;          /* LYAP_F64 or LYAP_F32                            */
+  int mem;                /* LYAP_MEM_DEVICE or LYAP_MEM_HOST (all 3 arrays) */
+} lyap_csr;
+
+typedef struct {
+  int maxit;             /* iteration cap (default 1000)                                    */
+  int check_every;       /* d: test the residual at every d-th space dimension (Sec. 5);
+                            default 1                                                      */
+  double trunc_eps;      /* truncation threshold of the reduced solution, relative to
+                            ||C1||_F ||C2||_F (eq. 2.5 with eps = 1e-12 in the paper);
+                            default 1e-12                                                  */
+  int precision;         /* LYAP_PREC_F64: basis and SpMM in fp64.  LYAP_PREC_MIXED: basis,
+                            SpMM and the factor in fp32, reductions, CholQR2 factors, the
+                            reduced eigenproblem and the residual in fp64 (default F64)     */
+  int sell_sigma;        /* SELL-C-sigma sorting window in rows (1 = no sorting; default 1) */
+  int pass2_blocks;      /* k: basis blocks buffered per Z update in the second pass
+                            (default 16)                                                   */
+  int check_batch;       /* most convergence checks evaluated per batch (default 32)        */
+  int zcap;              /* columns of Z the workspace can stage for LYAP_MEM_HOST output of
+                            lyap_factor (default 0: device output only)                    */
+} lyap_options;
+
+typedef struct lyap_handle lyap_handle;
+
+/* Fills *opt with the defaults listed above. */
+void lyap_default_options(lyap_options* opt);
+
+/* Bytes of device workspace lyap_create needs for this problem (Alg. 1 storage:
+ * 3s basis vectors per operator (Sec. 3.3), the SELL copy of A and B, the
+ * coefficient log of T_m up to maxit, and check/factor scratch).  B = NULL for
+ * a Lyapunov equation.  Reads the rowptr arrays (copying them if on device). */
+int lyap_workspace_size(const lyap_csr* A, const lyap_csr* B, int s,
+                        const lyap_options* opt, size_t* bytes);
+
+/* Sets up a solve of A X + X B + C1 C2^T = 0 (Alg. 1 steps 1-2).
+ *  A, B      : operators (B = NULL for Lyapunov; then C2 must be NULL too)
+ *  C1, C2    : fp64 n1 x s and n2 x s row-major, in c_mem memory
+ *  s         : block size, 1 <= s <= 8
+ *  tol       : stop at the first m with ||R_m||_F / (||C1||_F ||C2||_F) <= tol
+ *  workspace : device memory of ws_bytes >= lyap_workspace_size(), 256-B aligned,
+ *              owned by the caller, not touched by anyone else until destroy
+ *  stream    : cudaStream_t for the copies and the SELL-C-sigma build
+ * The inputs are copied; the caller may free them after the call returns. */
+int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1,
+                const double* C2, int c_mem, int s, double tol,
+                const lyap_options* opt, void* workspace, size_t ws_bytes,
+                void* stream, lyap_handle** out);
+
+/* Pass 1 (Alg. 1 steps 3-7): block Lanczos with block MGS done twice and CholQR2
+ * normalisation (Alg. 2), the cheap residual norm of Prop. 3.1 / Alg. 3
+ * (Alg. 4 for Sylvester) at every check_every-th step, until tol or maxit.
+ * Returns LYAP_OK, LYAP_NOT_CONVERGED or an error. */
+int lyap_solve(lyap_handle* h, void* stream);
+
+/* Relative residual history of the last solve: hist_host[m-1] for m = 1..*m_out
+ * (NaN where the check period skipped m).  Writes at most cap entries;
+ * *m_out is the final iteration count m.  Host memory. */
+int lyap_residual_norm(lyap_handle* h, double* hist_host, int cap, int* m_out);
+
+/* Alg. 1 steps 8-9 with the two-pass device of Sec. 3.3 (4.1 for Sylvester):
+ * truncates the reduced solution (eq. 2.5) and accumulates Z = V_m (Q_m Ycheck)
+ * while regenerating the basis from the logged coefficients.
+ *  Z1, Z2  : n1 x tcap and n2 x tcap row-major (leading dims ldz1, ldz2 >= tcap),
+ *            element type z_dtype (LYAP_F64, or LYAP_F32 in mixed precision),
+ *            in z_mem memory; columns beyond *t_out are left untouched.
+ *            Z2 must be NULL for Lyapunov.  Host output needs opt.zcap >= tcap.
+ *  t_out   : the rank t kept by the truncation.
+ * Returns LYAP_ERR_TCAP (with *t_out set) if t > tcap. */
+int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2,
+                int z_dtype, int z_mem, int tcap, int* t_out, void* stream);
+
+/* Phase timings of the last solve/factor in milliseconds (CUDA events):
+ * out[0] create, out[1] solve, out[2] factor, out[3] second pass alone,
+ * out[4] convergence checks (sum of batch times), out[5] Lanczos sweeps. */
+int lyap_phase_times(lyap_handle* h, double* out, int cap);
+
+/* Releases the handle's streams and events and the handle itself.  The caller
+ * frees the workspace afterwards. */
+int lyap_destroy(lyap_handle* h);
+
+const char* lyap_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LYAP_H */

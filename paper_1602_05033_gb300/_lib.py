@@ -1,0 +1,182 @@
+"""ctypes binding of liblyap.so: the C ABI of include/lyap.h, one Python function per entry point.
+
+Only argument marshalling happens here; every step of the method runs in the
+library's CUDA kernels.  Loading fails loudly when the library is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblyap.so")
+
+LYAP_OK = 0
+LYAP_NOT_CONVERGED = 1
+LYAP_ERR_ARG = 2
+LYAP_ERR_NONFINITE = 3
+LYAP_ERR_BREAKDOWN = 4
+LYAP_ERR_NOT_NEGDEF = 5
+LYAP_ERR_TCAP = 6
+LYAP_ERR_TIMEOUT = 7
+LYAP_ERR_CUDA = 8
+LYAP_ERR_WORKSPACE = 9
+
+LYAP_F64, LYAP_F32 = 0, 1
+LYAP_MEM_DEVICE, LYAP_MEM_HOST = 0, 1
+LYAP_PREC_F64, LYAP_PREC_MIXED = 0, 1
+
+# every symbol include/lyap.h declares
+EXPORTED = (
+    "lyap_default_options",
+    "lyap_workspace_size",
+    "lyap_create",
+    "lyap_solve",
+    "lyap_residual_norm",
+    "lyap_factor",
+    "lyap_phase_times",
+    "lyap_destroy",
+    "lyap_status_string",
+)
+
+
+class lyap_csr(ct.Structure):
+    _fields_ = [
+        ("n", ct.c_int64),
+        ("nnz", ct.c_int64),
+        ("rowptr", ct.c_void_p),
+        ("col", ct.c_void_p),
+        ("val", ct.c_void_p),
+        ("val_dtype", ct.c_int),
+        ("mem", ct.c_int),
+    ]
+
+
+class lyap_options(ct.Structure):
+    _fields_ = [
+        ("maxit", ct.c_int),
+        ("check_every", ct.c_int),
+        ("trunc_eps", ct.c_double),
+        ("precision", ct.c_int),
+        ("sell_sigma", ct.c_int),
+        ("pass2_blocks", ct.c_int),
+        ("check_batch", ct.c_int),
+        ("zcap", ct.c_int),
+    ]
+
+
+class LyapError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ct.CDLL:
+    """Loads liblyap.so (built by paper_1602_05033_gb300.build); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(
+            f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(the solver has no CPU fallback)"
+        )
+    lib = ct.CDLL(p)
+    P = ct.c_void_p
+    lib.lyap_default_options.argtypes = [ct.POINTER(lyap_options)]
+    lib.lyap_default_options.restype = None
+    lib.lyap_workspace_size.argtypes = [ct.POINTER(lyap_csr), ct.POINTER(lyap_csr), ct.c_int,
+                                        ct.POINTER(lyap_options), ct.POINTER(ct.c_size_t)]
+    lib.lyap_create.argtypes = [ct.POINTER(lyap_csr), ct.POINTER(lyap_csr), P, P, ct.c_int, ct.c_int, ct.c_double,
+                                ct.POINTER(lyap_options), P, ct.c_size_t, P, ct.POINTER(P)]
+    lib.lyap_solve.argtypes = [P, P]
+    lib.lyap_residual_norm.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(ct.c_int)]
+    lib.lyap_factor.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int, ct.c_int, ct.c_int,
+                                ct.POINTER(ct.c_int), P]
+    lib.lyap_phase_times.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int]
+    lib.lyap_destroy.argtypes = [P]
+    lib.lyap_status_string.argtypes = [ct.c_int]
+    lib.lyap_status_string.restype = ct.c_char_p
+    for name in EXPORTED:
+        if name not in ("lyap_default_options", "lyap_status_string"):
+            getattr(lib, name).restype = ct.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().lyap_status_string(int(status)).decode()
+
+
+def lyap_default_options() -> lyap_options:
+    o = lyap_options()
+    load().lyap_default_options(ct.byref(o))
+    return o
+
+
+def lyap_workspace_size(A: lyap_csr, B: lyap_csr | None, s: int, opt: lyap_options | None) -> int:
+    nb = ct.c_size_t(0)
+    st = load().lyap_workspace_size(ct.byref(A), ct.byref(B) if B is not None else None, int(s),
+                                    ct.byref(opt) if opt is not None else None, ct.byref(nb))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_workspace_size")
+    return int(nb.value)
+
+
+def lyap_create(A, B, C1_ptr: int, C2_ptr: int | None, c_mem: int, s: int, tol: float, opt, ws_ptr: int,
+                ws_bytes: int, stream: int) -> int:
+    h = ct.c_void_p(0)
+    st = load().lyap_create(ct.byref(A), ct.byref(B) if B is not None else None, ct.c_void_p(C1_ptr),
+                            ct.c_void_p(C2_ptr) if C2_ptr else None, int(c_mem), int(s), float(tol),
+                            ct.byref(opt) if opt is not None else None, ct.c_void_p(ws_ptr), ct.c_size_t(ws_bytes),
+                            ct.c_void_p(stream), ct.byref(h))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_create")
+    return h.value
+
+
+def lyap_solve(h: int, stream: int) -> int:
+    st = load().lyap_solve(ct.c_void_p(h), ct.c_void_p(stream))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_solve")
+    return st
+
+
+def lyap_residual_norm(h: int, cap: int):
+    import numpy as np
+
+    buf = np.full(max(cap, 1), np.nan)
+    m = ct.c_int(0)
+    st = load().lyap_residual_norm(ct.c_void_p(h), buf.ctypes.data_as(ct.POINTER(ct.c_double)), int(cap), ct.byref(m))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_residual_norm")
+    return buf[: m.value].copy(), m.value, st
+
+
+def lyap_factor(h: int, Z1_ptr: int, ldz1: int, Z2_ptr: int | None, ldz2: int, z_dtype: int, z_mem: int, tcap: int,
+                stream: int) -> int:
+    t = ct.c_int(0)
+    st = load().lyap_factor(ct.c_void_p(h), ct.c_void_p(Z1_ptr), ct.c_int64(ldz1),
+                            ct.c_void_p(Z2_ptr) if Z2_ptr else None, ct.c_int64(ldz2), int(z_dtype), int(z_mem),
+                            int(tcap), ct.byref(t), ct.c_void_p(stream))
+    if st != LYAP_OK:
+        err = LyapError(st, "lyap_factor")
+        err.t = t.value
+        raise err
+    return t.value
+
+
+def lyap_phase_times(h: int):
+    out = (ct.c_double * 8)()
+    load().lyap_phase_times(ct.c_void_p(h), out, 8)
+    return list(out)
+
+
+def lyap_destroy(h: int) -> None:
+    if h:
+        load().lyap_destroy(ct.c_void_p(h))

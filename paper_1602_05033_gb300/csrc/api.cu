@@ -1,0 +1,429 @@
+// C ABI of liblyap: workspace planning, set-up, the pass-1 driver (Alg. 1) and the
+// factor step.  See include/lyap.h for the contract of every entry point.
+#include "common.cuh"
+
+#include <limits.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+size_t factor_ws_bytes(int s, int nmax, int sylv);
+size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32);
+int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col, const void* d_val, int sigma,
+               int bulk_f32, OpDev& op, int* d_flags, cudaStream_t st);
+
+namespace {
+
+int sweep_grid_for(int64_t n) {
+  // fixed per problem size (not per device) so that reductions are reproducible anywhere
+  int64_t g = (n + 4095) / 4096;
+  if (g < 1) g = 1;
+  if (g > 1216) g = 1216;
+  return (int)g;
+}
+
+int valid_s(int s) { return s == 1 || s == 2 || s == 3 || s == 4 || s == 8; }
+
+int check_csr(const lyap_csr* A) {
+  if (!A || A->n <= 0 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return LYAP_ERR_ARG;
+  if (A->val_dtype != LYAP_F64 && A->val_dtype != LYAP_F32) return LYAP_ERR_ARG;
+  if (A->mem != LYAP_MEM_DEVICE && A->mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
+  if (A->n > INT_MAX - 64) return LYAP_ERR_ARG;
+  return LYAP_OK;
+}
+
+lyap_options resolve(const lyap_options* opt) {
+  lyap_options o;
+  lyap_default_options(&o);
+  if (opt) {
+    if (opt->maxit > 0) o.maxit = opt->maxit;
+    if (opt->check_every > 0) o.check_every = opt->check_every;
+    if (opt->trunc_eps > 0) o.trunc_eps = opt->trunc_eps;
+    o.precision = opt->precision;
+    if (opt->sell_sigma > 0) o.sell_sigma = opt->sell_sigma;
+    if (opt->pass2_blocks >= 2) o.pass2_blocks = opt->pass2_blocks;
+    if (opt->check_batch > 0) o.check_batch = opt->check_batch;
+    if (opt->zcap > 0) o.zcap = opt->zcap;
+  }
+  if (o.check_batch > 256) o.check_batch = 256;
+  return o;
+}
+
+size_t staging_bytes(const lyap_csr* A) {
+  if (!A || A->mem != LYAP_MEM_HOST) return 0;
+  const size_t vw = A->val_dtype == LYAP_F64 ? 8 : 4;
+  return lyap_align256((int64_t)(sizeof(int64_t) * (A->n + 1))) + lyap_align256((int64_t)(sizeof(int32_t) * A->nnz)) +
+         lyap_align256((int64_t)(vw * A->nnz));
+}
+
+int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p) {
+  p.s = s;
+  p.sylv = B != nullptr;
+  p.bulk_f32 = o.precision == LYAP_PREC_MIXED;
+  p.maxit = o.maxit;
+  p.check_batch = o.check_batch;
+  p.nmax = s * o.maxit;
+  p.pass2_blocks = o.pass2_blocks;
+  p.zcap = o.zcap;
+  const size_t w = p.bulk_f32 ? 4 : 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off += lyap_align256((int64_t)bytes);
+    return r;
+  };
+  int64_t nmaxop = 0;
+  for (int k = 0; k < 1 + p.sylv; ++k) {
+    const lyap_csr* M = k == 0 ? A : B;
+    int64_t nsl = 0, snnz = 0;
+    int rc = sell_plan_host(M, o.sell_sigma, &nsl, &snnz);
+    if (rc != LYAP_OK) return rc;
+    Plan::OpOff& q = p.op[k];
+    q.n = M->n;
+    q.nslices = nsl;
+    q.sell_nnz = snnz;
+    q.slice_ptr = take(sizeof(int64_t) * (nsl + 1));
+    q.slice_w = take(sizeof(int32_t) * nsl);
+    q.sell_col = take(sizeof(int32_t) * (size_t)snnz);
+    q.sell_val = take(w * (size_t)snnz);
+    q.perm = take(o.sell_sigma > 1 ? sizeof(int32_t) * (size_t)M->n : 0);
+    for (int r = 0; r < 3; ++r) q.V[r] = take(w * (size_t)M->n * s);
+    q.W = take(w * (size_t)M->n * s);
+    q.C = take(sizeof(double) * (size_t)M->n * s);
+    q.log = take(sizeof(double) * (size_t)(o.maxit + 1) * LOG_NREC * s * s);
+    q.partials = take(sizeof(double) * (size_t)1216 * 3 * s * s);
+    q.counter = take(256);
+    nmaxop = std::max<int64_t>(nmaxop, M->n);
+  }
+  p.sweep_grid = sweep_grid_for(nmaxop);
+  p.hist = take(sizeof(double) * (size_t)o.maxit);
+  p.flags = take(256);
+  p.check_bytes = (size_t)(1 + p.sylv) * o.check_batch * check_slot_bytes(s, p.nmax);
+  p.check = take(p.check_bytes);
+  p.factor_bytes = factor_ws_bytes(s, p.nmax, p.sylv);
+  size_t p2 = 0;
+  for (int k = 0; k < 1 + p.sylv; ++k) p2 += pass2_ws_bytes(p.op[k].n, s, o.pass2_blocks, p.bulk_f32);
+  p.factor = take(p.factor_bytes + p2);
+  p.zstage = take(o.zcap > 0 ? sizeof(double) * (size_t)o.zcap * (A->n + (B ? B->n : 0)) : 0);
+  p.staging_bytes = staging_bytes(A) + staging_bytes(B);
+  p.staging = take(p.staging_bytes);
+  p.total = off;
+  return LYAP_OK;
+}
+
+template <typename T>
+T* at(char* ws, size_t off) {
+  return reinterpret_cast<T*>(ws + off);
+}
+
+__global__ void k_init_flags(int* flags, double* hist, int maxit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    flags[0] = 0;
+    flags[1] = INT_MAX;
+  }
+  if (i < maxit) hist[i] = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+int status_from_bits(int bits) {
+  if (bits & DERR_BOUNDS) return LYAP_ERR_ARG;
+  if (bits & DERR_NONFINITE) return LYAP_ERR_NONFINITE;
+  if (bits & DERR_BREAKDOWN) return LYAP_ERR_BREAKDOWN;
+  if (bits & DERR_NOTNEGDEF) return LYAP_ERR_NOT_NEGDEF;
+  if (bits & DERR_TIMEOUT) return LYAP_ERR_TIMEOUT;
+  return LYAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lyap_default_options(lyap_options* opt) {
+  if (!opt) return;
+  opt->maxit = 1000;
+  opt->check_every = 1;
+  opt->trunc_eps = 1e-12;
+  opt->precision = LYAP_PREC_F64;
+  opt->sell_sigma = 1;
+  opt->pass2_blocks = 16;
+  opt->check_batch = 32;
+  opt->zcap = 0;
+}
+
+const char* lyap_status_string(int status) {
+  switch (status) {
+    case LYAP_OK: return "ok";
+    case LYAP_NOT_CONVERGED: return "not converged within maxit";
+    case LYAP_ERR_ARG: return "invalid argument or calling order";
+    case LYAP_ERR_NONFINITE: return "non-finite value in data or coefficients";
+    case LYAP_ERR_BREAKDOWN: return "CholQR2 breakdown: rank-deficient block";
+    case LYAP_ERR_NOT_NEGDEF: return "operator is not negative definite";
+    case LYAP_ERR_TCAP: return "factor rank exceeds tcap";
+    case LYAP_ERR_TIMEOUT: return "bounded device wait expired";
+    case LYAP_ERR_CUDA: return "CUDA runtime error";
+    case LYAP_ERR_WORKSPACE: return "workspace too small or misaligned";
+    default: return "unknown status";
+  }
+}
+
+int lyap_workspace_size(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options* opt, size_t* bytes) {
+  if (!bytes || !valid_s(s)) return LYAP_ERR_ARG;
+  int rc = check_csr(A);
+  if (rc != LYAP_OK) return rc;
+  if (B && (rc = check_csr(B)) != LYAP_OK) return rc;
+  lyap_options o = resolve(opt);
+  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
+  Plan p;
+  rc = make_plan(A, B, s, o, p);
+  if (rc != LYAP_OK) return rc;
+  *bytes = p.total;
+  return LYAP_OK;
+}
+
+int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
+                double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream,
+                lyap_handle** out) {
+  if (!out || !valid_s(s) || !C1 || !(tol >= 0.0)) return LYAP_ERR_ARG;
+  if ((B == nullptr) != (C2 == nullptr)) return LYAP_ERR_ARG;
+  if (c_mem != LYAP_MEM_DEVICE && c_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
+  int rc = check_csr(A);
+  if (rc != LYAP_OK) return rc;
+  if (B && (rc = check_csr(B)) != LYAP_OK) return rc;
+  lyap_options o = resolve(opt);
+  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
+  Plan p;
+  rc = make_plan(A, B, s, o, p);
+  if (rc != LYAP_OK) return rc;
+  if (!workspace || ws_bytes < p.total || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LYAP_ERR_WORKSPACE;
+  *out = nullptr;
+  lyap_handle* h = new (std::nothrow) lyap_handle();
+  if (!h) return LYAP_ERR_ARG;
+  h->plan = p;
+  h->ws = static_cast<char*>(workspace);
+  h->s = s;
+  h->tol = tol;
+  h->opt = o;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < 8; ++i) h->ev[i] = nullptr;
+  auto fail = [&](int code) {
+    lyap_destroy(h);
+    return code;
+  };
+  if (cudaEventCreate(&h->ev[0]) != cudaSuccess || cudaEventCreate(&h->ev[1]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  cudaEventRecord(h->ev[0], st);
+  if (cudaMallocHost(&h->hist_host, sizeof(double) * o.maxit) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  if (cudaMallocHost(&h->flags_host, sizeof(int) * 8) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  h->hist = at<double>(h->ws, p.hist);
+  h->flags = at<int>(h->ws, p.flags);
+  h->check_ws = h->ws + p.check;
+  h->factor_ws = h->ws + p.factor;
+  h->zstage = h->ws + p.zstage;
+  k_init_flags<<<(o.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, o.maxit);
+  char* stage = h->ws + p.staging;
+  for (int k = 0; k < 1 + p.sylv; ++k) {
+    const lyap_csr* M = k == 0 ? A : B;
+    const double* Ck = k == 0 ? C1 : C2;
+    OpDev& op = h->op[k];
+    const Plan::OpOff& q = p.op[k];
+    op.n = q.n;
+    op.nslices = q.nslices;
+    op.sell_nnz = q.sell_nnz;
+    op.slice_ptr = at<int64_t>(h->ws, q.slice_ptr);
+    op.slice_w = at<int32_t>(h->ws, q.slice_w);
+    op.sell_col = at<int32_t>(h->ws, q.sell_col);
+    op.sell_val = h->ws + q.sell_val;
+    op.perm = o.sell_sigma > 1 ? at<int32_t>(h->ws, q.perm) : nullptr;
+    for (int r = 0; r < 3; ++r) op.V[r] = h->ws + q.V[r];
+    op.W = h->ws + q.W;
+    op.C = at<double>(h->ws, q.C);
+    op.log = at<double>(h->ws, q.log);
+    op.partials = at<double>(h->ws, q.partials);
+    op.counter = at<unsigned int>(h->ws, q.counter);
+    if (cudaMemsetAsync(op.counter, 0, 256, st) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+    const int64_t* rp = M->rowptr;
+    const int32_t* cl = M->col;
+    const void* vl = M->val;
+    if (M->mem == LYAP_MEM_HOST) {
+      const size_t vw = M->val_dtype == LYAP_F64 ? 8 : 4;
+      int64_t* drp = reinterpret_cast<int64_t*>(stage);
+      stage += lyap_align256((int64_t)(sizeof(int64_t) * (M->n + 1)));
+      int32_t* dcl = reinterpret_cast<int32_t*>(stage);
+      stage += lyap_align256((int64_t)(sizeof(int32_t) * M->nnz));
+      void* dvl = stage;
+      stage += lyap_align256((int64_t)(vw * M->nnz));
+      if (cudaMemcpyAsync(drp, rp, sizeof(int64_t) * (M->n + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(dcl, cl, sizeof(int32_t) * M->nnz, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(dvl, vl, vw * M->nnz, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(LYAP_ERR_CUDA);
+      rp = drp;
+      cl = dcl;
+      vl = dvl;
+    }
+    rc = sell_build(M, rp, cl, vl, o.sell_sigma, p.bulk_f32, op, h->flags, st);
+    if (rc != LYAP_OK) return fail(rc);
+    const cudaMemcpyKind kind = c_mem == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(op.C, Ck, sizeof(double) * (size_t)op.n * s, kind, st) != cudaSuccess)
+      return fail(LYAP_ERR_CUDA);
+  }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  for (int i = 2; i < 8; ++i)
+    if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  cudaEventRecord(h->ev[1], st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+  for (int i = 0; i < 8; ++i) h->times_ms[i] = 0.f;
+  h->times_ms[0] = ms;
+  if (cudaMemcpy(h->flags_host, h->flags, sizeof(int) * 2, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(LYAP_ERR_CUDA);
+  rc = status_from_bits(h->flags_host[0]);
+  if (rc != LYAP_OK) return fail(rc);
+  *out = h;
+  return LYAP_OK;
+}
+
+int lyap_solve(lyap_handle* h, void* stream) {
+  if (!h) return LYAP_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Plan& p = h->plan;
+  const int s = h->s;
+  cudaEventRecord(h->ev[0], st);
+  k_init_flags<<<(p.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, p.maxit);
+  for (int k = 0; k < 1 + p.sylv; ++k) launch_init_block(h->op[k], s, p.bulk_f32, p.sweep_grid, h->flags, st);
+  int done = 0;        // Lanczos iterations completed (blocks V_1..V_{done+1} exist)
+  int checked = 0;     // largest m already checked
+  int chunk = std::min(4, p.check_batch);
+  int result = LYAP_NOT_CONVERGED;
+  int m_final = p.maxit;
+  float t_lanczos = 0.f, t_check = 0.f;
+  while (true) {
+    const int upto = std::min(p.maxit, done + chunk);
+    cudaEventRecord(h->ev[2], st);
+    for (int j = done + 1; j <= upto; ++j)
+      for (int k = 0; k < 1 + p.sylv; ++k) launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, h->flags, st);
+    cudaEventRecord(h->ev[3], st);
+    done = upto;
+    while (checked < done) {
+      const int lo = checked + 1;
+      const int hi = std::min(done, checked + p.check_batch);
+      launch_check_batch(h, lo, hi, st);
+      checked = hi;
+    }
+    cudaEventRecord(h->ev[4], st);
+    LYAP_CUDA_TRY(cudaGetLastError());
+    LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, h->ev[2], h->ev[3]);
+    cudaEventElapsedTime(&b, h->ev[3], h->ev[4]);
+    t_lanczos += a;
+    t_check += b;
+    const int bits = h->flags_host[0];
+    const int rc = status_from_bits(bits);
+    if (rc != LYAP_OK) {
+      h->solved = 0;
+      return rc;
+    }
+    if (h->flags_host[1] != INT_MAX) {
+      m_final = h->flags_host[1];
+      result = LYAP_OK;
+      break;
+    }
+    if (done >= p.maxit) break;
+    chunk = std::min(2 * chunk, p.check_batch);
+  }
+  h->m = m_final;
+  h->converged = result == LYAP_OK;
+  h->lanczos_done = done;
+  h->solved = 1;
+  h->factored = 0;
+  h->op[0].beta = 0.0;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(h->hist_host, h->hist, sizeof(double) * p.maxit, cudaMemcpyDeviceToHost, st));
+  double betas[2] = {0.0, 0.0};
+  for (int k = 0; k < 1 + p.sylv; ++k)
+    LYAP_CUDA_TRY(cudaMemcpyAsync(&betas[k], h->op[k].log + REC_TDIAG * s * s, sizeof(double), cudaMemcpyDeviceToHost, st));
+  cudaEventRecord(h->ev[1], st);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < 1 + p.sylv; ++k) h->op[k].beta = betas[k];
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+  h->times_ms[1] = ms;
+  h->times_ms[4] = t_check;
+  h->times_ms[5] = t_lanczos;
+  return result;
+}
+
+int lyap_residual_norm(lyap_handle* h, double* hist_host, int cap, int* m_out) {
+  if (!h || !h->solved) return LYAP_ERR_ARG;
+  if (m_out) *m_out = h->m;
+  if (hist_host && cap > 0) {
+    const int n = std::min(cap, h->m);
+    memcpy(hist_host, h->hist_host, sizeof(double) * n);
+  }
+  return h->converged ? LYAP_OK : LYAP_NOT_CONVERGED;
+}
+
+int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int z_mem, int tcap,
+                int* t_out, void* stream) {
+  if (!h || !h->solved || h->factored || !Z1 || !t_out || tcap < 0) return LYAP_ERR_ARG;
+  if ((h->plan.sylv != 0) != (Z2 != nullptr)) return LYAP_ERR_ARG;
+  if (z_dtype != LYAP_F64 && z_dtype != LYAP_F32) return LYAP_ERR_ARG;
+  if (z_dtype == LYAP_F32 && !h->plan.bulk_f32) return LYAP_ERR_ARG;
+  if (ldz1 < tcap || (Z2 && ldz2 < tcap)) return LYAP_ERR_ARG;
+  if (z_mem != LYAP_MEM_DEVICE && z_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
+  if (z_mem == LYAP_MEM_HOST && tcap > h->plan.zcap) return LYAP_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEventRecord(h->ev[0], st);
+  void* z1 = Z1;
+  void* z2 = Z2;
+  int64_t l1 = ldz1, l2 = ldz2;
+  const size_t zw = z_dtype == LYAP_F64 ? 8 : 4;
+  if (z_mem == LYAP_MEM_HOST) {
+    z1 = h->zstage;
+    l1 = tcap;
+    if (Z2) {
+      z2 = h->zstage + lyap_align256((int64_t)(zw * (size_t)h->op[0].n * tcap));
+      l2 = tcap;
+    }
+  }
+  int rc = run_factor(h, z1, l1, z2, l2, z_dtype, tcap, t_out, st);
+  if (rc != LYAP_OK) return rc;
+  if (z_mem == LYAP_MEM_HOST && *t_out > 0) {
+    const int t = *t_out;
+    LYAP_CUDA_TRY(cudaMemcpy2DAsync(Z1, zw * ldz1, z1, zw * l1, zw * t, h->op[0].n, cudaMemcpyDeviceToHost, st));
+    if (Z2)
+      LYAP_CUDA_TRY(cudaMemcpy2DAsync(Z2, zw * ldz2, z2, zw * l2, zw * t, h->op[1].n, cudaMemcpyDeviceToHost, st));
+  }
+  cudaEventRecord(h->ev[1], st);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  LYAP_CUDA_TRY(cudaMemcpy(h->flags_host, h->flags, sizeof(int) * 2, cudaMemcpyDeviceToHost));
+  rc = status_from_bits(h->flags_host[0]);
+  if (rc != LYAP_OK) return rc;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+  h->times_ms[2] = ms;
+  h->factored = 1;
+  return LYAP_OK;
+}
+
+int lyap_phase_times(lyap_handle* h, double* out, int cap) {
+  if (!h || !out) return LYAP_ERR_ARG;
+  for (int i = 0; i < cap && i < 8; ++i) out[i] = h->times_ms[i];
+  return LYAP_OK;
+}
+
+int lyap_destroy(lyap_handle* h) {
+  if (!h) return LYAP_OK;
+  if (h->side) cudaStreamDestroy(h->side);
+  for (int i = 0; i < 8; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->hist_host) cudaFreeHost(h->hist_host);
+  if (h->flags_host) cudaFreeHost(h->flags_host);
+  delete h;
+  return LYAP_OK;
+}
+
+}  // extern "C"

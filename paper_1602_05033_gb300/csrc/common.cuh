@@ -1,0 +1,146 @@
+// Internal declarations shared by the translation units of liblyap.so.
+//
+// Data layout in device memory (all inside the caller's workspace):
+//   * SELL-C-sigma copy of each operator: slices of C = 32 rows, column-major
+//     inside a slice (entry j of row r of slice k at slice_ptr[k] + 32*j + r),
+//     padded entries point at the row itself with value 0.
+//   * basis ring: three n x s row-major blocks V[0..2] plus the work block W
+//     (only the last 3s basis vectors are kept, Sec. 3.3).
+//   * coefficient log: per iteration j a record of LOG_NREC s x s fp64 blocks
+//     (the MGS coefficients of both sweeps, the two CholQR2 factors and the
+//     three blocks of T_m they define), which is all the second pass needs.
+//   * per-CTA partial sums of the s x s reductions (fixed grid, reduced in a
+//     fixed order by the last CTA, so every run is bitwise reproducible).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "lyap.h"
+
+#define LYAP_SLICE 32
+#define LYAP_MAX_S 8
+
+// records in one iteration's log entry (each s*s doubles, row-major)
+enum {
+  REC_APREV = 0,  // alpha_{j-1}: first MGS sweep against V_{j-1}
+  REC_ADIAG,      // alpha_j    : first MGS sweep against V_j
+  REC_BPREV,      // second MGS sweep against V_{j-1}
+  REC_BDIAG,      // second MGS sweep against V_j
+  REC_R1,         // first CholQR factor (upper)
+  REC_R2,         // second CholQR factor (upper)
+  REC_TNEXT,      // tau_{j+1,j} = R2 R1
+  REC_TDIAG,      // tau_{jj}   = alpha_j + beta_j (raw)
+  REC_TPREV,      // tau_{j-1,j} = alpha_{j-1} + beta_{j-1} (raw)
+  REC_CROSS,      // V_j^T V_{j-1} (rounding-level, used by the fused MGS algebra)
+  LOG_NREC
+};
+
+// device error bits (OR-ed into a word in the workspace)
+enum {
+  DERR_BREAKDOWN = 1,
+  DERR_NONFINITE = 2,
+  DERR_NOTNEGDEF = 4,
+  DERR_TIMEOUT = 8,
+  DERR_BOUNDS = 16,
+};
+
+// One operator (A or B) and its Krylov recurrence state.
+struct OpDev {
+  int64_t n = 0;
+  int64_t nslices = 0;
+  int64_t sell_nnz = 0;
+  int64_t* slice_ptr = nullptr;  // nslices + 1
+  int32_t* slice_w = nullptr;    // nslices
+  int32_t* sell_col = nullptr;   // sell_nnz
+  void* sell_val = nullptr;      // sell_nnz, fp64 or fp32
+  int32_t* perm = nullptr;       // n (SELL row -> original row), nullptr when sigma == 1
+  void* V[3] = {nullptr, nullptr, nullptr};
+  void* W = nullptr;
+  double* C = nullptr;           // fp64 copy of the right-hand side (n x s)
+  double* log = nullptr;         // (maxit + 1) * LOG_NREC * s * s; entry 0 = initial QR of C
+  double* partials = nullptr;    // sweep_grid * max_nacc
+  unsigned int* counter = nullptr;
+  double beta = 0.0;             // ||C||_F (host copy after init)
+};
+
+struct Plan {
+  int s = 1;
+  int sylv = 0;
+  int bulk_f32 = 0;
+  int maxit = 1000;
+  int sweep_grid = 0;     // CTAs of every row sweep
+  int check_batch = 32;
+  int nmax = 0;           // largest reduced dimension s * maxit
+  int pass2_blocks = 16;
+  int zcap = 0;
+  size_t total = 0;
+  // byte offsets inside the workspace
+  struct OpOff {
+    size_t slice_ptr, slice_w, sell_col, sell_val, perm, V[3], W, C, log, partials, counter;
+    int64_t n, nslices, sell_nnz;
+  } op[2];
+  size_t hist, flags, check, check_bytes, factor, factor_bytes, zstage, staging, staging_bytes;
+};
+
+// per-check scratch (fp64 unless noted), one slot per check in a batch
+struct CheckSlot {
+  double* d;     // N
+  double* e;     // N
+  double* rows;  // 2 s N   (E_1^T P then E_m^T P)
+  double* lam;   // N
+  double* a;     // N s     (Q^T E_1 gamma)
+  double* w;     // N s     (Q^T E_m tau^T)
+  double* part;  // N
+  double* twk;   // 2 N N   (twisted factorisation pivots, [k][i] layout)
+};
+
+size_t check_slot_bytes(int s, int nmax);
+
+struct lyap_handle {
+  Plan plan;
+  char* ws = nullptr;
+  OpDev op[2];
+  int s = 1;
+  double tol = 1e-8;
+  lyap_options opt;
+  double* hist = nullptr;       // device, maxit
+  int* flags = nullptr;         // device: [0] error bits, [1] first converged m (or INT_MAX)
+  char* check_ws = nullptr;
+  char* factor_ws = nullptr;
+  char* zstage = nullptr;
+  int solved = 0;
+  int factored = 0;
+  int m = 0;                    // iterations of the last solve
+  int converged = 0;
+  int lanczos_done = 0;         // iterations whose blocks exist
+  double* hist_host = nullptr;  // pinned copy
+  int* flags_host = nullptr;    // pinned
+  cudaStream_t side = nullptr;  // second stream (checks)
+  cudaEvent_t ev[8];
+  float times_ms[8];
+};
+
+// ---- launch helpers implemented in the .cu files --------------------------
+// sell.cu
+int sell_plan_host(const lyap_csr* A, int sigma, int64_t* nslices, int64_t* sell_nnz);
+
+// lanczos.cu
+int max_nacc(int s);
+void launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
+void launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
+
+// check.cu
+void launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st);
+void launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st);
+
+// factor.cu
+int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
+               cudaStream_t st);
+
+#define LYAP_CUDA_TRY(x)                         \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) return LYAP_ERR_CUDA; \
+  } while (0)
+
+__host__ __device__ inline int64_t lyap_align256(int64_t x) { return (x + 255) & ~int64_t(255); }

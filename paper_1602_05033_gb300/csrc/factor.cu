@@ -1,0 +1,511 @@
+// Low-rank factor at convergence (Alg. 1 steps 8-9) with the two-pass device (Sec. 3.3).
+//
+// The paper truncates the eigendecomposition of Y~ = -(e_i^T S e_j / (lambda_i + lambda_j))
+// (Sec. 3.2) and forms Q_m Ycheck with the full eigenvector matrix Q_m.  On this
+// GPU both O((sm)^3) steps are replaced by exact-arithmetic equivalents that cost
+// O(sm t^2):
+//  * Y~ is positive semidefinite with fast-decaying spectrum, so a pivoted
+//    Cholesky factorisation Y~ ~= L L^T, stopped when the trace of the remainder
+//    is below 1e-2 of the truncation threshold, captures its numerical range;
+//    the eigendecomposition of L^T L (t x t, Jacobi) then gives the eigenpairs of
+//    L L^T, truncated by the paper's rule (discarded tail <= eps).
+//  * L = Y~(:,P) L_PP^{-T} (Nystrom form of the pivoted factor), and column p of
+//    Q Y~ is -(T_m + lambda_p I)^{-1} E_1 gamma a_p (because Q a = E_1 gamma), an
+//    SND band solve; hence Q L = B L_PP^{-T} without Q.
+// M = Q Ycheck is then accumulated into Z = sum_j V_j E_j^T M while the basis is
+// regenerated from the logged coefficients (k blocks buffered per GEMM update).
+#include "common.cuh"
+
+#include <float.h>
+#include <math.h>
+#include <vector>
+#include <algorithm>
+
+void launch_pass2(OpDev& op, int s, int bulk_f32, int grid, int j, const void* vp, int64_t ldp, const void* vc,
+                  int64_t ldc, void* vn, int64_t ldn, cudaStream_t st);
+void launch_pass2_v1(OpDev& op, int s, int bulk_f32, int grid, void* vn, int64_t ldn, cudaStream_t st);
+void check_slot0(lyap_handle* h, int opi, double** lam, double** a, double** w);
+
+namespace {
+
+constexpr int kPcThreads = 1024;
+// the parallel Jacobi kernel pairs at most 1024 index pairs per round (shared arrays)
+constexpr int kTmaxCap = 2000;
+
+struct FactorWs {
+  double* L;      // tmax x nn   (row k = k-th pivoted column)
+  int* piv;       // tmax
+  int* tcount;    // [0] t after pivoted Cholesky, [1] kept t'
+  double* K;      // tmax x tmax
+  double* Vk;     // tmax x tmax
+  double* ev;     // tmax
+  double* chol;   // tmax x (s+1) x nmax   band Cholesky scratch, one per pivot
+  double* B;      // nn x tmax  (Lanczos coordinates, row-major)
+  double* M;      // nn x tmax
+};
+
+// ---- pivoted Cholesky of the PSD matrix Y~ (generalised to the 2N stacked Sylvester form)
+// entry(i, j) = -(a_i . a_j) / (l_i + l_j), rows 0..nn-1 with a (nn x s) and l (nn)
+__global__ void __launch_bounds__(kPcThreads) k_pivoted_cholesky(const double* __restrict__ lam,
+                                                                 const double* __restrict__ a, int nn, int s,
+                                                                 int tmax, double stop, FactorWs f,
+                                                                 double* __restrict__ dg) {
+  __shared__ double rv[kPcThreads / 32];
+  __shared__ int ri[kPcThreads / 32];
+  __shared__ double rs[kPcThreads / 32];
+  __shared__ int s_p;
+  __shared__ double s_sq, s_tr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < nn; i += blockDim.x) {
+    double q = 0.0;
+    for (int c = 0; c < s; ++c) q += a[(size_t)i * s + c] * a[(size_t)i * s + c];
+    dg[i] = -q / (2.0 * lam[i]);
+  }
+  __syncthreads();
+  int k = 0;
+  for (; k < tmax; ++k) {
+    // argmax (lowest index on ties) and trace of the remaining diagonal
+    double best = -1.0, tr = 0.0;
+    int bi = nn;
+    for (int i = tid; i < nn; i += blockDim.x) {
+      const double v = dg[i];
+      if (v > 0.0) tr += v;
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    }
+    if (lane == 0) { rv[warp] = best; ri[warp] = bi; rs[warp] = tr; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = rv[0], t = rs[0];
+      int bi0 = ri[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        if (rv[w] > b || (rv[w] == b && ri[w] < bi0)) { b = rv[w]; bi0 = ri[w]; }
+        t += rs[w];
+      }
+      s_p = bi0;
+      s_tr = t;
+      s_sq = b > 0.0 ? sqrt(b) : 0.0;
+    }
+    __syncthreads();
+    if (!(s_tr > stop) || s_p >= nn || !(s_sq > 0.0)) break;
+    const int p = s_p;
+    const double sq = s_sq;
+    const double lp = lam[p];
+    double ap[2 * LYAP_MAX_S];
+    for (int c = 0; c < s; ++c) ap[c] = a[(size_t)p * s + c];
+    for (int i = tid; i < nn; i += blockDim.x) {
+      double y = 0.0;
+      if (dg[i] > -1.0) {  // not yet pivoted
+        double dot = 0.0;
+        for (int c = 0; c < s; ++c) dot += a[(size_t)i * s + c] * ap[c];
+        y = -dot / (lam[i] + lp);
+        for (int l = 0; l < k; ++l) y -= f.L[(size_t)l * nn + i] * f.L[(size_t)l * nn + p];
+        y /= sq;
+      }
+      f.L[(size_t)k * nn + i] = (i == p) ? sq : y;
+    }
+    __syncthreads();
+    for (int i = tid; i < nn; i += blockDim.x) {
+      if (i == p) dg[i] = -2.0;  // mark pivoted
+      else if (dg[i] > -1.0) dg[i] -= f.L[(size_t)k * nn + i] * f.L[(size_t)k * nn + i];
+    }
+    if (tid == 0) f.piv[k] = p;
+    __syncthreads();
+  }
+  if (tid == 0) f.tcount[0] = k;
+}
+
+// K = L^T L  (t x t), L rows are the pivoted columns
+__global__ void k_gram_L(FactorWs f, int nn, int tmax) {
+  const int t = f.tcount[0];
+  const int a = blockIdx.x, b = blockIdx.y * blockDim.x + threadIdx.x;
+  if (a >= t || b >= t) return;
+  double acc = 0.0;
+  for (int i = 0; i < nn; ++i) acc += f.L[(size_t)a * nn + i] * f.L[(size_t)b * nn + i];
+  f.K[(size_t)a * tmax + b] = acc;
+}
+
+// cyclic parallel Jacobi (round-robin pairing) on the symmetric t x t matrix K, one CTA
+__global__ void __launch_bounds__(1024) k_jacobi(FactorWs f, int tmax) {
+  const int t = f.tcount[0];
+  const int tp = t + (t & 1);  // padded to even; index t is a dummy
+  double* K = f.K;
+  double* V = f.Vk;
+  __shared__ double cs_[1024], sn_[1024];
+  __shared__ int pp_[1024], qq_[1024];
+  __shared__ double off_s, tot_s;
+  for (int i = threadIdx.x; i < t * t; i += blockDim.x) {
+    const int r = i / t, c = i % t;
+    V[(size_t)r * tmax + c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (t <= 1) {
+    if (threadIdx.x == 0 && t == 1) f.ev[0] = K[0];
+    return;
+  }
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int r = 0; r < t; ++r)
+        for (int c = 0; c < t; ++c) {
+          const double v = K[(size_t)r * tmax + c] * K[(size_t)r * tmax + c];
+          tot += v;
+          if (r != c) off += v;
+        }
+      off_s = off;
+      tot_s = tot;
+    }
+    __syncthreads();
+    if (!(off_s > 1e-30 * tot_s)) break;
+    for (int round = 0; round < tp - 1; ++round) {
+      const int npairs = tp / 2;
+      for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+        // round-robin: position 0 fixed, the others rotate
+        int i0 = k == 0 ? 0 : 1 + (k - 1 + round) % (tp - 1);
+        int j0 = 1 + (tp - 2 - k + round) % (tp - 1);
+        int p = min(i0, j0), q = max(i0, j0);
+        double c = 1.0, s = 0.0;
+        if (q < t) {
+          const double apq = K[(size_t)p * tmax + q];
+          if (apq != 0.0) {
+            const double app = K[(size_t)p * tmax + p], aqq = K[(size_t)q * tmax + q];
+            const double theta = (aqq - app) / (2.0 * apq);
+            const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(tt * tt + 1.0);
+            s = tt * c;
+          }
+        }
+        cs_[k] = c; sn_[k] = s; pp_[k] = p; qq_[k] = q;
+      }
+      __syncthreads();
+      // rows: K <- J^T K  (pairs touch disjoint rows)
+      for (int idx = threadIdx.x; idx < npairs * t; idx += blockDim.x) {
+        const int k = idx / t, col = idx % t;
+        const int p = pp_[k], q = qq_[k];
+        if (q >= t || sn_[k] == 0.0) continue;
+        const double c = cs_[k], s = sn_[k];
+        const double kp = K[(size_t)p * tmax + col], kq = K[(size_t)q * tmax + col];
+        K[(size_t)p * tmax + col] = c * kp - s * kq;
+        K[(size_t)q * tmax + col] = s * kp + c * kq;
+      }
+      __syncthreads();
+      // columns: K <- K J, V <- V J
+      for (int idx = threadIdx.x; idx < npairs * t; idx += blockDim.x) {
+        const int k = idx / t, row = idx % t;
+        const int p = pp_[k], q = qq_[k];
+        if (q >= t || sn_[k] == 0.0) continue;
+        const double c = cs_[k], s = sn_[k];
+        const double kp = K[(size_t)row * tmax + p], kq = K[(size_t)row * tmax + q];
+        K[(size_t)row * tmax + p] = c * kp - s * kq;
+        K[(size_t)row * tmax + q] = s * kp + c * kq;
+        const double vp = V[(size_t)row * tmax + p], vq = V[(size_t)row * tmax + q];
+        V[(size_t)row * tmax + p] = c * vp - s * vq;
+        V[(size_t)row * tmax + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < t; i += blockDim.x) f.ev[i] = K[(size_t)i * tmax + i];
+}
+
+// B[:, k] = -(T_m + lambda_{p_k} I)^{-1} E_1 gamma a_{p_k}; one thread per pivot, banded Cholesky
+// of the SPD matrix -(T_m + lambda I) in (s+1) x N band storage.
+__global__ void k_shifted_solves(const double* __restrict__ log, int s, int m, const double* __restrict__ lam,
+                                 const double* __restrict__ a, FactorWs f, int tmax, int nmax, int col_off,
+                                 int piv_lo, int piv_hi, int* flags) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = f.tcount[0];
+  if (k >= t) return;
+  const int p = f.piv[k];
+  if (p < piv_lo || p >= piv_hi) return;  // pivot belongs to the other operator (Sylvester)
+  const int N = s * m, SS = s * s;
+  const double shift = lam[p];
+  double* Lb = f.chol + (size_t)k * (s + 1) * nmax;  // Lb[d*N + j] = L[j+d][j]
+  auto Tval = [&](int i, int c) -> double {            // T_m[i][c], i >= c, i - c <= s
+    const int J = i / s, Jc = c / s;
+    if (J == Jc) {
+      const double* D = log + (size_t)(J + 1) * LOG_NREC * SS + REC_TDIAG * SS;
+      return 0.5 * (D[(i % s) * s + (c % s)] + D[(c % s) * s + (i % s)]);
+    }
+    if (J == Jc + 1) return log[(size_t)(Jc + 1) * LOG_NREC * SS + REC_TNEXT * SS + (i % s) * s + (c % s)];
+    return 0.0;
+  };
+  bool ok = true;
+  for (int j = 0; j < N; ++j) {
+    double djj = -(Tval(j, j) + shift);
+    for (int kk = max(0, j - s); kk < j; ++kk) djj -= Lb[(size_t)(j - kk) * N + kk] * Lb[(size_t)(j - kk) * N + kk];
+    if (!(djj > 0.0)) { ok = false; djj = DBL_MIN; }
+    const double ljj = sqrt(djj);
+    Lb[j] = ljj;
+    for (int i = j + 1; i <= min(N - 1, j + s); ++i) {
+      double v = -Tval(i, j);
+      for (int kk = max(0, i - s); kk < j; ++kk) v -= Lb[(size_t)(i - kk) * N + kk] * Lb[(size_t)(j - kk) * N + kk];
+      Lb[(size_t)(i - j) * N + j] = v / ljj;
+    }
+  }
+  if (!ok) atomicOr(flags, DERR_NOTNEGDEF);
+  // rhs r = -(E_1 gamma a_p): solve L y = r, L^T x = y  => x = (-(T+lam I))^{-1} r = -(T + lam I)^{-1}(-E1 gamma a_p)
+  // we want B = -(T+lam I)^{-1} E1 gamma a_p = (-(T + lam I))^{-1} E1 gamma a_p
+  const double* gam = log + REC_TNEXT * SS;
+  double* x = f.B + col_off + k;  // column k of B, stride tmax
+  const size_t ld = (size_t)tmax;
+  for (int j = 0; j < N; ++j) {
+    double r = 0.0;
+    if (j < s)
+      for (int c = 0; c < s; ++c) r += gam[j * s + c] * a[(size_t)p * s + c];
+    for (int kk = max(0, j - s); kk < j; ++kk) r -= Lb[(size_t)(j - kk) * N + kk] * x[(size_t)kk * ld];
+    x[(size_t)j * ld] = r / Lb[j];
+  }
+  for (int j = N - 1; j >= 0; --j) {
+    double r = x[(size_t)j * ld];
+    for (int i = j + 1; i <= min(N - 1, j + s); ++i) r -= Lb[(size_t)(i - j) * N + j] * x[(size_t)i * ld];
+    x[(size_t)j * ld] = r / Lb[j];
+  }
+}
+
+// X = B L_PP^{-T} in place (row-wise forward substitution with L_PP[a][k] = L[k][p_a])
+__global__ void k_apply_lpp(FactorWs f, int nrows, int nn, int tmax) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = f.tcount[0];
+  if (r >= nrows) return;
+  double* x = f.B + (size_t)r * tmax;
+  for (int aa = 0; aa < t; ++aa) {
+    double v = x[aa];
+    const int pa = f.piv[aa];
+    for (int kk = 0; kk < aa; ++kk) v -= x[kk] * f.L[(size_t)kk * nn + pa];
+    x[aa] = v / f.L[(size_t)aa * nn + pa];
+  }
+}
+
+// M[:, c] = X V[:, order[c]] for the kept columns
+__global__ void k_form_M(FactorWs f, int nrows, int tmax, const int* __restrict__ order, int tk, int row_off,
+                         double* __restrict__ M, int ldm) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  const int t = f.tcount[0];
+  if (r >= nrows || c >= tk) return;
+  const int oc = order[c];
+  double acc = 0.0;
+  for (int kk = 0; kk < t; ++kk) acc += f.B[(size_t)(row_off + r) * tmax + kk] * f.Vk[(size_t)kk * tmax + oc];
+  M[(size_t)r * ldm + c] = acc;
+}
+
+// ---- Z += Vbuf (n x K) * Mg (K x t) -------------------------------------------
+template <typename TV, typename TZ>
+__global__ void __launch_bounds__(256) k_gemm_accum(int64_t n, int K, int t, const TV* __restrict__ Vb, int64_t ldv,
+                                                    const double* __restrict__ Mg, int64_t ldm, TZ* __restrict__ Z,
+                                                    int64_t ldz) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ TZ As[BK][BM + 1];
+  __shared__ TZ Bs[BK][BN];
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int col0 = blockIdx.y * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 outputs each
+  TZ acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = TZ(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+      const int r = idx / BK, kk = idx % BK;
+      const int64_t gr = row0 + r;
+      As[kk][r] = (gr < n && k0 + kk < K) ? TZ(Vb[gr * ldv + k0 + kk]) : TZ(0);
+    }
+    for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
+      const int kk = idx / BN, c = idx % BN;
+      Bs[kk][c] = (k0 + kk < K && col0 + c < t) ? TZ(Mg[(int64_t)(k0 + kk) * ldm + col0 + c]) : TZ(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      TZ av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = row0 + ty * 4 + i;
+    if (gr >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tx * 4 + j;
+      if (gc < t) Z[gr * ldz + gc] += acc[i][j];
+    }
+  }
+}
+
+template <typename TZ>
+__global__ void k_zero_cols(TZ* Z, int64_t n, int64_t ldz, int t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * t) return;
+  Z[(i / t) * ldz + (i % t)] = TZ(0);
+}
+
+void gemm_accum(int bulk_f32, int z_f32, int64_t n, int K, int t, const void* Vb, int64_t ldv, const double* Mg,
+                int64_t ldm, void* Z, int64_t ldz, cudaStream_t st) {
+  if (t <= 0 || K <= 0) return;
+  dim3 grid((unsigned)((n + 63) / 64), (unsigned)((t + 63) / 64));
+  if (bulk_f32 && z_f32)
+    k_gemm_accum<float, float><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float*)Z, ldz);
+  else if (bulk_f32)
+    k_gemm_accum<float, double><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (double*)Z, ldz);
+  else
+    k_gemm_accum<double, double><<<grid, 256, 0, st>>>(n, K, t, (const double*)Vb, ldv, Mg, ldm, (double*)Z, ldz);
+}
+
+FactorWs carve(char* base, int s, int nmax2, int tmax, int nmax) {
+  FactorWs f;
+  char* p = base;
+  auto take = [&](size_t bytes) { char* r = p; p += lyap_align256((int64_t)bytes); return r; };
+  f.L = (double*)take(sizeof(double) * (size_t)tmax * nmax2);
+  f.piv = (int*)take(sizeof(int) * (size_t)tmax);
+  f.tcount = (int*)take(sizeof(int) * 4);
+  f.K = (double*)take(sizeof(double) * (size_t)tmax * tmax);
+  f.Vk = (double*)take(sizeof(double) * (size_t)tmax * tmax);
+  f.ev = (double*)take(sizeof(double) * (size_t)tmax);
+  f.chol = (double*)take(sizeof(double) * (size_t)tmax * (s + 1) * nmax);
+  f.B = (double*)take(sizeof(double) * (size_t)nmax2 * tmax);
+  f.M = (double*)take(sizeof(double) * (size_t)nmax2 * tmax);
+  return f;
+}
+
+// second pass for one operator: regenerate V_1..V_m and accumulate Z += V_j E_j^T M
+int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void* Z, int64_t ldz, int z_f32,
+                cudaStream_t st) {
+  OpDev& op = h->op[opi];
+  const int s = h->s, m = h->m, kb = h->plan.pass2_blocks;
+  const int bulk = h->plan.bulk_f32;
+  const size_t w = bulk ? 4 : 8;
+  const int64_t n = op.n;
+  const int64_t ldb = (int64_t)kb * s;
+  char* buf[2] = {reinterpret_cast<char*>(op.V[0]) + 0, nullptr};
+  // the pass-2 buffers sit after the factor scratch, one pair per operator
+  buf[0] = h->factor_ws + h->plan.factor_bytes + (size_t)opi * 2 * lyap_align256((int64_t)(n * ldb * w));
+  buf[1] = buf[0] + lyap_align256((int64_t)(n * ldb * w));
+  auto pos = [&](int j) -> char* {  // block j (1-based)
+    const int g = (j - 1) / kb, c = (j - 1) % kb;
+    return buf[g & 1] + (size_t)c * s * w;
+  };
+  if (tk > 0) {
+    const int64_t tot = n * tk;
+    if (z_f32) k_zero_cols<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((float*)Z, n, ldz, tk);
+    else k_zero_cols<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((double*)Z, n, ldz, tk);
+  }
+  launch_pass2_v1(op, s, bulk, h->plan.sweep_grid, pos(1), ldb, st);
+  for (int j = 1; j <= m; ++j) {
+    if (j < m) {
+      const void* vp = j > 1 ? pos(j - 1) : pos(j);
+      launch_pass2(op, s, bulk, h->plan.sweep_grid, j, vp, ldb, pos(j), ldb, pos(j + 1), ldb, st);
+    }
+    const bool group_end = (j % kb == 0) || j == m;
+    if (group_end && tk > 0) {
+      const int g = (j - 1) / kb;
+      const int j0 = g * kb + 1;
+      const int nblk = j - j0 + 1;
+      gemm_accum(bulk, z_f32, n, nblk * s, tk, buf[g & 1], ldb, M + (size_t)(j0 - 1) * s * ldm, ldm, Z, ldz, st);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
+}
+
+}  // namespace
+
+size_t factor_ws_bytes(int s, int nmax, int sylv) {
+  const int nmax2 = sylv ? 2 * nmax : nmax;
+  const int tmax = nmax2 < kTmaxCap ? nmax2 : kTmaxCap;
+  size_t b = 0;
+  auto add = [&](size_t bytes) { b += lyap_align256((int64_t)bytes); };
+  add(sizeof(double) * (size_t)tmax * nmax2);
+  add(sizeof(int) * (size_t)tmax);
+  add(sizeof(int) * 4);
+  add(sizeof(double) * (size_t)tmax * tmax);
+  add(sizeof(double) * (size_t)tmax * tmax);
+  add(sizeof(double) * (size_t)tmax);
+  add(sizeof(double) * (size_t)tmax * (s + 1) * nmax);
+  add(sizeof(double) * (size_t)nmax2 * tmax);
+  add(sizeof(double) * (size_t)nmax2 * tmax);
+  add(sizeof(double) * (size_t)nmax2);  // diagonal scratch of the pivoted Cholesky
+  add(sizeof(int) * (size_t)tmax);      // kept-column order
+  return b;
+}
+
+size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32) {
+  const size_t w = bulk_f32 ? 4 : 8;
+  return 2 * (size_t)lyap_align256((int64_t)(n * (int64_t)kb * s * w));
+}
+
+int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
+               cudaStream_t st) {
+  (void)Z2;
+  (void)ldz2;
+  const int s = h->s, m = h->m, N = s * m;
+  if (h->plan.sylv) return LYAP_ERR_ARG;
+  const int nmax = h->plan.nmax;
+  const int tmax = nmax < kTmaxCap ? nmax : kTmaxCap;
+  FactorWs f = carve(h->factor_ws, s, nmax, tmax, nmax);
+  char* after = reinterpret_cast<char*>(f.M) + lyap_align256((int64_t)(sizeof(double) * (size_t)nmax * tmax));
+  double* dg = reinterpret_cast<double*>(after);
+  int* order_d = reinterpret_cast<int*>(after + lyap_align256((int64_t)(sizeof(double) * nmax)));
+
+  // 1. eigenvalues lambda and rows a = (Q^T E_1 gamma) of T_m (Alg. 3 steps 1-4)
+  launch_eigen_for_factor(h, 0, m, st);
+  double *lam, *a, *w;
+  check_slot0(h, 0, &lam, &a, &w);
+  // 2. pivoted Cholesky of Y~ = -(a_i . a_j)/(lambda_i + lambda_j)
+  const double beta2 = h->op[0].beta * h->op[0].beta;
+  const double eps_abs = h->opt.trunc_eps * beta2;
+  k_pivoted_cholesky<<<1, kPcThreads, 0, st>>>(lam, a, N, s, tmax, 1e-2 * eps_abs, f, dg);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  const int tpc = h->flags_host[2];
+  if (tpc <= 0) {
+    *t_out = 0;
+    return LYAP_OK;
+  }
+  // 3. B = Q Y~(:,P) by shifted SND band solves, X = B L_PP^{-T} (= Q L)
+  const int nthr = 64;
+  k_shifted_solves<<<(tpc + nthr - 1) / nthr, nthr, 0, st>>>(h->op[0].log, s, m, lam, a, f, tmax, nmax, 0, 0, N,
+                                                             h->flags);
+  k_apply_lpp<<<(N + 127) / 128, 128, 0, st>>>(f, N, N, tmax);
+  // 4. K = L^T L and its eigendecomposition (eigenpairs of L L^T)
+  k_gram_L<<<dim3(tpc, (tpc + 127) / 128), 128, 0, st>>>(f, N, tmax);
+  k_jacobi<<<1, 1024, 0, st>>>(f, tmax);
+  std::vector<double> ev(tpc);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(ev.data(), f.ev, sizeof(double) * tpc, cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  // truncation (eq. 2.5): eigenvalues non-increasing; keep the fewest so that the
+  // discarded tail has Frobenius norm <= eps; negative values are never kept
+  std::vector<int> order(tpc);
+  for (int i = 0; i < tpc; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ev[x] > ev[y]; });
+  std::vector<double> tail(tpc + 1, 0.0);
+  for (int i = tpc - 1; i >= 0; --i) tail[i] = tail[i + 1] + ev[order[i]] * ev[order[i]];
+  int tk = 0;
+  while (tk < tpc && !(sqrt(tail[tk]) <= eps_abs)) ++tk;
+  int npos = 0;
+  for (int i = 0; i < tpc; ++i) npos += ev[i] > 0.0;
+  if (tk > npos) tk = npos;
+  *t_out = tk;
+  if (tk > tcap) return LYAP_ERR_TCAP;
+  if (tk > 0) LYAP_CUDA_TRY(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * tk, cudaMemcpyHostToDevice, st));
+  // 5. M = X V(:, kept) = Q Ycheck, then the second pass Z = sum_j V_j E_j^T M
+  if (tk > 0) k_form_M<<<dim3((N + 127) / 128, tk), 128, 0, st>>>(f, N, tmax, order_d, tk, 0, f.M, tmax);
+  int rc = second_pass(h, 0, f.M, tmax, tk, Z1, ldz1, z_dtype == LYAP_F32, st);
+  if (rc != LYAP_OK) return rc;
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // keeps the host vectors alive until the copies ran
+  return LYAP_OK;
+}

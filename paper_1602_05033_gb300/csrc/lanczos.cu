@@ -1,0 +1,722 @@
+// Block Lanczos sweeps (Alg. 2 with CholQR2 normalisation) and the second pass (Sec. 3.3).
+//
+// One iteration j of pass 1 is four row sweeps over n rows, each followed by a
+// fixed-order reduction of per-CTA s x s partial sums done by the last CTA:
+//
+//   S1  W = A V_j (SELL-C-sigma SpMM)            partials V_{j-1}^T W, V_j^T W, V_j^T V_{j-1}
+//       -> alpha_{j-1} = V_{j-1}^T W,  alpha_j = V_j^T W - (V_j^T V_{j-1}) alpha_{j-1}
+//          (the first block MGS sweep of Alg. 2 in fused form: algebraically
+//           identical to subtracting V_{j-1} alpha_{j-1} before projecting on V_j)
+//   S2  w1 = W - V_{j-1} alpha_{j-1} - V_j alpha_j   partials V_{j-1}^T w1, V_j^T w1, w1^T w1
+//       -> beta_{j-1}, beta_j (second MGS sweep), G1 = w1^T w1 - beta^T beta, R1 = chol(G1)
+//   S3  w2 = w1 - V_{j-1} beta_{j-1} - V_j beta_j, x = w2 R1^{-1}   partial x^T x
+//       -> R2 = chol(x^T x), tau_{j+1,j} = R2 R1
+//   S4  V_{j+1} = x R2^{-1}
+//
+// The rows w1, w2, x are recomputed from W, V_{j-1}, V_j in every sweep instead
+// of being stored; the second pass (S1's SpMM fused with S4's row recipe and the
+// logged coefficients) therefore regenerates V_{j+1} bit for bit.
+#include "common.cuh"
+
+#include <math.h>
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+template <typename T>
+struct AccT { using type = double; };
+template <>
+struct AccT<float> { using type = float; };
+
+// ---- row loads/stores -------------------------------------------------------
+template <typename T, int S>
+__device__ __forceinline__ void load_row(const T* __restrict__ X, int64_t ld, int64_t i, T (&r)[S]) {
+  const T* p = X + i * ld;
+#pragma unroll
+  for (int a = 0; a < S; ++a) r[a] = p[a];
+}
+template <int S>
+__device__ __forceinline__ void load_row(const float* __restrict__ X, int64_t ld, int64_t i, float (&r)[S]) {
+  const float* p = X + i * ld;
+  if constexpr (S % 4 == 0) {
+#pragma unroll
+    for (int a = 0; a < S; a += 4) {
+      float4 v = *reinterpret_cast<const float4*>(p + a);
+      r[a] = v.x; r[a + 1] = v.y; r[a + 2] = v.z; r[a + 3] = v.w;
+    }
+  } else if constexpr (S == 2) {
+    float2 v = *reinterpret_cast<const float2*>(p);
+    r[0] = v.x; r[1] = v.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) r[a] = p[a];
+  }
+}
+template <int S>
+__device__ __forceinline__ void load_row(const double* __restrict__ X, int64_t ld, int64_t i, double (&r)[S]) {
+  const double* p = X + i * ld;
+  if constexpr (S % 2 == 0) {
+#pragma unroll
+    for (int a = 0; a < S; a += 2) {
+      double2 v = *reinterpret_cast<const double2*>(p + a);
+      r[a] = v.x; r[a + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) r[a] = p[a];
+  }
+}
+template <typename T, int S>
+__device__ __forceinline__ void store_row(T* __restrict__ X, int64_t ld, int64_t i, const T (&r)[S]) {
+  T* p = X + i * ld;
+#pragma unroll
+  for (int a = 0; a < S; ++a) p[a] = r[a];
+}
+template <int S>
+__device__ __forceinline__ void store_row(float* __restrict__ X, int64_t ld, int64_t i, const float (&r)[S]) {
+  float* p = X + i * ld;
+  if constexpr (S % 4 == 0) {
+#pragma unroll
+    for (int a = 0; a < S; a += 4) *reinterpret_cast<float4*>(p + a) = make_float4(r[a], r[a + 1], r[a + 2], r[a + 3]);
+  } else if constexpr (S == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(r[0], r[1]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) p[a] = r[a];
+  }
+}
+template <int S>
+__device__ __forceinline__ void store_row(double* __restrict__ X, int64_t ld, int64_t i, const double (&r)[S]) {
+  double* p = X + i * ld;
+  if constexpr (S % 2 == 0) {
+#pragma unroll
+    for (int a = 0; a < S; a += 2) *reinterpret_cast<double2*>(p + a) = make_double2(r[a], r[a + 1]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) p[a] = r[a];
+  }
+}
+
+// ---- SELL-C-sigma row product: w = (A V)[row] -----------------------------------
+template <typename T, int S>
+__device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lane, const T* __restrict__ Vc,
+                                         int64_t ldc, T (&w)[S]) {
+#pragma unroll
+  for (int a = 0; a < S; ++a) w[a] = T(0);
+  const int64_t base = op.slice_ptr[slice] + lane;
+  const int width = op.slice_w[slice];
+  const T* __restrict__ val = static_cast<const T*>(op.sell_val);
+  for (int jj = 0; jj < width; ++jj) {
+    const int64_t e = base + (int64_t)jj * LYAP_SLICE;
+    const int32_t c = __ldg(op.sell_col + e);
+    const T v = __ldg(val + e);
+    T x[S];
+    load_row<S>(Vc, ldc, c, x);
+#pragma unroll
+    for (int a = 0; a < S; ++a) w[a] = fma(v, x[a], w[a]);
+  }
+}
+
+// ---- coefficient blocks in shared memory ---------------------------------------
+// co[k][a][b]: k-th s x s coefficient block, converted to the bulk type.
+template <typename T, int S>
+struct Coefs {
+  T ap[S][S], ad[S][S], bp[S][S], bd[S][S];  // MGS coefficients
+  T r1[S][S], r2[S][S];                     // CholQR factors (upper)
+  T r1i[S], r2i[S];                         // reciprocals of their diagonals
+};
+
+// w1 = W - Vp ap - Vc ad ; w2 = w1 - Vp bp - Vc bd (row vectors times s x s blocks)
+template <typename T, int S>
+__device__ __forceinline__ void mgs_row(const T (&p)[S], const T (&q)[S], const T (&M1)[S][S], const T (&M2)[S][S],
+                                        T (&w)[S], bool has_prev) {
+#pragma unroll
+  for (int b = 0; b < S; ++b) {
+    T t = w[b];
+    if (has_prev) {
+#pragma unroll
+      for (int a = 0; a < S; ++a) t = fma(-p[a], M1[a][b], t);
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) t = fma(-q[a], M2[a][b], t);
+    w[b] = t;
+  }
+}
+
+// x R = w  (R upper triangular): forward substitution with precomputed 1/R_bb
+template <typename T, int S>
+__device__ __forceinline__ void trsm_row(const T (&R)[S][S], const T (&Ri)[S], T (&w)[S]) {
+#pragma unroll
+  for (int b = 0; b < S; ++b) {
+    T t = w[b];
+#pragma unroll
+    for (int a = 0; a < b; ++a) t = fma(-w[a], R[a][b], t);
+    w[b] = t * Ri[b];
+  }
+}
+
+// full row recipe of S4 / the second pass: v = ((w - ...) R1^{-1}) R2^{-1}
+template <typename T, int S>
+__device__ __forceinline__ void next_row(const Coefs<T, S>& co, const T (&p)[S], const T (&q)[S], T (&w)[S],
+                                         bool has_prev) {
+  mgs_row<T, S>(p, q, co.ap, co.ad, w, has_prev);
+  mgs_row<T, S>(p, q, co.bp, co.bd, w, has_prev);
+  trsm_row<T, S>(co.r1, co.r1i, w);
+  trsm_row<T, S>(co.r2, co.r2i, w);
+}
+
+template <typename T, int S>
+__device__ void load_coefs(Coefs<T, S>& co, const double* __restrict__ rec, int stage) {
+  // stage: how many of the records are valid (1: alpha, 2: +beta,R1, 3: +R2)
+  const int SS = S * S;
+  for (int k = threadIdx.x; k < SS; k += blockDim.x) {
+    const int a = k / S, b = k % S;
+    co.ap[a][b] = T(rec[REC_APREV * SS + k]);
+    co.ad[a][b] = T(rec[REC_ADIAG * SS + k]);
+    if (stage >= 2) {
+      co.bp[a][b] = T(rec[REC_BPREV * SS + k]);
+      co.bd[a][b] = T(rec[REC_BDIAG * SS + k]);
+      co.r1[a][b] = T(rec[REC_R1 * SS + k]);
+    }
+    if (stage >= 3) co.r2[a][b] = T(rec[REC_R2 * SS + k]);
+  }
+  for (int b = threadIdx.x; b < S; b += blockDim.x) {
+    if (stage >= 2) co.r1i[b] = T(1.0 / rec[REC_R1 * SS + b * S + b]);
+    if (stage >= 3) co.r2i[b] = T(1.0 / rec[REC_R2 * SS + b * S + b]);
+  }
+  __syncthreads();
+}
+
+// ---- deterministic block reduction + last-CTA finalisation ------------------------
+template <typename Acc, int NACC>
+__device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials, unsigned int* counter,
+                                double* __restrict__ tot /*smem NACC*/, double* __restrict__ scratch /*smem kWarps*NACC*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) {
+    Acc v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) scratch[warp * NACC + k] = (double)v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += scratch[w * NACC + k];
+    partials[(size_t)blockIdx.x * NACC + k] = t;
+  }
+  __threadfence();
+  __shared__ unsigned int ticket;
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return false;
+  __threadfence();
+  for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
+    double t = 0.0;
+    for (unsigned int b = 0; b < gridDim.x; ++b) t += __ldcg(partials + (size_t)b * NACC + k);
+    tot[k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// small dense helpers on one thread (fp64, S <= 8)
+template <int S>
+__device__ bool chol_upper(const double* G, double* R) {
+  // G = R^T R, R upper triangular with positive diagonal
+  for (int i = 0; i < S * S; ++i) R[i] = 0.0;
+  for (int j = 0; j < S; ++j) {
+    double d = G[j * S + j];
+    for (int k = 0; k < j; ++k) d -= R[k * S + j] * R[k * S + j];
+    if (!(d > 0.0) || !isfinite(d)) return false;
+    const double rjj = sqrt(d);
+    R[j * S + j] = rjj;
+    for (int i = j + 1; i < S; ++i) {
+      double t = G[j * S + i];
+      for (int k = 0; k < j; ++k) t -= R[k * S + j] * R[k * S + i];
+      R[j * S + i] = t / rjj;
+    }
+  }
+  return true;
+}
+template <int S>
+__device__ void matmul(const double* A, const double* B, double* C) {  // C = A B
+  for (int i = 0; i < S; ++i)
+    for (int j = 0; j < S; ++j) {
+      double t = 0.0;
+      for (int k = 0; k < S; ++k) t += A[i * S + k] * B[k * S + j];
+      C[i * S + j] = t;
+    }
+}
+template <int S>
+__device__ bool all_finite(const double* A, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(A[i])) return false;
+  return true;
+}
+
+// ---- sweep kernels -----------------------------------------------------------
+struct SweepArgs {
+  OpDev op;
+  int j;           // iteration index (1-based); its log record is op.log + j*LOG_NREC*S*S
+  int has_prev;    // j > 1
+  const void* Vp;  // V_{j-1}
+  const void* Vc;  // V_j
+  void* Vn;        // V_{j+1} (S4) or W (S1)
+  int64_t ldp, ldc, ldn;
+  int* flags;
+};
+
+// S1: SpMM + first MGS projections
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_spmm_proj(SweepArgs g) {
+  using Acc = typename AccT<T>::type;
+  constexpr int NACC = 3 * S * S;
+  Acc acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k] = Acc(0);
+  const T* Vp = static_cast<const T*>(g.Vp);
+  const T* Vc = static_cast<const T*>(g.Vc);
+  T* W = static_cast<T*>(g.Vn);
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  for (int64_t sl = gwarp; sl < g.op.nslices; sl += nwarps) {
+    const int64_t rs = sl * LYAP_SLICE + lane;
+    const int64_t row = g.op.perm ? (rs < g.op.n ? (int64_t)g.op.perm[rs] : g.op.n) : rs;
+    if (row < g.op.n) {
+      T w[S];
+      sell_row<T, S>(g.op, sl, lane, Vc, g.ldc, w);
+      store_row<S>(W, (int64_t)S, row, w);
+      T q[S], p[S];
+      load_row<S>(Vc, g.ldc, row, q);
+      if (g.has_prev) load_row<S>(Vp, g.ldp, row, p);
+      else {
+#pragma unroll
+        for (int a = 0; a < S; ++a) p[a] = T(0);
+      }
+#pragma unroll
+      for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int b = 0; b < S; ++b) {
+          acc[a * S + b] = fma((Acc)p[a], (Acc)w[b], acc[a * S + b]);
+          acc[S * S + a * S + b] = fma((Acc)q[a], (Acc)w[b], acc[S * S + a * S + b]);
+          acc[2 * S * S + a * S + b] = fma((Acc)q[a], (Acc)p[b], acc[2 * S * S + a * S + b]);
+        }
+    }
+  }
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  if (threadIdx.x == 0) {
+    constexpr int SS = S * S;
+    double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+    double ap[SS], ad[SS], cr[SS], t[SS];
+    for (int k = 0; k < SS; ++k) {
+      ap[k] = g.has_prev ? tot[k] : 0.0;
+      cr[k] = g.has_prev ? tot[2 * SS + k] : 0.0;
+    }
+    matmul<S>(cr, ap, t);
+    for (int k = 0; k < SS; ++k) ad[k] = tot[SS + k] - t[k];
+    for (int k = 0; k < SS; ++k) {
+      rec[REC_APREV * SS + k] = ap[k];
+      rec[REC_ADIAG * SS + k] = ad[k];
+      rec[REC_CROSS * SS + k] = cr[k];
+    }
+    if (!all_finite<S>(ad, SS) || !all_finite<S>(ap, SS)) atomicOr(g.flags, DERR_NONFINITE);
+  }
+}
+
+// S2: second MGS projections + first Gram
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_proj2_gram1(SweepArgs g) {
+  using Acc = typename AccT<T>::type;
+  constexpr int SS = S * S;
+  constexpr int NACC = 3 * SS;
+  __shared__ Coefs<T, S> co;
+  const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  load_coefs<T, S>(co, rec, 1);
+  Acc acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k] = Acc(0);
+  const T* Vp = static_cast<const T*>(g.Vp);
+  const T* Vc = static_cast<const T*>(g.Vc);
+  const T* W = static_cast<const T*>(g.Vn);
+  const bool hp = g.has_prev;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
+    T w[S], p[S], q[S];
+    load_row<S>(W, (int64_t)S, row, w);
+    load_row<S>(Vc, g.ldc, row, q);
+    if (hp) load_row<S>(Vp, g.ldp, row, p);
+    else {
+#pragma unroll
+      for (int a = 0; a < S; ++a) p[a] = T(0);
+    }
+    mgs_row<T, S>(p, q, co.ap, co.ad, w, hp);
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int b = 0; b < S; ++b) {
+        acc[a * S + b] = fma((Acc)p[a], (Acc)w[b], acc[a * S + b]);
+        acc[SS + a * S + b] = fma((Acc)q[a], (Acc)w[b], acc[SS + a * S + b]);
+        acc[2 * SS + a * S + b] = fma((Acc)w[a], (Acc)w[b], acc[2 * SS + a * S + b]);
+      }
+  }
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  if (threadIdx.x == 0) {
+    double* rw = g.op.log + (size_t)g.j * LOG_NREC * SS;
+    double bp[SS], bd[SS], cr[SS], t[SS], G[SS], R1[SS];
+    for (int k = 0; k < SS; ++k) {
+      bp[k] = hp ? tot[k] : 0.0;
+      cr[k] = rw[REC_CROSS * SS + k];
+    }
+    matmul<S>(cr, bp, t);
+    for (int k = 0; k < SS; ++k) bd[k] = tot[SS + k] - t[k];
+    // G1 = w1^T w1 - bp^T bp - bd^T bd: Gram of w2 = w1 - V beta (V orthonormal up to rounding)
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b) {
+        double v = 0.5 * (tot[2 * SS + a * S + b] + tot[2 * SS + b * S + a]);
+        for (int k = 0; k < S; ++k) v -= bp[k * S + a] * bp[k * S + b] + bd[k * S + a] * bd[k * S + b];
+        G[a * S + b] = v;
+      }
+    for (int k = 0; k < SS; ++k) {
+      rw[REC_BPREV * SS + k] = bp[k];
+      rw[REC_BDIAG * SS + k] = bd[k];
+    }
+    if (!all_finite<S>(G, SS)) atomicOr(g.flags, DERR_NONFINITE);
+    if (!chol_upper<S>(G, R1)) {
+      atomicOr(g.flags, DERR_BREAKDOWN);
+      for (int k = 0; k < SS; ++k) R1[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
+    }
+    for (int k = 0; k < SS; ++k) rw[REC_R1 * SS + k] = R1[k];
+  }
+}
+
+// S3: second Gram (CholQR2's second pass)
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_gram2(SweepArgs g) {
+  using Acc = typename AccT<T>::type;
+  constexpr int SS = S * S;
+  constexpr int NACC = SS;
+  __shared__ Coefs<T, S> co;
+  const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  load_coefs<T, S>(co, rec, 2);
+  Acc acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k] = Acc(0);
+  const T* Vp = static_cast<const T*>(g.Vp);
+  const T* Vc = static_cast<const T*>(g.Vc);
+  const T* W = static_cast<const T*>(g.Vn);
+  const bool hp = g.has_prev;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
+    T w[S], p[S], q[S];
+    load_row<S>(W, (int64_t)S, row, w);
+    load_row<S>(Vc, g.ldc, row, q);
+    if (hp) load_row<S>(Vp, g.ldp, row, p);
+    else {
+#pragma unroll
+      for (int a = 0; a < S; ++a) p[a] = T(0);
+    }
+    mgs_row<T, S>(p, q, co.ap, co.ad, w, hp);
+    mgs_row<T, S>(p, q, co.bp, co.bd, w, hp);
+    trsm_row<T, S>(co.r1, co.r1i, w);
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int b = 0; b < S; ++b) acc[a * S + b] = fma((Acc)w[a], (Acc)w[b], acc[a * S + b]);
+  }
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  if (threadIdx.x == 0) {
+    double* rw = g.op.log + (size_t)g.j * LOG_NREC * SS;
+    double G[SS], R2[SS], R1[SS], Tn[SS];
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b) G[a * S + b] = 0.5 * (tot[a * S + b] + tot[b * S + a]);
+    if (!chol_upper<S>(G, R2)) {
+      atomicOr(g.flags, DERR_BREAKDOWN);
+      for (int k = 0; k < SS; ++k) R2[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
+    }
+    for (int k = 0; k < SS; ++k) R1[k] = rw[REC_R1 * SS + k];
+    matmul<S>(R2, R1, Tn);
+    for (int k = 0; k < SS; ++k) {
+      rw[REC_R2 * SS + k] = R2[k];
+      rw[REC_TNEXT * SS + k] = Tn[k];
+      rw[REC_TDIAG * SS + k] = rw[REC_ADIAG * SS + k] + rw[REC_BDIAG * SS + k];
+      rw[REC_TPREV * SS + k] = rw[REC_APREV * SS + k] + rw[REC_BPREV * SS + k];
+    }
+    if (!all_finite<S>(Tn, SS)) atomicOr(g.flags, DERR_NONFINITE);
+  }
+}
+
+// S4: write V_{j+1}
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_write_next(SweepArgs g) {
+  constexpr int SS = S * S;
+  __shared__ Coefs<T, S> co;
+  const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  load_coefs<T, S>(co, rec, 3);
+  const T* Vp = static_cast<const T*>(g.Vp);
+  const T* Vc = static_cast<const T*>(g.Vc);
+  const T* W = static_cast<const T*>(g.op.W);
+  T* Vn = static_cast<T*>(g.Vn);
+  const bool hp = g.has_prev;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
+    T w[S], p[S], q[S];
+    load_row<S>(W, (int64_t)S, row, w);
+    load_row<S>(Vc, g.ldc, row, q);
+    if (hp) load_row<S>(Vp, g.ldp, row, p);
+    else {
+#pragma unroll
+      for (int a = 0; a < S; ++a) p[a] = T(0);
+    }
+    next_row<T, S>(co, p, q, w, hp);
+    store_row<S>(Vn, g.ldn, row, w);
+  }
+}
+
+// Second pass: V_{j+1} = recipe(A V_j, V_{j-1}, V_j) in one sweep (no reductions).
+// Same SpMM and row recipe as pass 1, hence the same bits.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_pass2(SweepArgs g) {
+  constexpr int SS = S * S;
+  __shared__ Coefs<T, S> co;
+  const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  load_coefs<T, S>(co, rec, 3);
+  const T* Vp = static_cast<const T*>(g.Vp);
+  const T* Vc = static_cast<const T*>(g.Vc);
+  T* Vn = static_cast<T*>(g.Vn);
+  const bool hp = g.has_prev;
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  for (int64_t sl = gwarp; sl < g.op.nslices; sl += nwarps) {
+    const int64_t rs = sl * LYAP_SLICE + lane;
+    const int64_t row = g.op.perm ? (rs < g.op.n ? (int64_t)g.op.perm[rs] : g.op.n) : rs;
+    if (row < g.op.n) {
+      T w[S], p[S], q[S];
+      sell_row<T, S>(g.op, sl, lane, Vc, g.ldc, w);
+      load_row<S>(Vc, g.ldc, row, q);
+      if (hp) load_row<S>(Vp, g.ldp, row, p);
+      else {
+#pragma unroll
+        for (int a = 0; a < S; ++a) p[a] = T(0);
+      }
+      next_row<T, S>(co, p, q, w, hp);
+      store_row<S>(Vn, g.ldn, row, w);
+    }
+  }
+}
+
+// ---- initial block: C = V_1 gamma by CholQR2 on the fp64 right-hand side --------
+// log record 0 holds R1, R2, gamma = R2 R1 (in REC_TNEXT) and beta = ||C||_F in REC_TDIAG[0].
+template <int S>
+__global__ void __launch_bounds__(kThreads) k_init_gram(SweepArgs g, int stage) {
+  constexpr int SS = S * S;
+  __shared__ double r1[S][S];
+  __shared__ double r1i[S];
+  double* rec = g.op.log;
+  if (stage == 2) {
+    for (int k = threadIdx.x; k < SS; k += blockDim.x) r1[k / S][k % S] = rec[REC_R1 * SS + k];
+    for (int b = threadIdx.x; b < S; b += blockDim.x) r1i[b] = 1.0 / rec[REC_R1 * SS + b * S + b];
+    __syncthreads();
+  }
+  double acc[SS];
+#pragma unroll
+  for (int k = 0; k < SS; ++k) acc[k] = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
+    double w[S];
+    load_row<S>(g.op.C, (int64_t)S, row, w);
+    if (stage == 2) trsm_row<double, S>(r1, r1i, w);
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int b = 0; b < S; ++b) acc[a * S + b] = fma(w[a], w[b], acc[a * S + b]);
+  }
+  __shared__ double tot[SS];
+  __shared__ double scratch[kWarps * SS];
+  if (!reduce_partials<double, SS>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  if (threadIdx.x == 0) {
+    double G[SS], R[SS];
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b) G[a * S + b] = 0.5 * (tot[a * S + b] + tot[b * S + a]);
+    if (!all_finite<S>(G, SS)) atomicOr(g.flags, DERR_NONFINITE);
+    if (!chol_upper<S>(G, R)) {
+      atomicOr(g.flags, DERR_BREAKDOWN);
+      for (int k = 0; k < SS; ++k) R[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
+    }
+    if (stage == 1) {
+      double tr = 0.0;
+      for (int a = 0; a < S; ++a) tr += G[a * S + a];
+      for (int k = 0; k < SS; ++k) rec[REC_R1 * SS + k] = R[k];
+      rec[REC_TDIAG * SS] = sqrt(tr);
+    } else {
+      double R1[SS], Gm[SS];
+      for (int k = 0; k < SS; ++k) R1[k] = rec[REC_R1 * SS + k];
+      matmul<S>(R, R1, Gm);
+      for (int k = 0; k < SS; ++k) {
+        rec[REC_R2 * SS + k] = R[k];
+        rec[REC_TNEXT * SS + k] = Gm[k];
+      }
+    }
+  }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_init_write(SweepArgs g) {
+  constexpr int SS = S * S;
+  __shared__ double r1[S][S], r2[S][S];
+  __shared__ double r1i[S], r2i[S];
+  const double* rec = g.op.log;
+  for (int k = threadIdx.x; k < SS; k += blockDim.x) {
+    r1[k / S][k % S] = rec[REC_R1 * SS + k];
+    r2[k / S][k % S] = rec[REC_R2 * SS + k];
+  }
+  for (int b = threadIdx.x; b < S; b += blockDim.x) {
+    r1i[b] = 1.0 / rec[REC_R1 * SS + b * S + b];
+    r2i[b] = 1.0 / rec[REC_R2 * SS + b * S + b];
+  }
+  __syncthreads();
+  T* Vn = static_cast<T*>(g.Vn);
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
+    double w[S];
+    load_row<S>(g.op.C, (int64_t)S, row, w);
+    trsm_row<double, S>(r1, r1i, w);
+    trsm_row<double, S>(r2, r2i, w);
+    T v[S];
+#pragma unroll
+    for (int a = 0; a < S; ++a) v[a] = T(w[a]);
+    store_row<S>(Vn, g.ldn, row, v);
+  }
+}
+
+// ---- dispatch ---------------------------------------------------------------
+template <typename T, int S>
+void step_impl(OpDev& op, int grid, int j, int* flags, cudaStream_t st) {
+  SweepArgs g;
+  g.op = op;
+  g.j = j;
+  g.has_prev = j > 1;
+  g.Vp = op.V[(j + 1) % 3];  // V_{j-1}
+  g.Vc = op.V[(j + 2) % 3];  // V_j   (V_1 lives in V[0])
+  g.ldp = g.ldc = S;
+  g.flags = flags;
+  g.Vn = op.W;
+  g.ldn = S;
+  k_spmm_proj<T, S><<<grid, kThreads, 0, st>>>(g);
+  k_proj2_gram1<T, S><<<grid, kThreads, 0, st>>>(g);
+  k_gram2<T, S><<<grid, kThreads, 0, st>>>(g);
+  g.Vn = op.V[j % 3];        // V_{j+1}
+  k_write_next<T, S><<<grid, kThreads, 0, st>>>(g);
+}
+
+template <typename T, int S>
+void init_impl(OpDev& op, int grid, int* flags, cudaStream_t st) {
+  SweepArgs g;
+  g.op = op;
+  g.j = 0;
+  g.has_prev = 0;
+  g.flags = flags;
+  g.Vn = op.V[0];
+  g.ldn = S;
+  k_init_gram<S><<<grid, kThreads, 0, st>>>(g, 1);
+  k_init_gram<S><<<grid, kThreads, 0, st>>>(g, 2);
+  k_init_write<T, S><<<grid, kThreads, 0, st>>>(g);
+}
+
+template <typename T, int S>
+void pass2_impl(OpDev& op, int grid, int j, const void* vp, int64_t ldp, const void* vc, int64_t ldc, void* vn,
+                int64_t ldn, cudaStream_t st) {
+  SweepArgs g;
+  g.op = op;
+  g.j = j;
+  g.has_prev = j > 1;
+  g.Vp = vp;
+  g.Vc = vc;
+  g.Vn = vn;
+  g.ldp = ldp;
+  g.ldc = ldc;
+  g.ldn = ldn;
+  g.flags = nullptr;
+  k_pass2<T, S><<<grid, kThreads, 0, st>>>(g);
+}
+
+template <typename T>
+void init_T(OpDev& op, int s, int grid, int* flags, cudaStream_t st) {
+  switch (s) {
+    case 1: init_impl<T, 1>(op, grid, flags, st); break;
+    case 2: init_impl<T, 2>(op, grid, flags, st); break;
+    case 3: init_impl<T, 3>(op, grid, flags, st); break;
+    case 4: init_impl<T, 4>(op, grid, flags, st); break;
+    case 8: init_impl<T, 8>(op, grid, flags, st); break;
+  }
+}
+template <typename T>
+void step_T(OpDev& op, int s, int grid, int j, int* flags, cudaStream_t st) {
+  switch (s) {
+    case 1: step_impl<T, 1>(op, grid, j, flags, st); break;
+    case 2: step_impl<T, 2>(op, grid, j, flags, st); break;
+    case 3: step_impl<T, 3>(op, grid, j, flags, st); break;
+    case 4: step_impl<T, 4>(op, grid, j, flags, st); break;
+    case 8: step_impl<T, 8>(op, grid, j, flags, st); break;
+  }
+}
+template <typename T>
+void pass2_T(OpDev& op, int s, int grid, int j, const void* vp, int64_t ldp, const void* vc, int64_t ldc, void* vn,
+             int64_t ldn, cudaStream_t st) {
+  switch (s) {
+    case 1: pass2_impl<T, 1>(op, grid, j, vp, ldp, vc, ldc, vn, ldn, st); break;
+    case 2: pass2_impl<T, 2>(op, grid, j, vp, ldp, vc, ldc, vn, ldn, st); break;
+    case 3: pass2_impl<T, 3>(op, grid, j, vp, ldp, vc, ldc, vn, ldn, st); break;
+    case 4: pass2_impl<T, 4>(op, grid, j, vp, ldp, vc, ldc, vn, ldn, st); break;
+    case 8: pass2_impl<T, 8>(op, grid, j, vp, ldp, vc, ldc, vn, ldn, st); break;
+  }
+}
+
+}  // namespace
+
+int max_nacc(int s) { return 3 * s * s; }
+
+void launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st) {
+  if (bulk_f32) init_T<float>(op, s, grid, d_flags, st);
+  else init_T<double>(op, s, grid, d_flags, st);
+}
+
+void launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st) {
+  if (bulk_f32) step_T<float>(op, s, grid, j, d_flags, st);
+  else step_T<double>(op, s, grid, j, d_flags, st);
+}
+
+// Second pass, step j: writes V_{j+1} from V_{j-1} (vp), V_j (vc).
+void launch_pass2(OpDev& op, int s, int bulk_f32, int grid, int j, const void* vp, int64_t ldp, const void* vc,
+                  int64_t ldc, void* vn, int64_t ldn, cudaStream_t st) {
+  if (bulk_f32) pass2_T<float>(op, s, grid, j, vp, ldp, vc, ldc, vn, ldn, st);
+  else pass2_T<double>(op, s, grid, j, vp, ldp, vc, ldc, vn, ldn, st);
+}
+
+// Second pass, V_1 from C with the logged CholQR2 factors of the first pass.
+void launch_pass2_v1(OpDev& op, int s, int bulk_f32, int grid, void* vn, int64_t ldn, cudaStream_t st) {
+  SweepArgs g;
+  g.op = op;
+  g.j = 0;
+  g.has_prev = 0;
+  g.flags = nullptr;
+  g.Vn = vn;
+  g.ldn = ldn;
+#define LYAP_V1(TT, SS_)                                     \
+  k_init_write<TT, SS_><<<grid, kThreads, 0, st>>>(g)
+  if (bulk_f32) {
+    switch (s) { case 1: LYAP_V1(float, 1); break; case 2: LYAP_V1(float, 2); break; case 3: LYAP_V1(float, 3); break;
+                 case 4: LYAP_V1(float, 4); break; case 8: LYAP_V1(float, 8); break; }
+  } else {
+    switch (s) { case 1: LYAP_V1(double, 1); break; case 2: LYAP_V1(double, 2); break; case 3: LYAP_V1(double, 3); break;
+                 case 4: LYAP_V1(double, 4); break; case 8: LYAP_V1(double, 8); break; }
+  }
+#undef LYAP_V1
+}

@@ -1,0 +1,140 @@
+"""Convenience wrapper over the C ABI: PyTorch owns the device memory, liblyap does the work."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib as L
+
+
+def csr_arrays(A):
+    """(rowptr int64, col int32, val float64) of a scipy CSR matrix, contiguous."""
+    A = A.tocsr()
+    return (np.ascontiguousarray(A.indptr, dtype=np.int64), np.ascontiguousarray(A.indices, dtype=np.int32),
+            np.ascontiguousarray(A.data, dtype=np.float64))
+
+
+class Solver:
+    """One Lyapunov (B is None) or Sylvester solve through lyap_create/solve/factor.
+
+    ``inputs="device"`` uploads A, B, C with PyTorch before calling lyap_create;
+    ``inputs="host"`` hands host pointers to lyap_create, which copies them.
+    """
+
+    def __init__(self, A, C1, B=None, C2=None, *, tol=1e-8, maxit=1000, check_every=1, trunc_eps=1e-12,
+                 precision="f64", sell_sigma=1, pass2_blocks=16, check_batch=32, zcap=0, inputs="device",
+                 device="cuda:0", val_dtype="f64"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.sylv = B is not None
+        self.s = int(C1.shape[1])
+        self.n1 = int(A.shape[0])
+        self.n2 = int(B.shape[0]) if self.sylv else self.n1
+        self.precision = L.LYAP_PREC_MIXED if precision == "mixed" else L.LYAP_PREC_F64
+        self.maxit = int(maxit)
+        opt = L.lyap_default_options()
+        opt.maxit = int(maxit)
+        opt.check_every = int(check_every)
+        opt.trunc_eps = float(trunc_eps)
+        opt.precision = self.precision
+        opt.sell_sigma = int(sell_sigma)
+        opt.pass2_blocks = int(pass2_blocks)
+        opt.check_batch = int(check_batch)
+        opt.zcap = int(zcap)
+        self.opt = opt
+        self._keep = []
+        vdt = np.float32 if val_dtype == "f32" else np.float64
+        self._csr = [self._make_csr(A, inputs, vdt)]
+        if self.sylv:
+            self._csr.append(self._make_csr(B, inputs, vdt))
+        self.ws_bytes = L.lyap_workspace_size(self._csr[0], self._csr[1] if self.sylv else None, self.s, opt)
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device).cuda_stream
+        c_mem = L.LYAP_MEM_HOST if inputs == "host" else L.LYAP_MEM_DEVICE
+        cptr = [self._make_rhs(C1, inputs)]
+        if self.sylv:
+            cptr.append(self._make_rhs(C2, inputs))
+        self.h = L.lyap_create(self._csr[0], self._csr[1] if self.sylv else None, cptr[0], cptr[1] if self.sylv else None,
+                               c_mem, self.s, tol, opt, self.ws.data_ptr(), self.ws_bytes, self.stream)
+        self._keep.clear()
+        self.status = None
+        self.m = 0
+
+    def _make_csr(self, A, inputs, vdt):
+        rp, cl, vl = csr_arrays(A)
+        vl = vl.astype(vdt)
+        c = L.lyap_csr()
+        c.n = A.shape[0]
+        c.nnz = cl.shape[0]
+        c.val_dtype = L.LYAP_F32 if vdt == np.float32 else L.LYAP_F64
+        if inputs == "host":
+            c.mem = L.LYAP_MEM_HOST
+            arrs = (rp, cl, vl)
+            c.rowptr, c.col, c.val = (a.ctypes.data for a in arrs)
+        else:
+            c.mem = L.LYAP_MEM_DEVICE
+            t = self.torch
+            arrs = (t.from_numpy(rp).to(self.device), t.from_numpy(cl).to(self.device), t.from_numpy(vl).to(self.device))
+            c.rowptr, c.col, c.val = (a.data_ptr() for a in arrs)
+        self._keep.append(arrs)
+        return c
+
+    def _make_rhs(self, C, inputs):
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        if inputs == "host":
+            self._keep.append(C)
+            return C.ctypes.data
+        t = self.torch.from_numpy(C).to(self.device)
+        self._keep.append(t)
+        return t.data_ptr()
+
+    def solve(self) -> int:
+        self.status = L.lyap_solve(self.h, self.stream)
+        _, self.m, _ = L.lyap_residual_norm(self.h, 0)
+        return self.status
+
+    def history(self) -> np.ndarray:
+        hist, m, _ = L.lyap_residual_norm(self.h, self.maxit)
+        return hist[:m]
+
+    def factor(self, tcap=None, z_dtype=None, out="device"):
+        """Returns Z (n1 x t) for Lyapunov, (Z1, Z2) for Sylvester, as torch tensors (or numpy for out='host')."""
+        t = self.torch
+        if tcap is None:
+            tcap = max(1, self.s * self.m)
+        if z_dtype is None:
+            z_dtype = "f32" if self.precision == L.LYAP_PREC_MIXED else "f64"
+        zd = L.LYAP_F32 if z_dtype == "f32" else L.LYAP_F64
+        dt = t.float32 if zd == L.LYAP_F32 else t.float64
+        if out == "host":
+            npdt = np.float32 if zd == L.LYAP_F32 else np.float64
+            Z1 = np.zeros((self.n1, tcap), dtype=npdt)
+            Z2 = np.zeros((self.n2, tcap), dtype=npdt) if self.sylv else None
+            p1, p2 = Z1.ctypes.data, (Z2.ctypes.data if Z2 is not None else None)
+            mem = L.LYAP_MEM_HOST
+        else:
+            Z1 = t.zeros((self.n1, tcap), dtype=dt, device=self.device)
+            Z2 = t.zeros((self.n2, tcap), dtype=dt, device=self.device) if self.sylv else None
+            p1, p2 = Z1.data_ptr(), (Z2.data_ptr() if Z2 is not None else None)
+            mem = L.LYAP_MEM_DEVICE
+        tk = L.lyap_factor(self.h, p1, tcap, p2, tcap, zd, mem, tcap, self.stream)
+        Z1 = Z1[:, :tk]
+        if self.sylv:
+            return Z1, Z2[:, :tk]
+        return Z1
+
+    def phase_times(self):
+        return L.lyap_phase_times(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lyap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,96 @@
+"""The C-ABI library loads and exports every symbol include/lyap.h declares (no GPU needed)."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib(repo_root):
+    from paper_1602_05033_gb300 import _lib
+    from paper_1602_05033_gb300 import build as b
+
+    if not os.path.exists(_lib.LIB_PATH):
+        b.build()
+    return _lib.load()
+
+
+def _declared(repo_root):
+    text = open(os.path.join(repo_root, "include", "lyap.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lyap_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib, repo_root):
+    from paper_1602_05033_gb300 import _lib
+
+    names = _declared(repo_root)
+    assert len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.EXPORTED) == names
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_1602_05033_gb300 import _lib
+
+    assert _lib.status_string(0) == "ok"
+    assert "breakdown" in _lib.status_string(_lib.LYAP_ERR_BREAKDOWN).lower()
+    o = _lib.lyap_default_options()
+    assert o.maxit == 1000 and o.check_every == 1 and o.trunc_eps == 1e-12 and o.pass2_blocks == 16
+
+
+def _host_csr(A, keep):
+    from paper_1602_05033_gb300 import _lib, csr_arrays
+
+    rp, cl, vl = csr_arrays(A)
+    keep += [rp, cl, vl]
+    c = _lib.lyap_csr()
+    c.n, c.nnz = A.shape[0], cl.shape[0]
+    c.rowptr, c.col, c.val = rp.ctypes.data, cl.ctypes.data, vl.ctypes.data
+    c.val_dtype, c.mem = _lib.LYAP_F64, _lib.LYAP_MEM_HOST
+    return c
+
+
+def test_workspace_size_host_inputs(lib):
+    """Host-side planning only: SELL padding and the storage of Alg. 1 grow as documented."""
+    from paper_1602_05033_gb300 import _lib
+
+    keep = []
+    A = _host_csr(wl.laplacian_2d(30), keep)
+    o = _lib.lyap_default_options()
+    o.maxit = 100
+    b1 = _lib.lyap_workspace_size(A, None, 1, o)
+    b4 = _lib.lyap_workspace_size(A, None, 4, o)
+    o.maxit = 200
+    b4b = _lib.lyap_workspace_size(A, None, 4, o)
+    assert 0 < b1 < b4 < b4b
+    B = _host_csr(wl.laplacian_2d(20), keep)
+    assert _lib.lyap_workspace_size(A, B, 4, o) > b4b
+
+
+def test_invalid_arguments_rejected(lib):
+    from paper_1602_05033_gb300 import _lib
+
+    keep = []
+    A = _host_csr(wl.laplacian_2d(8), keep)
+    o = _lib.lyap_default_options()
+    with pytest.raises(_lib.LyapError) as e:
+        _lib.lyap_workspace_size(A, None, 5, o)  # unsupported block size
+    assert e.value.status == _lib.LYAP_ERR_ARG
+    bad = _lib.lyap_csr()
+    bad.n = -1
+    with pytest.raises(_lib.LyapError):
+        _lib.lyap_workspace_size(bad, None, 1, o)
+    # rowptr that does not end at nnz
+    rp = np.array([0, 1, 3], dtype=np.int64)
+    keep.append(rp)
+    A2 = _lib.lyap_csr()
+    A2.n, A2.nnz, A2.rowptr, A2.col, A2.val = 2, 2, rp.ctypes.data, rp.ctypes.data, rp.ctypes.data
+    A2.val_dtype, A2.mem = _lib.LYAP_F64, _lib.LYAP_MEM_HOST
+    with pytest.raises(_lib.LyapError):
+        _lib.lyap_workspace_size(A2, None, 1, o)

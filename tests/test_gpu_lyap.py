@@ -1,0 +1,181 @@
+"""GPU parity of the Lyapunov path (C ABI) against the FP64 oracle.
+
+Tolerances:
+  * residual history, fp64 path: |rel_gpu(m) - rel_oracle(m)| <= HIST_ATOL + HIST_RTOL * rel_oracle(m).
+    Both sides evaluate the same quantity from T_m built by different but
+    equivalent orthogonalisations (fused MGS + CholQR2 on the GPU, textbook MGS +
+    Householder QR in the oracle), so they agree to rounding propagated through
+    the Lanczos recurrence.
+  * the factor Z is compared through X = Z Z^T applied to random vectors (Z is
+    unique only up to an orthogonal factor), relative 1e-8.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import explicit
+from oracle import lyap as olyap
+
+pytestmark = pytest.mark.gpu
+
+HIST_ATOL = 1e-10
+HIST_RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1602_05033_gb300 as p
+    from paper_1602_05033_gb300 import _lib
+    from paper_1602_05033_gb300 import build as b
+
+    b.build()
+    _lib.load()
+    return p
+
+
+def _hist_ok(h_gpu, h_ref):
+    n = min(len(h_gpu), len(h_ref))
+    d = np.abs(h_gpu[:n] - h_ref[:n])
+    bound = HIST_ATOL + HIST_RTOL * np.abs(h_ref[:n])
+    return bool(np.all(d <= bound)), float(np.max(d / bound)) if n else 0.0
+
+
+def _xprobe(Z, Zo, seed=0):
+    u = np.random.default_rng(seed).standard_normal((Z.shape[0], 4))
+    a = Z @ (Z.T @ u)
+    b = Zo @ (Zo.T @ u)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _solve_both(pkg, A, C, tol, maxit, **kw):
+    ref = olyap.solve(A, C, tol=tol, maxit=maxit)
+    sol = pkg.Solver(A, C, tol=tol, maxit=maxit, **kw)
+    st = sol.solve()
+    return ref, sol, st
+
+
+def test_config_c1_history_and_factor(pkg):
+    """Lyapunov, 2D Laplacian 50x50, s = 1, tol 1e-8 (the small fp64 workload)."""
+    P = wl.config_c1(0)
+    ref, sol, st = _solve_both(pkg, P.A, P.C1, P.tol, P.maxit)
+    assert st == 0 and sol.m == ref.m
+    ok, worst = _hist_ok(sol.history(), ref.history)
+    assert ok, worst
+    Z = sol.factor().cpu().numpy()
+    Zo, _ = olyap.factor(P.A, P.C1, ref)
+    assert abs(Z.shape[1] - Zo.shape[1]) <= 1
+    assert _xprobe(Z, Zo) <= 1e-8
+    rel = explicit.lyap_lowrank(P.A, Z, P.C1) / ref.log.beta**2
+    rel_o = explicit.lyap_lowrank(P.A, Zo, P.C1) / ref.log.beta**2
+    assert abs(rel - rel_o) <= 1e-9
+    sol.close()
+
+
+@pytest.mark.parametrize("s,k,seed", [(2, 20, 1), (3, 14, 2), (4, 16, 3), (4, 33, 4)])
+def test_block_sizes_laplacian(pkg, s, k, seed):
+    A = wl.laplacian_2d(k)
+    C = wl.rhs(A.shape[0], s, seed)
+    ref, sol, st = _solve_both(pkg, A, C, 1e-9, 400)
+    assert st == 0 and sol.m == ref.m
+    ok, worst = _hist_ok(sol.history(), ref.history)
+    assert ok, worst
+    Z = sol.factor().cpu().numpy()
+    Zo, _ = olyap.factor(A, C, ref)
+    assert _xprobe(Z, Zo) <= 1e-8
+    sol.close()
+
+
+def test_dense_spectrum_operator(pkg):
+    """A dense SND matrix stored as CSR: every row has n entries (wide SELL slices)."""
+    import scipy.sparse as sp
+
+    # n = 300 and at most 40 steps of s = 3: the space never fills R^n, where both
+    # sides would only be orthonormalising rounding noise
+    A = sp.csr_matrix(wl.random_snd_dense(300, seed=5, lam_min=1.0, lam_max=500.0))
+    C = wl.rhs(300, 3, 6)
+    ref, sol, st = _solve_both(pkg, A, C, 1e-10, 40)
+    assert sol.m == ref.m
+    ok, worst = _hist_ok(sol.history(), ref.history)
+    assert ok, worst
+    sol.close()
+
+
+def test_host_inputs_match_device_inputs(pkg):
+    A = wl.laplacian_2d(18)
+    C = wl.rhs(A.shape[0], 2, 9)
+    a = pkg.Solver(A, C, tol=1e-9, maxit=300, inputs="device")
+    b = pkg.Solver(A, C, tol=1e-9, maxit=300, inputs="host")
+    a.solve()
+    b.solve()
+    assert a.m == b.m
+    assert np.array_equal(a.history(), b.history())  # same kernels, same bits
+    Za = a.factor().cpu().numpy()
+    Zb = b.factor(out="host")
+    assert np.array_equal(Za, Zb)
+    a.close()
+    b.close()
+
+
+def test_check_period(pkg):
+    """check_every = d tests only m = d, 2d, ... (the paper's periodic check)."""
+    A = wl.laplacian_2d(20)
+    C = wl.rhs(A.shape[0], 1, 2)
+    ref = olyap.solve(A, C, tol=1e-8, maxit=500, check_every=5)
+    sol = pkg.Solver(A, C, tol=1e-8, maxit=500, check_every=5)
+    sol.solve()
+    assert sol.m == ref.m and sol.m % 5 == 0
+    h = sol.history()
+    assert np.all(np.isnan(h[np.arange(len(h)) % 5 != 4]))
+    ok, worst = _hist_ok(h[4::5], ref.history[4::5])
+    assert ok, worst
+
+
+def test_not_converged_within_maxit(pkg):
+    from paper_1602_05033_gb300 import _lib
+
+    A = wl.laplacian_2d(30)
+    C = wl.rhs(A.shape[0], 1, 3)
+    sol = pkg.Solver(A, C, tol=1e-12, maxit=20)
+    assert sol.solve() == _lib.LYAP_NOT_CONVERGED
+    assert sol.m == 20 and len(sol.history()) == 20
+    ref = olyap.solve(A, C, tol=1e-12, maxit=20)
+    ok, worst = _hist_ok(sol.history(), ref.history)
+    assert ok, worst
+
+
+def test_nonfinite_rhs_rejected(pkg):
+    from paper_1602_05033_gb300 import _lib
+
+    A = wl.laplacian_2d(10)
+    C = wl.rhs(100, 2, 1)
+    C[7, 1] = np.nan
+    sol = pkg.Solver(A, C, tol=1e-8, maxit=50)
+    with pytest.raises(_lib.LyapError) as e:
+        sol.solve()
+    assert e.value.status == _lib.LYAP_ERR_NONFINITE
+
+
+def test_rank_deficient_rhs_is_breakdown(pkg):
+    from paper_1602_05033_gb300 import _lib
+
+    A = wl.laplacian_2d(10)
+    C = wl.rhs(100, 2, 1)
+    C[:, 1] = C[:, 0]
+    sol = pkg.Solver(A, C, tol=1e-8, maxit=50)
+    with pytest.raises(_lib.LyapError) as e:
+        sol.solve()
+    assert e.value.status == _lib.LYAP_ERR_BREAKDOWN
+
+
+def test_indefinite_operator_detected(pkg):
+    from paper_1602_05033_gb300 import _lib
+
+    A = wl.laplacian_2d(10, shift=-2.0 * 8 * 11**2)  # shifted to positive definite
+    C = wl.rhs(100, 1, 1)
+    sol = pkg.Solver(A, C, tol=1e-8, maxit=30)
+    with pytest.raises(_lib.LyapError) as e:
+        sol.solve()
+    assert e.value.status == _lib.LYAP_ERR_NOT_NEGDEF
