@@ -1,0 +1,411 @@
+"""Benchmark: time to relative residual 1e-8 on the n = 1e6 Lyapunov workload.
+
+Workload: A = -(3D 7-point Laplacian on a 100^3 grid, h = 1/101), n = 1e6,
+C = rhs(n, 4, seed = rank) iid N(0,1), s = 4, tol 1e-8, maxit 400, mixed
+precision (fp32 basis and SpMM, fp64 reductions, CholQR2 factors, reduced
+eigenproblem and residual), two-pass factor.  One step = lyap_create (SELL-C-sigma
+build from the device-resident CSR) + lyap_solve + lyap_factor into a device Z;
+the metric is that step's time in seconds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica (seed = rank, weak scaling;
+the method has no cross-rank exchange on one GPU per problem).  Rank 0 prints
+one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time to rel. residual 1e-8 (s)"
+UNIT = "s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_c2_lap3d100_s4.json")
+WORKLOAD = "Lyapunov, A = -(3D 7-point Laplacian on 100^3), n = 1e6, s = 4, C iid N(0,1), tol 1e-8, maxit 400, mixed precision, two-pass"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k", type=int, default=100, help="grid edge (100 -> n = 1e6)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(k: int, m_star: int, sample_its: int = 40):
+    """Times the FP64 oracle (as it stands) on a bounded sample of the workload and
+    extrapolates to the full solve of m_star iterations.
+
+    Sample: the first ``sample_its`` block Lanczos steps with every convergence check,
+    5 second-pass steps and the truncated factor at m = sample_its.  Model (the step
+    costs are constant in m, the check of T_m grows like m^2 at these sizes, the
+    factor's small dense eigenproblems like m^2 as well):
+        T = m_star (t_lanczos + t_pass2) + c sum_{m <= m_star} m^2 + t_factor (m_star / sample_its)^2
+    with c the mean of t_check(m) / m^2 over the second half of the sample."""
+    import workloads as wl
+    from oracle import lyap
+
+    P = wl.config_c2(0, k=k)
+    A, C = P.A, P.C1
+    t0 = time.perf_counter()
+    V1, log = lyap.start(C)
+    Vp, Vc = None, V1
+    tl, tc = [], []
+    for j in range(1, sample_its + 1):
+        a = time.perf_counter()
+        Vn, tp, td, tn = lyap.lanczos_step(A, Vp, Vc)
+        log.tau_prev.append(tp)
+        log.tau_diag.append(td)
+        log.tau_next.append(tn)
+        Vp, Vc = Vc, Vn
+        b = time.perf_counter()
+        lyap.residual_at(log, j)
+        c = time.perf_counter()
+        tl.append(b - a)
+        tc.append(c - b)
+    a = time.perf_counter()
+    for _ in zip(range(5), lyap.regenerate_basis(A, C, log, sample_its)):
+        pass
+    t_p2 = (time.perf_counter() - a) / 5
+    a = time.perf_counter()
+    lyap.truncated_factor(log, sample_its)
+    t_fac = time.perf_counter() - a
+    sample_secs = time.perf_counter() - t0
+    ms = np.arange(1, sample_its + 1)
+    sel = ms >= sample_its // 2
+    cfit = float(np.mean(np.array(tc)[sel] / ms[sel] ** 2))
+    checks = cfit * float(np.sum(np.arange(1, m_star + 1, dtype=float) ** 2))
+    total = m_star * (float(np.mean(tl)) + t_p2) + checks + t_fac * (m_star / sample_its) ** 2
+    desc = (f"FP64 oracle, first {sample_its} of {m_star} block Lanczos steps of the n={k**3} workload with every "
+            f"check, 5 second-pass steps and the truncated factor at m={sample_its} ({sample_secs:.1f} s of CPU "
+            f"time); extrapolated to m={m_star}: steps x {m_star}, checks as c*m^2")
+    return total, sample_secs, desc
+
+
+def cores_used():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    golden = json.load(open(GOLDEN))
+    m_star = golden["m"] if args.k == 100 else 400
+    vals, secs = [], 0.0
+    desc = ""
+    for it in range(args.warmup + args.steps):
+        v, s, desc = oracle_sample(args.k, m_star, sample_its=30)
+        secs += s
+        if it >= args.warmup:
+            vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 * value,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("mixed precision", "fp64 oracle")},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ours(args):
+    import torch
+
+    import workloads as wl
+    from paper_1602_05033_gb300 import _lib as L
+    from paper_1602_05033_gb300 import csr_arrays
+
+    rank, world, local = dist_env()
+    golden = json.load(open(GOLDEN)) if args.k == 100 else None
+    # the CPU baseline runs first, before any CUDA work in this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m_star = golden["m"] if golden else 400
+        v, s, desc = oracle_sample(args.k, m_star)
+        cpu = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": desc}
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    P = wl.config_c2(rank, k=args.k)
+    rp, cl, vl = csr_arrays(P.A)
+    vl32 = vl.astype(np.float32)
+    assert np.array_equal(vl32.astype(np.float64), vl), "Laplacian values must be exact in fp32"
+    n, s = P.A.shape[0], P.s
+    d_rp, d_cl, d_vl = (torch.from_numpy(x).to(dev) for x in (rp, cl, vl32))
+    d_C = torch.from_numpy(P.C1).to(dev)
+    csr = L.lyap_csr()
+    csr.n, csr.nnz = n, cl.shape[0]
+    csr.rowptr, csr.col, csr.val = d_rp.data_ptr(), d_cl.data_ptr(), d_vl.data_ptr()
+    csr.val_dtype, csr.mem = L.LYAP_F32, L.LYAP_MEM_DEVICE
+    opt = L.lyap_default_options()
+    opt.maxit = 400
+    opt.precision = L.LYAP_PREC_MIXED
+    tcap = 256
+    ws_bytes = L.lyap_workspace_size(csr, None, s, opt)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    Z = torch.empty((n, tcap), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def step():
+        h = L.lyap_create(csr, None, d_C.data_ptr(), None, L.LYAP_MEM_DEVICE, s, 1e-8, opt, ws.data_ptr(), ws_bytes,
+                          stream)
+        try:
+            st = L.lyap_solve(h, stream)
+            t = L.lyap_factor(h, Z.data_ptr(), tcap, None, 0, L.LYAP_F32, L.LYAP_MEM_DEVICE, tcap, stream)
+            hist, m, _ = L.lyap_residual_norm(h, opt.maxit)
+            ph = L.lyap_phase_times(h)
+        finally:
+            L.lyap_destroy(h)
+        return st, t, m, hist, ph
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, phases, last = [], [], None
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush (512 MB write) outside the timed interval
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        last = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phases.append(last[4])
+    clk = clocks.stop()
+    barrier()
+    total_ms = float(np.sum(times))
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    st, t, m, hist, ph = last
+    if st != L.LYAP_OK:
+        raise RuntimeError(f"solve did not converge (status {st})")
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the block Lanczos step (SpMM + two MGS sweeps + CholQR2): algorithmic
+    # bytes = A (fp32 value + int32 column per nonzero) + 5 blocks of n x s fp32
+    # (read V_j, V_{j-1}; W written and read once; V_{j+1} written)
+    nnz = cl.shape[0]
+    alg_bytes = nnz * 8 + 5 * n * s * 4
+    lanczos_ms = float(np.mean([p[5] for p in phases]))
+    steps_run = float(np.mean([p[3] for p in phases]))
+    achieved = alg_bytes * steps_run / (lanczos_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    phase = {k: round(float(np.mean([p[i] for p in phases])), 3) for i, k in
+             enumerate(["create_ms", "solve_ms", "factor_ms", "lanczos_steps", "check_ms", "lanczos_ms"])}
+    launches = int(np.mean([p[6] for p in phases]))
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_arm(args, P, rp, cl, vl32, s, opt, dev)
+    parity = None
+    if golden is not None:
+        g = np.array(golden["history"])
+        k_ = min(len(g), len(hist))
+        parity = {"m_oracle": golden["m"], "m_gpu": int(m), "t_oracle": golden["t"], "t_gpu": int(t),
+                  "max_abs_dhist": float(np.max(np.abs(hist[:k_] - g[:k_])))}
+    line = {
+        "metric": METRIC,
+        "value": ms_per_step / 1000.0,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 bulk / f64 reductions and reduced problem",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "s": s, "nnz": nnz, "tol": 1e-8, "maxit": 400,
+                   "parallelism": f"{world} independent replicas", "l2": "flushed before each step (512 MB write)"},
+        "roofline": {"kernel": "block Lanczos step: SELL SpMM + 2 block MGS sweeps + CholQR2 (4 launches)",
+                     "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "bytes_per_unit": alg_bytes, "peak_source": peak_src},
+        "phases_ms": phase,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "result": {"m": int(m), "t": int(t), "rel_residual": float(hist[m - 1])},
+        "parity_vs_oracle": parity,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def e2e_arm(args, P, rp, cl, vl32, s, opt, dev):
+    """Same metric through the C ABI with host buffers: pinned CSR and C in, pinned Z out."""
+    import torch
+
+    from paper_1602_05033_gb300 import _lib as L
+
+    n = P.A.shape[0]
+    tcap = 128
+    pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+    h_rp, h_cl, h_vl, h_C = pin(rp), pin(cl), pin(vl32), pin(np.ascontiguousarray(P.C1))
+    h_Z = torch.empty((n, tcap), dtype=torch.float32).pin_memory()
+    csr = L.lyap_csr()
+    csr.n, csr.nnz = n, cl.shape[0]
+    csr.rowptr, csr.col, csr.val = h_rp.data_ptr(), h_cl.data_ptr(), h_vl.data_ptr()
+    csr.val_dtype, csr.mem = L.LYAP_F32, L.LYAP_MEM_HOST
+    o = L.lyap_options()
+    for f, _ in L.lyap_options._fields_:
+        setattr(o, f, getattr(opt, f))
+    o.zcap = tcap
+    ws_bytes = L.lyap_workspace_size(csr, None, s, o)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    hist_buf = np.empty(o.maxit)
+    times, t, m = [], 0, 0
+    for it in range(1 + min(args.steps, 3)):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        h = L.lyap_create(csr, None, h_C.data_ptr(), None, L.LYAP_MEM_HOST, s, 1e-8, o, ws.data_ptr(), ws_bytes, stream)
+        try:
+            L.lyap_solve(h, stream)
+            t = L.lyap_factor(h, h_Z.data_ptr(), tcap, None, 0, L.LYAP_F32, L.LYAP_MEM_HOST, tcap, stream)
+            hist, m, _ = L.lyap_residual_norm(h, o.maxit)
+            hist_buf[:m] = hist
+        finally:
+            L.lyap_destroy(h)
+        b = time.perf_counter()
+        if it > 0:
+            times.append(b - a)
+    h2d = rp.nbytes + cl.nbytes + vl32.nbytes + P.C1.nbytes
+    d2h = n * t * 4 + m * 8
+    return {"value": float(np.median(times)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": len(times)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -48,7 +48,8 @@ typedef enum {
   LYAP_ERR_TCAP = 6,       /* the factor needs more than tcap columns              */
   LYAP_ERR_TIMEOUT = 7,    /* a bounded device wait gave up                        */
   LYAP_ERR_CUDA = 8,       /* a CUDA runtime call failed                           */
-  LYAP_ERR_WORKSPACE = 9   /* workspace too small or misaligned (256 B)            */
+  LYAP_ERR_WORKSPACE = 9,  /* workspace too small or misaligned (256 B)            */
+  LYAP_ERR_EIGEN = 10      /* the eigensolver of T_m did not converge (residual test) */
 } lyap_status;
 
 enum { LYAP_F64 = 0, LYAP_F32 = 1 };            /* element types              */
@@ -123,6 +124,16 @@ int lyap_solve(lyap_handle* h, void* stream);
  * *m_out is the final iteration count m.  Host memory. */
 int lyap_residual_norm(lyap_handle* h, double* hist_host, int cap, int* m_out);
 
+/* The projected matrix T_m = V_m^T A V_m of the last solve (J_m for op = 1 in a
+ * Sylvester solve), built from the logged block Lanczos coefficients (Sec. 2):
+ * LAPACK lower band storage ab[d + i*ldab] = T_m[i+d][i], d = 0..s, i = 0..s*m-1,
+ * with the symmetric part of tau_jj on the diagonal blocks and tau_{j+1,j} below
+ * them; gamma (C = V_1 gamma) and tau_{m+1,m}, both s x s row-major.  Host memory;
+ * any pointer may be NULL.  Requires 1 <= m <= the Lanczos steps run by the last
+ * solve (also after a solve that returned an error, for diagnosis). */
+int lyap_projected_matrix(lyap_handle* h, int op, int m, double* ab, int ldab,
+                          double* gamma, double* tau_next);
+
 /* Alg. 1 steps 8-9 with the two-pass device of Sec. 3.3 (4.1 for Sylvester):
  * truncates the reduced solution (eq. 2.5) and accumulates Z = V_m (Q_m Ycheck)
  * while regenerating the basis from the logged coefficients.
@@ -135,9 +146,12 @@ int lyap_residual_norm(lyap_handle* h, double* hist_host, int cap, int* m_out);
 int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2,
                 int z_dtype, int z_mem, int tcap, int* t_out, void* stream);
 
-/* Phase timings of the last solve/factor in milliseconds (CUDA events):
- * out[0] create, out[1] solve, out[2] factor, out[3] second pass alone,
- * out[4] convergence checks (sum of batch times), out[5] Lanczos sweeps. */
+/* Phase timings in milliseconds (CUDA events on the caller's stream):
+ * out[0] create, out[1] solve, out[2] factor, out[3] block Lanczos steps run by the
+ * last solve (>= m: the iteration runs ahead of the checks by up to check_batch - 1),
+ * out[4] convergence checks of the last solve (sum over batches),
+ * out[5] block Lanczos sweeps of the last solve (sum over chunks),
+ * out[6] number of kernels the library launched since lyap_create. */
 int lyap_phase_times(lyap_handle* h, double* out, int cap);
 
 /* Releases the handle's streams and events and the handle itself.  The caller

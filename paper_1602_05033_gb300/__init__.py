@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     lyap_destroy,
     lyap_factor,
     lyap_phase_times,
+    lyap_projected_matrix,
     lyap_residual_norm,
     lyap_solve,
     lyap_workspace_size,

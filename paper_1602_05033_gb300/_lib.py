@@ -22,6 +22,7 @@ LYAP_ERR_TCAP = 6
 LYAP_ERR_TIMEOUT = 7
 LYAP_ERR_CUDA = 8
 LYAP_ERR_WORKSPACE = 9
+LYAP_ERR_EIGEN = 10
 
 LYAP_F64, LYAP_F32 = 0, 1
 LYAP_MEM_DEVICE, LYAP_MEM_HOST = 0, 1
@@ -35,6 +36,7 @@ EXPORTED = (
     "lyap_solve",
     "lyap_residual_norm",
     "lyap_factor",
+    "lyap_projected_matrix",
     "lyap_phase_times",
     "lyap_destroy",
     "lyap_status_string",
@@ -98,6 +100,7 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_residual_norm.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(ct.c_int)]
     lib.lyap_factor.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int, ct.c_int, ct.c_int,
                                 ct.POINTER(ct.c_int), P]
+    lib.lyap_projected_matrix.argtypes = [P, ct.c_int, ct.c_int, P, ct.c_int, P, P]
     lib.lyap_phase_times.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int]
     lib.lyap_destroy.argtypes = [P]
     lib.lyap_status_string.argtypes = [ct.c_int]
@@ -169,6 +172,21 @@ def lyap_factor(h: int, Z1_ptr: int, ldz1: int, Z2_ptr: int | None, ldz2: int, z
         err.t = t.value
         raise err
     return t.value
+
+
+def lyap_projected_matrix(h: int, op: int, m: int, s: int):
+    """(ab, gamma, tau_next): T_m in lower band storage ab[d, i] = T_m[i+d, i], and the s x s blocks."""
+    import numpy as np
+
+    N = s * m
+    ab = np.zeros((N, s + 1))
+    gam = np.zeros((s, s))
+    tau = np.zeros((s, s))
+    st = load().lyap_projected_matrix(ct.c_void_p(h), int(op), int(m), ab.ctypes.data, s + 1, gam.ctypes.data,
+                                      tau.ctypes.data)
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_projected_matrix")
+    return np.ascontiguousarray(ab.T), gam, tau
 
 
 def lyap_phase_times(h: int):

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 size_t factor_ws_bytes(int s, int nmax, int sylv);
 size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32);
@@ -18,10 +19,11 @@ int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col,
 namespace {
 
 int sweep_grid_for(int64_t n) {
-  // fixed per problem size (not per device) so that reductions are reproducible anywhere
-  int64_t g = (n + 4095) / 4096;
+  // fixed per problem size (not per device) so that reductions are reproducible anywhere;
+  // 456 = 3 CTAs of 256 threads on each of 152 SMs
+  int64_t g = (n + 2047) / 2048;
   if (g < 1) g = 1;
-  if (g > 1216) g = 1216;
+  if (g > 456) g = 456;
   return (int)g;
 }
 
@@ -101,7 +103,14 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
   p.sweep_grid = sweep_grid_for(nmaxop);
   p.hist = take(sizeof(double) * (size_t)o.maxit);
   p.flags = take(256);
-  p.check_bytes = (size_t)(1 + p.sylv) * o.check_batch * check_slot_bytes(s, p.nmax);
+  p.chk_err = take(sizeof(int) * (size_t)o.maxit);
+  // the check slots hold per-eigenpair fp64 scratch (O(nmax^2) each): cap their total at 16 GiB
+  {
+    const size_t per = (size_t)(1 + p.sylv) * check_slot_bytes(s, p.nmax);
+    const size_t cap = (size_t)16 << 30;
+    if ((size_t)p.check_batch * per > cap) p.check_batch = (int)std::max<size_t>(1, cap / per);
+  }
+  p.check_bytes = (size_t)(1 + p.sylv) * p.check_batch * check_slot_bytes(s, p.nmax);
   p.check = take(p.check_bytes);
   p.factor_bytes = factor_ws_bytes(s, p.nmax, p.sylv);
   size_t p2 = 0;
@@ -119,21 +128,27 @@ T* at(char* ws, size_t off) {
   return reinterpret_cast<T*>(ws + off);
 }
 
-__global__ void k_init_flags(int* flags, double* hist, int maxit) {
+__global__ void k_init_flags(int* flags, double* hist, int* chk_err, int maxit) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     flags[0] = 0;
     flags[1] = INT_MAX;
+    flags[2] = INT_MAX;
   }
-  if (i < maxit) hist[i] = __longlong_as_double(0x7ff8000000000000LL);
+  if (i < maxit) {
+    hist[i] = __longlong_as_double(0x7ff8000000000000LL);
+    chk_err[i] = 0;
+  }
 }
 
 int status_from_bits(int bits) {
+  // root causes first: a breakdown leaves a degenerate block whose later use may overflow
   if (bits & DERR_BOUNDS) return LYAP_ERR_ARG;
-  if (bits & DERR_NONFINITE) return LYAP_ERR_NONFINITE;
   if (bits & DERR_BREAKDOWN) return LYAP_ERR_BREAKDOWN;
+  if (bits & DERR_NONFINITE) return LYAP_ERR_NONFINITE;
   if (bits & DERR_NOTNEGDEF) return LYAP_ERR_NOT_NEGDEF;
   if (bits & DERR_TIMEOUT) return LYAP_ERR_TIMEOUT;
+  if (bits & DERR_EIGEN) return LYAP_ERR_EIGEN;
   return LYAP_OK;
 }
 
@@ -165,6 +180,7 @@ const char* lyap_status_string(int status) {
     case LYAP_ERR_TIMEOUT: return "bounded device wait expired";
     case LYAP_ERR_CUDA: return "CUDA runtime error";
     case LYAP_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case LYAP_ERR_EIGEN: return "reduced eigensolver did not converge";
     default: return "unknown status";
   }
 }
@@ -218,10 +234,12 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
   if (cudaMallocHost(&h->flags_host, sizeof(int) * 8) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   h->hist = at<double>(h->ws, p.hist);
   h->flags = at<int>(h->ws, p.flags);
+  h->chk_err = at<int>(h->ws, p.chk_err);
   h->check_ws = h->ws + p.check;
   h->factor_ws = h->ws + p.factor;
   h->zstage = h->ws + p.zstage;
-  k_init_flags<<<(o.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, o.maxit);
+  k_init_flags<<<(o.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, h->chk_err, o.maxit);
+  h->launches = 1;
   char* stage = h->ws + p.staging;
   for (int k = 0; k < 1 + p.sylv; ++k) {
     const lyap_csr* M = k == 0 ? A : B;
@@ -264,6 +282,7 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
     }
     rc = sell_build(M, rp, cl, vl, o.sell_sigma, p.bulk_f32, op, h->flags, st);
     if (rc != LYAP_OK) return fail(rc);
+    h->launches += 1;
     const cudaMemcpyKind kind = c_mem == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     if (cudaMemcpyAsync(op.C, Ck, sizeof(double) * (size_t)op.n * s, kind, st) != cudaSuccess)
       return fail(LYAP_ERR_CUDA);
@@ -291,8 +310,9 @@ int lyap_solve(lyap_handle* h, void* stream) {
   const Plan& p = h->plan;
   const int s = h->s;
   cudaEventRecord(h->ev[0], st);
-  k_init_flags<<<(p.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, p.maxit);
-  for (int k = 0; k < 1 + p.sylv; ++k) launch_init_block(h->op[k], s, p.bulk_f32, p.sweep_grid, h->flags, st);
+  k_init_flags<<<(p.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, h->chk_err, p.maxit);
+  h->launches += 1;
+  for (int k = 0; k < 1 + p.sylv; ++k) h->launches += launch_init_block(h->op[k], s, p.bulk_f32, p.sweep_grid, h->flags, st);
   int done = 0;        // Lanczos iterations completed (blocks V_1..V_{done+1} exist)
   int checked = 0;     // largest m already checked
   int chunk = std::min(4, p.check_batch);
@@ -303,18 +323,20 @@ int lyap_solve(lyap_handle* h, void* stream) {
     const int upto = std::min(p.maxit, done + chunk);
     cudaEventRecord(h->ev[2], st);
     for (int j = done + 1; j <= upto; ++j)
-      for (int k = 0; k < 1 + p.sylv; ++k) launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, h->flags, st);
+      for (int k = 0; k < 1 + p.sylv; ++k)
+        h->launches += launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, h->flags, st);
     cudaEventRecord(h->ev[3], st);
     done = upto;
+    h->lanczos_done = done;
     while (checked < done) {
       const int lo = checked + 1;
       const int hi = std::min(done, checked + p.check_batch);
-      launch_check_batch(h, lo, hi, st);
+      h->launches += launch_check_batch(h, lo, hi, st);
       checked = hi;
     }
     cudaEventRecord(h->ev[4], st);
     LYAP_CUDA_TRY(cudaGetLastError());
-    LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
     LYAP_CUDA_TRY(cudaStreamSynchronize(st));
     float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, h->ev[2], h->ev[3]);
@@ -322,7 +344,14 @@ int lyap_solve(lyap_handle* h, void* stream) {
     t_lanczos += a;
     t_check += b;
     const int bits = h->flags_host[0];
-    const int rc = status_from_bits(bits);
+    int rc = status_from_bits(bits);
+    if (rc == LYAP_OK && h->flags_host[2] < h->flags_host[1]) {
+      // a check failed before (or without) convergence: that failure is the result
+      int eb = 0;
+      LYAP_CUDA_TRY(cudaMemcpy(&eb, h->chk_err + h->flags_host[2] - 1, sizeof(int), cudaMemcpyDeviceToHost));
+      rc = status_from_bits(eb);
+      if (rc == LYAP_OK) rc = LYAP_ERR_EIGEN;
+    }
     if (rc != LYAP_OK) {
       h->solved = 0;
       return rc;
@@ -364,6 +393,31 @@ int lyap_residual_norm(lyap_handle* h, double* hist_host, int cap, int* m_out) {
     memcpy(hist_host, h->hist_host, sizeof(double) * n);
   }
   return h->converged ? LYAP_OK : LYAP_NOT_CONVERGED;
+}
+
+int lyap_projected_matrix(lyap_handle* h, int op, int m, double* ab, int ldab, double* gamma, double* tau_next) {
+  if (!h || op < 0 || op > h->plan.sylv || m < 1 || m > h->lanczos_done) return LYAP_ERR_ARG;
+  const int s = h->s, SS = s * s, N = s * m;
+  if (ab && ldab < s + 1) return LYAP_ERR_ARG;
+  std::vector<double> rec((size_t)(m + 1) * LOG_NREC * SS);
+  LYAP_CUDA_TRY(cudaMemcpy(rec.data(), h->op[op].log, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost));
+  auto R = [&](int j, int kind) { return rec.data() + ((size_t)j * LOG_NREC + kind) * SS; };
+  if (gamma) memcpy(gamma, R(0, REC_TNEXT), sizeof(double) * SS);
+  if (tau_next) memcpy(tau_next, R(m, REC_TNEXT), sizeof(double) * SS);
+  if (ab) {
+    for (int i = 0; i < N; ++i)
+      for (int d = 0; d <= s; ++d) {
+        const int r = i + d;
+        double v = 0.0;
+        if (r < N) {
+          const int J = r / s, Jc = i / s;
+          if (J == Jc) v = 0.5 * (R(J + 1, REC_TDIAG)[(r % s) * s + i % s] + R(J + 1, REC_TDIAG)[(i % s) * s + r % s]);
+          else if (J == Jc + 1) v = R(Jc + 1, REC_TNEXT)[(r % s) * s + i % s];
+        }
+        ab[d + (size_t)i * ldab] = v;
+      }
+  }
+  return LYAP_OK;
 }
 
 int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int z_mem, int tcap,
@@ -411,7 +465,9 @@ int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, 
 
 int lyap_phase_times(lyap_handle* h, double* out, int cap) {
   if (!h || !out) return LYAP_ERR_ARG;
-  for (int i = 0; i < cap && i < 8; ++i) out[i] = h->times_ms[i];
+  for (int i = 0; i < cap && i < 6; ++i) out[i] = h->times_ms[i];
+  if (cap > 3) out[3] = (double)h->lanczos_done;
+  if (cap > 6) out[6] = (double)h->launches;
   return LYAP_OK;
 }
 

@@ -42,6 +42,7 @@ enum {
   DERR_NOTNEGDEF = 4,
   DERR_TIMEOUT = 8,
   DERR_BOUNDS = 16,
+  DERR_EIGEN = 32,
 };
 
 // One operator (A or B) and its Krylov recurrence state.
@@ -79,7 +80,7 @@ struct Plan {
     size_t slice_ptr, slice_w, sell_col, sell_val, perm, V[3], W, C, log, partials, counter;
     int64_t n, nslices, sell_nnz;
   } op[2];
-  size_t hist, flags, check, check_bytes, factor, factor_bytes, zstage, staging, staging_bytes;
+  size_t hist, flags, chk_err, check, check_bytes, factor, factor_bytes, zstage, staging, staging_bytes;
 };
 
 // per-check scratch (fp64 unless noted), one slot per check in a batch
@@ -104,7 +105,8 @@ struct lyap_handle {
   double tol = 1e-8;
   lyap_options opt;
   double* hist = nullptr;       // device, maxit
-  int* flags = nullptr;         // device: [0] error bits, [1] first converged m (or INT_MAX)
+  int* flags = nullptr;         // device: [0] error bits, [1] first converged m, [2] first m whose check failed
+  int* chk_err = nullptr;       // device, maxit: error bits of the check at each m
   char* check_ws = nullptr;
   char* factor_ws = nullptr;
   char* zstage = nullptr;
@@ -118,6 +120,7 @@ struct lyap_handle {
   cudaStream_t side = nullptr;  // second stream (checks)
   cudaEvent_t ev[8];
   float times_ms[8];
+  int64_t launches = 0;          // kernels launched since lyap_create
 };
 
 // ---- launch helpers implemented in the .cu files --------------------------
@@ -126,12 +129,12 @@ int sell_plan_host(const lyap_csr* A, int sigma, int64_t* nslices, int64_t* sell
 
 // lanczos.cu
 int max_nacc(int s);
-void launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
-void launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
+int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
+int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
 
 // check.cu
-void launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st);
-void launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st);
+int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st);
+int launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st);
 
 // factor.cu
 int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,

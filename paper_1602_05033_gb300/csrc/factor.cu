@@ -404,12 +404,15 @@ int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void*
     const int64_t tot = n * tk;
     if (z_f32) k_zero_cols<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((float*)Z, n, ldz, tk);
     else k_zero_cols<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((double*)Z, n, ldz, tk);
+    h->launches += 1;
   }
   launch_pass2_v1(op, s, bulk, h->plan.sweep_grid, pos(1), ldb, st);
+  h->launches += 1;
   for (int j = 1; j <= m; ++j) {
     if (j < m) {
       const void* vp = j > 1 ? pos(j - 1) : pos(j);
       launch_pass2(op, s, bulk, h->plan.sweep_grid, j, vp, ldb, pos(j), ldb, pos(j + 1), ldb, st);
+      h->launches += 1;
     }
     const bool group_end = (j % kb == 0) || j == m;
     if (group_end && tk > 0) {
@@ -417,6 +420,7 @@ int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void*
       const int j0 = g * kb + 1;
       const int nblk = j - j0 + 1;
       gemm_accum(bulk, z_f32, n, nblk * s, tk, buf[g & 1], ldb, M + (size_t)(j0 - 1) * s * ldm, ldm, Z, ldz, st);
+      h->launches += 1;
     }
   }
   return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
@@ -462,13 +466,14 @@ int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, i
   int* order_d = reinterpret_cast<int*>(after + lyap_align256((int64_t)(sizeof(double) * nmax)));
 
   // 1. eigenvalues lambda and rows a = (Q^T E_1 gamma) of T_m (Alg. 3 steps 1-4)
-  launch_eigen_for_factor(h, 0, m, st);
+  h->launches += launch_eigen_for_factor(h, 0, m, st);
   double *lam, *a, *w;
   check_slot0(h, 0, &lam, &a, &w);
   // 2. pivoted Cholesky of Y~ = -(a_i . a_j)/(lambda_i + lambda_j)
   const double beta2 = h->op[0].beta * h->op[0].beta;
   const double eps_abs = h->opt.trunc_eps * beta2;
   k_pivoted_cholesky<<<1, kPcThreads, 0, st>>>(lam, a, N, s, tmax, 1e-2 * eps_abs, f, dg);
+  h->launches += 1;
   LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
   const int tpc = h->flags_host[2];
@@ -481,9 +486,11 @@ int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, i
   k_shifted_solves<<<(tpc + nthr - 1) / nthr, nthr, 0, st>>>(h->op[0].log, s, m, lam, a, f, tmax, nmax, 0, 0, N,
                                                              h->flags);
   k_apply_lpp<<<(N + 127) / 128, 128, 0, st>>>(f, N, N, tmax);
+  h->launches += 2;
   // 4. K = L^T L and its eigendecomposition (eigenpairs of L L^T)
   k_gram_L<<<dim3(tpc, (tpc + 127) / 128), 128, 0, st>>>(f, N, tmax);
   k_jacobi<<<1, 1024, 0, st>>>(f, tmax);
+  h->launches += 2;
   std::vector<double> ev(tpc);
   LYAP_CUDA_TRY(cudaMemcpyAsync(ev.data(), f.ev, sizeof(double) * tpc, cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -503,7 +510,10 @@ int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, i
   if (tk > tcap) return LYAP_ERR_TCAP;
   if (tk > 0) LYAP_CUDA_TRY(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * tk, cudaMemcpyHostToDevice, st));
   // 5. M = X V(:, kept) = Q Ycheck, then the second pass Z = sum_j V_j E_j^T M
-  if (tk > 0) k_form_M<<<dim3((N + 127) / 128, tk), 128, 0, st>>>(f, N, tmax, order_d, tk, 0, f.M, tmax);
+  if (tk > 0) {
+    k_form_M<<<dim3((N + 127) / 128, tk), 128, 0, st>>>(f, N, tmax, order_d, tk, 0, f.M, tmax);
+    h->launches += 1;
+  }
   int rc = second_pass(h, 0, f.M, tmax, tk, Z1, ldz1, z_dtype == LYAP_F32, st);
   if (rc != LYAP_OK) return rc;
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // keeps the host vectors alive until the copies ran

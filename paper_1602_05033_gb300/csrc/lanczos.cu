@@ -214,10 +214,14 @@ __device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials,
   __syncthreads();
   if (ticket != gridDim.x - 1) return false;
   __threadfence();
-  for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
+  // warp w sums coefficients k = w, w + kWarps, ...; its lanes stride over the CTAs and
+  // combine in a fixed shuffle order, so the result does not depend on timing
+  for (int k = warp; k < NACC; k += kWarps) {
     double t = 0.0;
-    for (unsigned int b = 0; b < gridDim.x; ++b) t += __ldcg(partials + (size_t)b * NACC + k);
-    tot[k] = t;
+    for (unsigned int b = lane; b < gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * NACC + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) tot[k] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
@@ -389,9 +393,10 @@ __global__ void __launch_bounds__(kThreads) k_proj2_gram1(SweepArgs g) {
       rw[REC_BPREV * SS + k] = bp[k];
       rw[REC_BDIAG * SS + k] = bd[k];
     }
-    if (!all_finite<S>(G, SS)) atomicOr(g.flags, DERR_NONFINITE);
+    const bool finite = all_finite<S>(G, SS);
+    if (!finite) atomicOr(g.flags, DERR_NONFINITE);
     if (!chol_upper<S>(G, R1)) {
-      atomicOr(g.flags, DERR_BREAKDOWN);
+      if (finite) atomicOr(g.flags, DERR_BREAKDOWN);
       for (int k = 0; k < SS; ++k) R1[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
     }
     for (int k = 0; k < SS; ++k) rw[REC_R1 * SS + k] = R1[k];
@@ -440,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_gram2(SweepArgs g) {
     for (int a = 0; a < S; ++a)
       for (int b = 0; b < S; ++b) G[a * S + b] = 0.5 * (tot[a * S + b] + tot[b * S + a]);
     if (!chol_upper<S>(G, R2)) {
-      atomicOr(g.flags, DERR_BREAKDOWN);
+      atomicOr(g.flags, all_finite<S>(G, SS) ? DERR_BREAKDOWN : DERR_NONFINITE);
       for (int k = 0; k < SS; ++k) R2[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
     }
     for (int k = 0; k < SS; ++k) R1[k] = rw[REC_R1 * SS + k];
@@ -546,9 +551,10 @@ __global__ void __launch_bounds__(kThreads) k_init_gram(SweepArgs g, int stage) 
     double G[SS], R[SS];
     for (int a = 0; a < S; ++a)
       for (int b = 0; b < S; ++b) G[a * S + b] = 0.5 * (tot[a * S + b] + tot[b * S + a]);
-    if (!all_finite<S>(G, SS)) atomicOr(g.flags, DERR_NONFINITE);
+    const bool finite = all_finite<S>(G, SS);
+    if (!finite) atomicOr(g.flags, DERR_NONFINITE);
     if (!chol_upper<S>(G, R)) {
-      atomicOr(g.flags, DERR_BREAKDOWN);
+      if (finite) atomicOr(g.flags, DERR_BREAKDOWN);
       for (int k = 0; k < SS; ++k) R[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
     }
     if (stage == 1) {
@@ -683,14 +689,16 @@ void pass2_T(OpDev& op, int s, int grid, int j, const void* vp, int64_t ldp, con
 
 int max_nacc(int s) { return 3 * s * s; }
 
-void launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st) {
+int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st) {
   if (bulk_f32) init_T<float>(op, s, grid, d_flags, st);
   else init_T<double>(op, s, grid, d_flags, st);
+  return 3;
 }
 
-void launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st) {
+int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st) {
   if (bulk_f32) step_T<float>(op, s, grid, j, d_flags, st);
   else step_T<double>(op, s, grid, j, d_flags, st);
+  return 4;
 }
 
 // Second pass, step j: writes V_{j+1} from V_{j-1} (vp), V_j (vc).

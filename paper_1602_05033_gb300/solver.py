@@ -41,7 +41,8 @@ class Solver:
         opt.sell_sigma = int(sell_sigma)
         opt.pass2_blocks = int(pass2_blocks)
         opt.check_batch = int(check_batch)
-        opt.zcap = int(zcap)
+        # host output of the factor is staged in the workspace; by default size it for any rank
+        opt.zcap = int(zcap) if zcap else (self.s * int(maxit) if inputs == "host" else 0)
         self.opt = opt
         self._keep = []
         vdt = np.float32 if val_dtype == "f32" else np.float64
@@ -124,6 +125,10 @@ class Solver:
         if self.sylv:
             return Z1, Z2[:, :tk]
         return Z1
+
+    def projected(self, m: int, op: int = 0):
+        """(ab, gamma, tau_next) of T_m (op 0) or J_m (op 1) from the device log."""
+        return L.lyap_projected_matrix(self.h, op, m, self.s)
 
     def phase_times(self):
         return L.lyap_phase_times(self.h)
