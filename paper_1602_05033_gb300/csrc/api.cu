@@ -18,12 +18,19 @@ int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col,
 
 namespace {
 
-int sweep_grid_for(int64_t n) {
-  // fixed per problem size (not per device) so that reductions are reproducible anywhere;
-  // 456 = 3 CTAs of 256 threads on each of 152 SMs
-  int64_t g = (n + 2047) / 2048;
+constexpr int kMaxSweepGrid = 2048;
+
+// one wave of the row sweeps on this device (at least 256 rows per CTA); the reduction
+// order depends on the grid, so results are reproducible run to run on a given GPU model
+int sweep_grid_for(int64_t n, int s, int bulk_f32) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+  int64_t g = (int64_t)sms * sweep_blocks_per_sm(s, bulk_f32);
+  const int64_t byrows = (n + 255) / 256;
+  if (g > byrows) g = byrows;
   if (g < 1) g = 1;
-  if (g > 456) g = 456;
+  if (g > kMaxSweepGrid) g = kMaxSweepGrid;
   return (int)g;
 }
 
@@ -96,11 +103,11 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
     q.W = take(w * (size_t)M->n * s);
     q.C = take(sizeof(double) * (size_t)M->n * s);
     q.log = take(sizeof(double) * (size_t)(o.maxit + 1) * LOG_NREC * s * s);
-    q.partials = take(sizeof(double) * (size_t)1216 * 3 * s * s);
+    q.partials = take(sizeof(double) * (size_t)kMaxSweepGrid * 3 * s * s);
     q.counter = take(256);
     nmaxop = std::max<int64_t>(nmaxop, M->n);
   }
-  p.sweep_grid = sweep_grid_for(nmaxop);
+  p.sweep_grid = 0;  // set at create (needs the device)
   p.hist = take(sizeof(double) * (size_t)o.maxit);
   p.flags = take(256);
   p.chk_err = take(sizeof(int) * (size_t)o.maxit);
@@ -217,6 +224,7 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
   *out = nullptr;
   lyap_handle* h = new (std::nothrow) lyap_handle();
   if (!h) return LYAP_ERR_ARG;
+  p.sweep_grid = sweep_grid_for(std::max(A->n, B ? B->n : (int64_t)0), s, p.bulk_f32);
   h->plan = p;
   h->ws = static_cast<char*>(workspace);
   h->s = s;

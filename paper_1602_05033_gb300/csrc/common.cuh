@@ -129,6 +129,7 @@ int sell_plan_host(const lyap_csr* A, int sigma, int64_t* nslices, int64_t* sell
 
 // lanczos.cu
 int max_nacc(int s);
+int sweep_blocks_per_sm(int s, int bulk_f32);
 int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
 int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
 

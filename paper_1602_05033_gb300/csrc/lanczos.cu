@@ -20,9 +20,17 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace {
 
 constexpr int kThreads = 256;
+// CTAs per SM the sweeps are compiled for: enough warps for HBM latency without spilling
+// the per-thread s x s accumulators (3 for fp32 rows, 2 for fp64)
+template <typename T>
+struct MinBlocks { static constexpr int value = 3; };
+template <>
+struct MinBlocks<double> { static constexpr int value = 2; };
 constexpr int kWarps = kThreads / 32;
 
 template <typename T>
@@ -100,6 +108,11 @@ __device__ __forceinline__ void store_row(double* __restrict__ X, int64_t ld, in
 }
 
 // ---- SELL-C-sigma row product: w = (A V)[row] -----------------------------------
+// Entries are taken kUnroll at a time: all column indices and values first, then all
+// gathers of V rows, then the FMAs, so a row has kUnroll independent gathers in flight
+// instead of waiting one DRAM round trip per nonzero.  The summation order is the
+// entry order of the row in every case (identical bits in both passes).
+constexpr int kUnroll = 8;
 template <typename T, int S>
 __device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lane, const T* __restrict__ Vc,
                                          int64_t ldc, T (&w)[S]) {
@@ -108,14 +121,23 @@ __device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lan
   const int64_t base = op.slice_ptr[slice] + lane;
   const int width = op.slice_w[slice];
   const T* __restrict__ val = static_cast<const T*>(op.sell_val);
-  for (int jj = 0; jj < width; ++jj) {
-    const int64_t e = base + (int64_t)jj * LYAP_SLICE;
-    const int32_t c = __ldg(op.sell_col + e);
-    const T v = __ldg(val + e);
-    T x[S];
-    load_row<S>(Vc, ldc, c, x);
+  for (int j0 = 0; j0 < width; j0 += kUnroll) {
+    int32_t c[kUnroll];
+    T v[kUnroll];
 #pragma unroll
-    for (int a = 0; a < S; ++a) w[a] = fma(v, x[a], w[a]);
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool in = j0 + u < width;
+      const int64_t e = base + (int64_t)(in ? j0 + u : 0) * LYAP_SLICE;
+      c[u] = __ldg(op.sell_col + e);
+      v[u] = in ? __ldg(val + e) : T(0);
+    }
+    T x[kUnroll][S];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) load_row<S>(Vc, ldc, c[u], x[u]);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int a = 0; a < S; ++a) w[a] = fma(v[u], x[u][a], w[a]);
   }
 }
 
@@ -123,9 +145,10 @@ __device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lan
 // co[k][a][b]: k-th s x s coefficient block, converted to the bulk type.
 template <typename T, int S>
 struct Coefs {
-  T ap[S][S], ad[S][S], bp[S][S], bd[S][S];  // MGS coefficients
-  T r1[S][S], r2[S][S];                     // CholQR factors (upper)
-  T r1i[S], r2i[S];                         // reciprocals of their diagonals
+  T ap[S][S], ad[S][S];  // first MGS sweep: alpha_{j-1}, alpha_j
+  T tp[S][S], td[S][S];  // both sweeps combined: tau_{j-1,j}, tau_jj
+  T r1[S][S], tn[S][S];  // first CholQR factor, tau_{j+1,j} = R2 R1 (upper)
+  T r1i[S], tni[S];      // reciprocals of their diagonals
 };
 
 // w1 = W - Vp ap - Vc ad ; w2 = w1 - Vp bp - Vc bd (row vectors times s x s blocks)
@@ -157,34 +180,33 @@ __device__ __forceinline__ void trsm_row(const T (&R)[S][S], const T (&Ri)[S], T
   }
 }
 
-// full row recipe of S4 / the second pass: v = ((w - ...) R1^{-1}) R2^{-1}
+// row recipe of S4 and of the second pass: v = (w - p tau_{j-1,j} - q tau_jj) tau_{j+1,j}^{-1}
+// (both MGS sweeps and both CholQR factors applied at once, as in the recurrence of eq. 2.6)
 template <typename T, int S>
 __device__ __forceinline__ void next_row(const Coefs<T, S>& co, const T (&p)[S], const T (&q)[S], T (&w)[S],
                                          bool has_prev) {
-  mgs_row<T, S>(p, q, co.ap, co.ad, w, has_prev);
-  mgs_row<T, S>(p, q, co.bp, co.bd, w, has_prev);
-  trsm_row<T, S>(co.r1, co.r1i, w);
-  trsm_row<T, S>(co.r2, co.r2i, w);
+  mgs_row<T, S>(p, q, co.tp, co.td, w, has_prev);
+  trsm_row<T, S>(co.tn, co.tni, w);
 }
 
 template <typename T, int S>
 __device__ void load_coefs(Coefs<T, S>& co, const double* __restrict__ rec, int stage) {
-  // stage: how many of the records are valid (1: alpha, 2: +beta,R1, 3: +R2)
+  // stage: records available (1: alpha; 2: + tau_{j-1,j}, tau_jj, R1; 3: + tau_{j+1,j})
   const int SS = S * S;
   for (int k = threadIdx.x; k < SS; k += blockDim.x) {
     const int a = k / S, b = k % S;
     co.ap[a][b] = T(rec[REC_APREV * SS + k]);
     co.ad[a][b] = T(rec[REC_ADIAG * SS + k]);
     if (stage >= 2) {
-      co.bp[a][b] = T(rec[REC_BPREV * SS + k]);
-      co.bd[a][b] = T(rec[REC_BDIAG * SS + k]);
+      co.tp[a][b] = T(rec[REC_TPREV * SS + k]);
+      co.td[a][b] = T(rec[REC_TDIAG * SS + k]);
       co.r1[a][b] = T(rec[REC_R1 * SS + k]);
     }
-    if (stage >= 3) co.r2[a][b] = T(rec[REC_R2 * SS + k]);
+    if (stage >= 3) co.tn[a][b] = T(rec[REC_TNEXT * SS + k]);
   }
   for (int b = threadIdx.x; b < S; b += blockDim.x) {
     if (stage >= 2) co.r1i[b] = T(1.0 / rec[REC_R1 * SS + b * S + b]);
-    if (stage >= 3) co.r2i[b] = T(1.0 / rec[REC_R2 * SS + b * S + b]);
+    if (stage >= 3) co.tni[b] = T(1.0 / rec[REC_TNEXT * SS + b * S + b]);
   }
   __syncthreads();
 }
@@ -277,7 +299,7 @@ struct SweepArgs {
 
 // S1: SpMM + first MGS projections
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_spmm_proj(SweepArgs g) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_spmm_proj(SweepArgs g) {
   using Acc = typename AccT<T>::type;
   constexpr int NACC = 3 * S * S;
   Acc acc[NACC];
@@ -337,10 +359,11 @@ __global__ void __launch_bounds__(kThreads) k_spmm_proj(SweepArgs g) {
 
 // S2: second MGS projections + first Gram
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_proj2_gram1(SweepArgs g) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_proj2_gram1(SweepArgs g) {
   using Acc = typename AccT<T>::type;
   constexpr int SS = S * S;
-  constexpr int NACC = 3 * SS;
+  constexpr int NSYM = S * (S + 1) / 2;  // upper triangle of the Gram block
+  constexpr int NACC = 2 * SS + NSYM;
   __shared__ Coefs<T, S> co;
   const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
   load_coefs<T, S>(co, rec, 1);
@@ -367,8 +390,12 @@ __global__ void __launch_bounds__(kThreads) k_proj2_gram1(SweepArgs g) {
       for (int b = 0; b < S; ++b) {
         acc[a * S + b] = fma((Acc)p[a], (Acc)w[b], acc[a * S + b]);
         acc[SS + a * S + b] = fma((Acc)q[a], (Acc)w[b], acc[SS + a * S + b]);
-        acc[2 * SS + a * S + b] = fma((Acc)w[a], (Acc)w[b], acc[2 * SS + a * S + b]);
       }
+    int e = 2 * SS;
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int b = a; b < S; ++b, ++e) acc[e] = fma((Acc)w[a], (Acc)w[b], acc[e]);
   }
   __shared__ double tot[NACC];
   __shared__ double scratch[kWarps * NACC];
@@ -383,15 +410,18 @@ __global__ void __launch_bounds__(kThreads) k_proj2_gram1(SweepArgs g) {
     matmul<S>(cr, bp, t);
     for (int k = 0; k < SS; ++k) bd[k] = tot[SS + k] - t[k];
     // G1 = w1^T w1 - bp^T bp - bd^T bd: Gram of w2 = w1 - V beta (V orthonormal up to rounding)
-    for (int a = 0; a < S; ++a)
-      for (int b = 0; b < S; ++b) {
-        double v = 0.5 * (tot[2 * SS + a * S + b] + tot[2 * SS + b * S + a]);
+    for (int a = 0, e = 2 * SS; a < S; ++a)
+      for (int b = a; b < S; ++b, ++e) {
+        double v = tot[e];
         for (int k = 0; k < S; ++k) v -= bp[k * S + a] * bp[k * S + b] + bd[k * S + a] * bd[k * S + b];
         G[a * S + b] = v;
+        G[b * S + a] = v;
       }
     for (int k = 0; k < SS; ++k) {
       rw[REC_BPREV * SS + k] = bp[k];
       rw[REC_BDIAG * SS + k] = bd[k];
+      rw[REC_TPREV * SS + k] = rw[REC_APREV * SS + k] + bp[k];
+      rw[REC_TDIAG * SS + k] = rw[REC_ADIAG * SS + k] + bd[k];
     }
     const bool finite = all_finite<S>(G, SS);
     if (!finite) atomicOr(g.flags, DERR_NONFINITE);
@@ -405,7 +435,7 @@ __global__ void __launch_bounds__(kThreads) k_proj2_gram1(SweepArgs g) {
 
 // S3: second Gram (CholQR2's second pass)
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_gram2(SweepArgs g) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_gram2(SweepArgs g) {
   using Acc = typename AccT<T>::type;
   constexpr int SS = S * S;
   constexpr int NACC = SS;
@@ -428,8 +458,7 @@ __global__ void __launch_bounds__(kThreads) k_gram2(SweepArgs g) {
 #pragma unroll
       for (int a = 0; a < S; ++a) p[a] = T(0);
     }
-    mgs_row<T, S>(p, q, co.ap, co.ad, w, hp);
-    mgs_row<T, S>(p, q, co.bp, co.bd, w, hp);
+    mgs_row<T, S>(p, q, co.tp, co.td, w, hp);
     trsm_row<T, S>(co.r1, co.r1i, w);
 #pragma unroll
     for (int a = 0; a < S; ++a)
@@ -453,8 +482,6 @@ __global__ void __launch_bounds__(kThreads) k_gram2(SweepArgs g) {
     for (int k = 0; k < SS; ++k) {
       rw[REC_R2 * SS + k] = R2[k];
       rw[REC_TNEXT * SS + k] = Tn[k];
-      rw[REC_TDIAG * SS + k] = rw[REC_ADIAG * SS + k] + rw[REC_BDIAG * SS + k];
-      rw[REC_TPREV * SS + k] = rw[REC_APREV * SS + k] + rw[REC_BPREV * SS + k];
     }
     if (!all_finite<S>(Tn, SS)) atomicOr(g.flags, DERR_NONFINITE);
   }
@@ -462,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) k_gram2(SweepArgs g) {
 
 // S4: write V_{j+1}
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_write_next(SweepArgs g) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_write_next(SweepArgs g) {
   constexpr int SS = S * S;
   __shared__ Coefs<T, S> co;
   const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
@@ -489,7 +516,7 @@ __global__ void __launch_bounds__(kThreads) k_write_next(SweepArgs g) {
 // Second pass: V_{j+1} = recipe(A V_j, V_{j-1}, V_j) in one sweep (no reductions).
 // Same SpMM and row recipe as pass 1, hence the same bits.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_pass2(SweepArgs g) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_pass2(SweepArgs g) {
   constexpr int SS = S * S;
   __shared__ Coefs<T, S> co;
   const double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
@@ -688,6 +715,27 @@ void pass2_T(OpDev& op, int s, int grid, int j, const void* vp, int64_t ldp, con
 }  // namespace
 
 int max_nacc(int s) { return 3 * s * s; }
+
+// CTAs of the sweep kernels that fit on one SM together (the smallest over the four)
+int sweep_blocks_per_sm(int s, int bulk_f32) {
+  int best = 1 << 30;
+  auto q = [&](const void* f) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kThreads, 0) == cudaSuccess && b > 0) best = std::min(best, b);
+  };
+#define LYAP_OCC(TT, SS_)                                                                    \
+  q((const void*)k_spmm_proj<TT, SS_>); q((const void*)k_proj2_gram1<TT, SS_>);           \
+  q((const void*)k_gram2<TT, SS_>); q((const void*)k_write_next<TT, SS_>)
+  if (bulk_f32) {
+    switch (s) { case 1: LYAP_OCC(float, 1); break; case 2: LYAP_OCC(float, 2); break; case 3: LYAP_OCC(float, 3); break;
+                 case 4: LYAP_OCC(float, 4); break; case 8: LYAP_OCC(float, 8); break; }
+  } else {
+    switch (s) { case 1: LYAP_OCC(double, 1); break; case 2: LYAP_OCC(double, 2); break; case 3: LYAP_OCC(double, 3); break;
+                 case 4: LYAP_OCC(double, 4); break; case 8: LYAP_OCC(double, 8); break; }
+  }
+#undef LYAP_OCC
+  return best == (1 << 30) ? 1 : best;
+}
 
 int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st) {
   if (bulk_f32) init_T<float>(op, s, grid, d_flags, st);
