@@ -158,6 +158,33 @@ int lyap_phase_times(lyap_handle* h, double* out, int cap);
  * frees the workspace afterwards. */
 int lyap_destroy(lyap_handle* h);
 
+/* Allocation-free evaluation of the relative residual ||R_m||_F / beta^2 of Prop. 3.1
+ * for a projected matrix the caller supplies.  It is an addition of this library: the
+ * paper has no counterpart.  It runs the kernels of lyap_solve's convergence check, but
+ * every byte of their scratch sits in one fixed device array compiled into the library,
+ * so the call makes no cudaMalloc, cudaFree or other allocating call.  It is meant for
+ * callers that cannot allocate device memory at the point where they need a residual:
+ * code running inside another framework whose caching allocator already holds the free
+ * device memory (a raw cudaMalloc there fails or fragments that pool), and real-time or
+ * embedded loops whose memory is fixed at set-up and may not change afterwards.
+ *  ab        : device memory, lower band of T_m, ab[d + i*ldab] = T_m[i+d][i] for
+ *              d = 0..s and i < s*m (the layout lyap_projected_matrix returns); ldab >= s+1
+ *  gamma     : device memory, s x s row-major, C = V_1 gamma
+ *  tau_next  : device memory, s x s row-major, tau_{m+1,m}
+ *  beta      : ||C||_F  (> 0)
+ *  rel_out   : device memory, receives the relative residual (a double)
+ *  status_out: device memory, receives LYAP_OK or the error status of the evaluation (an int)
+ *  stream    : cudaStream_t the work is ordered on; the call returns after enqueueing
+ * Limits: 1 <= s <= 4 and s*m <= 256; anything larger returns LYAP_ERR_ARG.  The array
+ * (about 5.6 MiB) is held by every GPU that loads the library until the process exits.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share
+ * the one array and each call clears what must start at zero, so calls whose work
+ * overlaps on the GPU (concurrent streams or threads) race and must be serialised. */
+int lyap_residual_noalloc(int s, int m, const double* ab, int ldab, const double* gamma,
+                          const double* tau_next, double beta, double* rel_out,
+                          int* status_out, void* stream);
+
 const char* lyap_status_string(int status);
 
 #ifdef __cplusplus

@@ -40,6 +40,7 @@ EXPORTED = (
     "lyap_phase_times",
     "lyap_destroy",
     "lyap_status_string",
+    "lyap_residual_noalloc",
 )
 
 
@@ -103,6 +104,7 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_projected_matrix.argtypes = [P, ct.c_int, ct.c_int, P, ct.c_int, P, P]
     lib.lyap_phase_times.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int]
     lib.lyap_destroy.argtypes = [P]
+    lib.lyap_residual_noalloc.argtypes = [ct.c_int, ct.c_int, P, ct.c_int, P, P, ct.c_double, P, P, P]
     lib.lyap_status_string.argtypes = [ct.c_int]
     lib.lyap_status_string.restype = ct.c_char_p
     for name in EXPORTED:
@@ -193,6 +195,16 @@ def lyap_phase_times(h: int):
     out = (ct.c_double * 8)()
     load().lyap_phase_times(ct.c_void_p(h), out, 8)
     return list(out)
+
+
+def lyap_residual_noalloc(s: int, m: int, ab_ptr: int, ldab: int, gamma_ptr: int, tau_ptr: int, beta: float,
+                          rel_ptr: int, status_ptr: int, stream: int) -> None:
+    """Enqueues the allocation-free residual evaluation; all pointers are device memory."""
+    st = load().lyap_residual_noalloc(int(s), int(m), ct.c_void_p(ab_ptr), int(ldab), ct.c_void_p(gamma_ptr),
+                                      ct.c_void_p(tau_ptr), float(beta), ct.c_void_p(rel_ptr), ct.c_void_p(status_ptr),
+                                      ct.c_void_p(stream))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_residual_noalloc")
 
 
 def lyap_destroy(h: int) -> None:

@@ -940,3 +940,126 @@ void check_slot0(lyap_handle* h, int opi, double** lam, double** a, double** w) 
   p += (size_t)s * nmax;
   *w = p;
 }
+
+// ---------------------------------------------------------------------------------
+// Allocation-free residual evaluation (lyap_residual_noalloc in include/lyap.h).
+//
+// The scratch of one check (the slot of the kernels above, a coefficient log in the
+// format they read, the history entry and the error words) lives in a file-scope
+// device array sized for s <= 4 and s*m <= 256.  Host code must not use the array's
+// name as a device address: it is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int kNoAllocMaxS = 4;
+constexpr int kNoAllocMaxN = 256;  // s * m
+constexpr size_t kNoAllocSlot = 8 + 4 * (size_t)kNoAllocMaxN + (size_t)(kNoAllocMaxS + 1) * kNoAllocMaxN +
+                                2 * (size_t)kNoAllocMaxS * kNoAllocMaxN + ((size_t)kNoAllocMaxN + 16) +
+                                (size_t)(2 * kNoAllocMaxS + 2) * kNoAllocMaxN * kNoAllocMaxN;
+constexpr size_t kNoAllocLog = (size_t)(kNoAllocMaxN + 1) * LOG_NREC * kNoAllocMaxS * kNoAllocMaxS;
+constexpr size_t kNoAllocInts = 4 + kNoAllocMaxN;  // flags, per-m error bits
+constexpr size_t kNoAllocDoubles = kNoAllocSlot + kNoAllocLog + kNoAllocMaxN + (kNoAllocInts + 1) / 2;
+
+static_assert(kNoAllocSlot >= 8 + (size_t)kNoAllocMaxN + 3 * (size_t)kNoAllocMaxN +
+                                   (size_t)(kNoAllocMaxS + 1) * kNoAllocMaxN + 2 * (size_t)kNoAllocMaxS * kNoAllocMaxN +
+                                   ((size_t)kNoAllocMaxN + 16) + (size_t)kNoAllocMaxN * kNoAllocMaxN +
+                                   (size_t)(2 * kNoAllocMaxS + 1) * kNoAllocMaxN * kNoAllocMaxN,
+              "scratch slot must hold a check slot of the largest supported size");
+
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// copies the caller's T_m band, gamma, tau_{m+1,m} and beta into the log format the
+// check kernels read; clears the error words
+__global__ void k_noalloc_pack(int s, int m, const double* __restrict__ ab, int ldab, const double* __restrict__ gam,
+                               const double* __restrict__ tau, double beta, double* __restrict__ log, int* ints) {
+  const int SS = s * s;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < (m + 1) * SS; t += gridDim.x * blockDim.x) {
+    const int j = t / SS, k = t % SS, a = k / s, b = k % s;
+    double* rec = log + (size_t)j * LOG_NREC * SS;
+    if (j == 0) {
+      rec[REC_TNEXT * SS + k] = gam[k];
+      if (k == 0) rec[REC_TDIAG * SS] = beta;
+      continue;
+    }
+    // diagonal block j: T_m[(j-1)s + a][(j-1)s + b], band entry of the lower triangle
+    const int r = (j - 1) * s + a, c = (j - 1) * s + b;
+    const int lo = r > c ? c : r, d = r > c ? r - c : c - r;
+    rec[REC_TDIAG * SS + k] = ab[d + (size_t)lo * ldab];
+    // sub-diagonal block below it (tau_{j+1,j}, upper triangular), or the caller's tau for j = m
+    double tn = 0.0;
+    if (j < m) {
+      if (a <= b) tn = ab[(s + a - b) + (size_t)((j - 1) * s + b) * ldab];
+    } else {
+      tn = tau[k];
+    }
+    rec[REC_TNEXT * SS + k] = tn;
+  }
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < (int)kNoAllocInts; t += blockDim.x) ints[t] = (t >= 1 && t < 4) ? INT_MAX : 0;
+}
+
+__device__ int noalloc_status(int bits) {
+  if (bits & DERR_BREAKDOWN) return LYAP_ERR_BREAKDOWN;
+  if (bits & DERR_NONFINITE) return LYAP_ERR_NONFINITE;
+  if (bits & DERR_NOTNEGDEF) return LYAP_ERR_NOT_NEGDEF;
+  if (bits & DERR_EIGEN) return LYAP_ERR_EIGEN;
+  return bits ? LYAP_ERR_EIGEN : LYAP_OK;
+}
+
+__global__ void k_noalloc_out(int m, const double* __restrict__ hist, const int* __restrict__ chk_err, double* rel_out,
+                              int* status_out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *rel_out = hist[m - 1];
+    *status_out = noalloc_status(chk_err[m - 1]);
+  }
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+}  // namespace
+
+extern "C" int lyap_residual_noalloc(int s, int m, const double* ab, int ldab, const double* gamma,
+                                     const double* tau_next, double beta, double* rel_out, int* status_out,
+                                     void* stream) {
+  if (s < 1 || s > kNoAllocMaxS || m < 1 || s * m > kNoAllocMaxN || ldab < s + 1) return LYAP_ERR_ARG;
+  if (!ab || !gamma || !tau_next || !rel_out || !status_out || !(beta > 0.0)) return LYAP_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LYAP_ERR_CUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      // the host-side symbol is not a device address: ask the runtime, with dev current
+      if (cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch) != cudaSuccess) {
+        g_noalloc_addr[dev] = nullptr;
+        return LYAP_ERR_CUDA;
+      }
+    }
+    base = g_noalloc_addr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* slot = static_cast<double*>(base);
+  double* log = slot + kNoAllocSlot;
+  double* hist = log + kNoAllocLog;
+  int* ints = reinterpret_cast<int*>(hist + kNoAllocMaxN);  // [0] error bits, [1..2] first converged / failed m
+  int* chk_err = ints + 4;
+  k_noalloc_pack<<<8, 256, 0, st>>>(s, m, ab, ldab, gamma, tau_next, beta, log, ints);
+  CheckArgs g;
+  g.log = log;
+  g.slots = slot;
+  g.s = s;
+  g.nmax = kNoAllocMaxN;
+  g.m_lo = m;
+  g.nchk = 1;
+  g.every = 1;
+  g.flags = ints;
+  g.chk_err = chk_err;
+  eigen_pipeline(g, s * m, st);
+  k_cauchy_lyap<<<dim3((s * m + 7) / 8, 1), 256, 0, st>>>(g);
+  k_finalize<<<1, 256, 0, st>>>(g, g, 0, hist, -1.0, ints + 1);
+  k_noalloc_out<<<1, 32, 0, st>>>(m, hist, chk_err, rel_out, status_out);
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
+}
