@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=100, help="grid edge (100 -> n = 1e6)")
+    ap.add_argument("--profile-case", choices=["lanczos", "check"], default=None,
+                    help="run a short solve of the workload for a profiler and exit: 'lanczos' runs 6 block "
+                         "Lanczos steps, 'check' 64 steps with their convergence checks (tol 0)")
     return ap.parse_args()
 
 
@@ -196,6 +199,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "lanczos_sweeps_lap3d100_s4.md")
+SWEEP_SOURCES = [os.path.join(ROOT, "paper_1602_05033_gb300", "csrc", f) for f in ("lanczos.cu", "common.cuh")]
+
+
+def sweep_traffic():
+    """DRAM bytes per block Lanczos step from the committed ncu summary, or None when the
+    sweep sources changed since those counters were taken."""
+    import hashlib
+
+    if not os.path.exists(SWEEP_PROFILE):
+        return None
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        h.update(open(f, "rb").read())
+    rec = {}
+    for line in open(SWEEP_PROFILE):
+        if ":" in line and line.split(":")[0].strip() in ("source_sha256", "dram_bytes_per_step"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("source_sha256") != h.hexdigest() or "dram_bytes_per_step" not in rec:
+        return None
+    return int(float(rec["dram_bytes_per_step"]))
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -335,7 +362,7 @@ def ours(args):
                    "parallelism": f"{world} independent replicas", "l2": "flushed before each step (512 MB write)"},
         "roofline": {"kernel": "block Lanczos step: SELL SpMM + 2 block MGS sweeps + CholQR2 (4 launches)",
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": sweep_traffic(),
                      "bytes_per_unit": alg_bytes, "peak_source": peak_src},
         "phases_ms": phase,
         "gpu_launches": launches,
@@ -400,8 +427,27 @@ def e2e_arm(args, P, rp, cl, vl32, s, opt, dev):
             "d2h_bytes_per_step": int(d2h), "steps": len(times)}
 
 
+def profile_case(args):
+    """A short, fixed piece of the workload for ncu captures (small device footprint)."""
+    import torch
+
+    import workloads as wl
+    from paper_1602_05033_gb300 import Solver
+
+    P = wl.config_c2(0, k=args.k)
+    maxit = 6 if args.profile_case == "lanczos" else 64
+    sol = Solver(P.A, P.C1, tol=0.0, maxit=maxit, precision="mixed",
+                 check_batch=8 if args.profile_case == "lanczos" else 32)
+    sol.solve()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "steps": int(sol.phase_times()[3])}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

@@ -148,17 +148,33 @@ __global__ void __launch_bounds__(1024) k_jacobi(FactorWs f, int tmax) {
     if (threadIdx.x == 0 && t == 1) f.ev[0] = K[0];
     return;
   }
+  __shared__ double red_off[1024 / 32], red_tot[1024 / 32];
   for (int sweep = 0; sweep < 40; ++sweep) {
+    // off-diagonal and total Frobenius mass, every thread a strided share, fixed-order sums
+    double off = 0.0, tot = 0.0;
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+      const int r = idx / t, c = idx % t;
+      const double v = K[(size_t)r * tmax + c] * K[(size_t)r * tmax + c];
+      tot += v;
+      if (r != c) off += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red_off[threadIdx.x >> 5] = off;
+      red_tot[threadIdx.x >> 5] = tot;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double off = 0.0, tot = 0.0;
-      for (int r = 0; r < t; ++r)
-        for (int c = 0; c < t; ++c) {
-          const double v = K[(size_t)r * tmax + c] * K[(size_t)r * tmax + c];
-          tot += v;
-          if (r != c) off += v;
-        }
-      off_s = off;
-      tot_s = tot;
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        a += red_off[w];
+        b += red_tot[w];
+      }
+      off_s = a;
+      tot_s = b;
     }
     __syncthreads();
     if (!(off_s > 1e-30 * tot_s)) break;
