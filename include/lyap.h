@@ -4,7 +4,7 @@
  * projection methods for symmetric Sylvester and Lyapunov matrix equations").
  *
  *   Lyapunov : A X + X A + C C^T = 0            (eq. 1.1 with B = A, C1 = C2 = C)
- *   Sylvester: A X + X B + C1 C2^T = 0          (eq. 4.1)
+ *   Sylvester: A X + X B + C1 C2^T = 0          (eq. 5.1)
  *
  * A and B are sparse, symmetric negative definite; C1 (n1 x s) and C2 (n2 x s)
  * are tall.  The solution is returned as low-rank factors: X ~= Z Z^T
@@ -71,7 +71,7 @@ typedef struct {
 
 typedef struct {
   int maxit;             /* iteration cap (default 1000)                                    */
-  int check_every;       /* d: test the residual at every d-th space dimension (Sec. 5);
+  int check_every;       /* d: test the residual at every d-th space dimension (Sec. 6);
                             default 1                                                      */
   double trunc_eps;      /* truncation threshold of the reduced solution, relative to
                             ||C1||_F ||C2||_F (eq. 2.5 with eps = 1e-12 in the paper);

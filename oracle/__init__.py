@@ -11,7 +11,7 @@ Modules
 -------
 lyap       block Lanczos (Alg. 2), cheap residual (Prop. 3.1 / Alg. 3),
            truncated factor (eq. 2.5, Sec. 3.2) and the two-pass device (Sec. 3.3)
-sylvester  two-sided variant for A X + X B + C1 C2^T = 0 (Sec. 4.1, Alg. 4)
+sylvester  two-sided variant for A X + X B + C1 C2^T = 0 (Sec. 5.1, Alg. 4)
 explicit   explicit residual norms used as pins (dense and exact low-rank form)
 """
 from . import lyap, sylvester, explicit  # noqa: F401

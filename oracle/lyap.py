@@ -164,7 +164,7 @@ def solve(A, C, tol=1e-8, maxit=1000, check_every=1, keep_basis=False) -> SolveR
     """Algorithm 1 with the standard block Krylov space, steps 1-7.
 
     The convergence test is applied at every ``check_every``-th space
-    dimension (the paper's d, Sec. 5), and at the first m with relative
+    dimension (the paper's d, Sec. 6), and at the first m with relative
     residual <= tol the iteration stops.
     """
     V1, log = start(C, keep_basis)

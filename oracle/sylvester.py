@@ -1,15 +1,15 @@
-"""FP64 oracle for the Sylvester equation A X + X B + C1 C2^T = 0, A and B large (Sec. 4.1).
+"""FP64 oracle for the Sylvester equation A X + X B + C1 C2^T = 0, A and B large (Sec. 5.1).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Two block Lanczos
 recurrences, (A, C1) giving V_m, T_m, tau and (B, C2) giving U_m, J_m, iota,
 advance together; the check at m uses both band eigendecompositions.
 
-Reading of the paper taken here: eq. (4.4) and Algorithm 4 print the
+Reading of the paper taken here: eq. (5.4) and Algorithm 4 print the
 denominator with the two spectra swapped.  The diagonalised reduced equation
 Lambda Y~ + Y~ Upsilon + S = 0 gives Y~_ij = -S_ij / (lambda_i + upsilon_j), so
 row i of S pairs with (lambda_i I + Upsilon)^{-1} G and column j with
 (upsilon_j I + Lambda)^{-1} F.  The tests pin this against scipy's
-Bartels-Stewart solve of the reduced problem and against eq. (4.5).
+Bartels-Stewart solve of the reduced problem and against eq. (5.5).
 """
 from __future__ import annotations
 
@@ -89,7 +89,7 @@ def solve(A, B, C1, C2, tol=1e-8, maxit=1000, check_every=1, keep_basis=False) -
 
 
 def truncated_factors(logA, logB, m, trunc_eps=1e-12):
-    """Truncated SVD of Y~ (Sec. 4.1): Y~ ~= Y1 Y2^T with ||tail||_F <= eps.
+    """Truncated SVD of Y~ (Sec. 5.1): Y~ ~= Y1 Y2^T with ||tail||_F <= eps.
 
     Returns M1 = Q Y1 and M2 = P Y2 (each s*m x t) and the kept singular values;
     eps = trunc_eps * ||C1||_F ||C2||_F.

@@ -230,10 +230,10 @@ def test_config_c1_explicit_residual():
 
 
 def test_paper_example_51_iteration_count():
-    """Loose pin to the paper's printed iteration count (Example 5.1, s = 1)."""
-    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_ex51_iterations.json")))
+    """Loose pin to the paper's printed iteration count (Example 6.1, s = 1)."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_ex61_iterations.json")))
     case = gold["cases"]["s1"]
-    A = wl.paper_ex51_operator(gold["grid"])
+    A = wl.paper_ex61_operator(gold["grid"])
     C = wl.paper_rand_rhs(A.shape[0], 1, seed=0)
     res = lyap.solve(A, C, tol=gold["tol"], maxit=2 * case["iterations"])
     assert res.converged

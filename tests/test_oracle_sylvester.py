@@ -1,4 +1,4 @@
-"""Pins for the FP64 Sylvester oracle (Sec. 4.1, Alg. 4, eq. 4.5)."""
+"""Pins for the FP64 Sylvester oracle (Sec. 5.1, Alg. 4, eq. 5.5)."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -33,7 +33,7 @@ def _reduced_bs(res, m):
 
 
 def test_cheap_equals_reduced_bartels_stewart(sylv_problem):
-    """eq. (4.5) with Y from scipy's Bartels-Stewart Sylvester solver."""
+    """eq. (5.5) with Y from scipy's Bartels-Stewart Sylvester solver."""
     *_, res = sylv_problem
     beta2 = res.logA.beta * res.logB.beta
     for m in range(1, res.m + 1):
@@ -55,7 +55,7 @@ def test_cheap_equals_explicit_residual(sylv_problem):
 
 
 def test_printed_pairing_is_wrong_when_spectra_differ(sylv_problem):
-    """The denominators printed in eq. (4.4)/Alg. 4 (spectra swapped) disagree with eq. (4.5)."""
+    """The denominators printed in eq. (5.4)/Alg. 4 (spectra swapped) disagree with eq. (5.5)."""
     *_, res = sylv_problem
     m, s = 6, res.logA.s
     lam, Q = lyap.eig_T(res.logA, m)
@@ -73,7 +73,7 @@ def test_printed_pairing_is_wrong_when_spectra_differ(sylv_problem):
 
 
 def test_symmetric_case_reduces_to_lyapunov():
-    """B = A, C2 = C1: eq. (4.5) becomes 2||Y E_m tau^T||^2 and the histories coincide (P7)."""
+    """B = A, C2 = C1: eq. (5.5) becomes 2||Y E_m tau^T||^2 and the histories coincide (P7)."""
     A = wl.laplacian_2d(9)
     C = wl.rhs(81, 2, 6)
     ly = lyap.solve(A, C, tol=0.0, maxit=15)
@@ -84,7 +84,7 @@ def test_symmetric_case_reduces_to_lyapunov():
 def test_factors_solve_full_equation():
     """Z1 Z2^T against Bartels-Stewart on the full (small) equation."""
     A = wl.laplacian_2d(10)
-    B = wl.paper_ex54_operator_B(8)
+    B = wl.paper_ex64_operator_B(8)
     C1 = wl.rhs(100, 2, 1)
     C2 = wl.rhs(64, 2, 2)
     res = sylvester.solve(A, B, C1, C2, tol=1e-11, maxit=200)

@@ -7,7 +7,7 @@ both consume identical inputs without sharing any of the method.
 
 Discretisation conventions (zero Dirichlet boundary, lexicographic ordering with
 x fastest, mesh width h = 1/(k+1), A = -(1/h^2) * SPD stencil matrix) follow the
-finite-difference operators of the paper's experiments (Section 5).
+finite-difference operators of the paper's experiments (Section 6).
 """
 from __future__ import annotations
 
@@ -23,8 +23,8 @@ __all__ = [
     "var_coeff_diffusion",
     "gaussian_field",
     "fd_operator",
-    "paper_ex51_operator",
-    "paper_ex54_operator_B",
+    "paper_ex61_operator",
+    "paper_ex64_operator_B",
     "paper_rand_rhs",
     "rhs",
     "random_snd_dense",
@@ -190,13 +190,13 @@ def fd_operator(k: int, ax, by) -> sp.csr_matrix:
     return _csr(A)
 
 
-def paper_ex51_operator(k: int = 148) -> sp.csr_matrix:
-    """(e^{-xy} u_x)_x + (e^{xy} u_y)_y (Section 5, Examples 5.1 and 5.4; n = 21904 / 16384)."""
+def paper_ex61_operator(k: int = 148) -> sp.csr_matrix:
+    """(e^{-xy} u_x)_x + (e^{xy} u_y)_y (Section 6, Examples 6.1 and 6.4; n = 21904 / 16384)."""
     return fd_operator(k, lambda x, y: np.exp(-x * y), lambda x, y: np.exp(x * y))
 
 
-def paper_ex54_operator_B(k: int = 128) -> sp.csr_matrix:
-    """(sin(xy) u_x)_x + (cos(xy) u_y)_y (Section 5, Example 5.4; n = 16384)."""
+def paper_ex64_operator_B(k: int = 128) -> sp.csr_matrix:
+    """(sin(xy) u_x)_x + (cos(xy) u_y)_y (Section 6, Example 6.4; n = 16384)."""
     return fd_operator(k, lambda x, y: np.sin(x * y), lambda x, y: np.cos(x * y))
 
 
