@@ -229,7 +229,7 @@ def test_config_c1_explicit_residual():
     assert explicit.lyap_dense(P.A, Z, P.C1) == pytest.approx(rel * res.log.beta**2, rel=1e-8)
 
 
-def test_paper_example_51_iteration_count():
+def test_paper_example_61_iteration_count():
     """Loose pin to the paper's printed iteration count (Example 6.1, s = 1)."""
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_ex61_iterations.json")))
     case = gold["cases"]["s1"]
