@@ -43,9 +43,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=100, help="grid edge (100 -> n = 1e6)")
-    ap.add_argument("--profile-case", choices=["lanczos", "check"], default=None,
+    ap.add_argument("--workload", choices=["lyap", "sylv"], default="lyap",
+                    help="lyap: the n = 1e6 Lyapunov workload (the bench line); sylv: the Sylvester workload "
+                         "(A = -(3D var.-coeff. diffusion 80^3, fp32), B = -(2D Laplacian 500^2), s = 2)")
+    ap.add_argument("--no-f64-path", action="store_true", help="skip the plain fp64 comparison solve")
+    ap.add_argument("--profile-case", choices=["lanczos", "check", "sylv-check"], default=None,
                     help="run a short solve of the workload for a profiler and exit: 'lanczos' runs 6 block "
-                         "Lanczos steps, 'check' 64 steps with their convergence checks (tol 0)")
+                         "Lanczos steps, 'check' 64 steps with their convergence checks (tol 0), 'sylv-check' "
+                         "800 steps of the Sylvester workload with their checks (tol 0)")
     return ap.parse_args()
 
 
@@ -231,6 +236,129 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def device_csr(A, dev, L):
+    """CSR arrays on the device with fp32 values (the operators' values are exact in fp32)."""
+    import torch
+
+    from paper_1602_05033_gb300 import csr_arrays
+
+    rp, cl, vl = csr_arrays(A)
+    vl32 = vl.astype(np.float32)
+    assert np.array_equal(vl32.astype(np.float64), vl), "operator values must be exact in fp32"
+    keep = [torch.from_numpy(x).to(dev) for x in (rp, cl, vl32)]
+    csr = L.lyap_csr()
+    csr.n, csr.nnz = A.shape[0], cl.shape[0]
+    csr.rowptr, csr.col, csr.val = (t.data_ptr() for t in keep)
+    csr.val_dtype, csr.mem = L.LYAP_F32, L.LYAP_MEM_DEVICE
+    return csr, keep
+
+
+def make_step(P, dev, precision, tcap, maxit):
+    """create + solve + factor of problem P through the C ABI, all inputs resident on the device."""
+    import torch
+
+    from paper_1602_05033_gb300 import _lib as L
+
+    sylv = P.B is not None
+    s = P.C1.shape[1]
+    csrA, kA = device_csr(P.A, dev, L)
+    csrB, kB = device_csr(P.B, dev, L) if sylv else (None, [])
+    d_C1 = torch.from_numpy(P.C1).to(dev)
+    d_C2 = torch.from_numpy(P.C2).to(dev) if sylv else None
+    opt = L.lyap_default_options()
+    opt.maxit = maxit
+    opt.precision = precision
+    zdt, tdt = (L.LYAP_F32, torch.float32) if precision == L.LYAP_PREC_MIXED else (L.LYAP_F64, torch.float64)
+    ws_bytes = L.lyap_workspace_size(csrA, csrB, s, opt)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    Z1 = torch.empty((P.A.shape[0], tcap), dtype=tdt, device=dev)
+    Z2 = torch.empty((P.B.shape[0], tcap), dtype=tdt, device=dev) if sylv else None
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    keep = (kA, kB, d_C1, d_C2, ws)
+
+    def step():
+        _ = keep
+        h = L.lyap_create(csrA, csrB, d_C1.data_ptr(), d_C2.data_ptr() if sylv else None, L.LYAP_MEM_DEVICE, s,
+                          P.tol, opt, ws.data_ptr(), ws_bytes, stream)
+        try:
+            st = L.lyap_solve(h, stream)
+            t = L.lyap_factor(h, Z1.data_ptr(), tcap, Z2.data_ptr() if sylv else None, tcap, zdt,
+                              L.LYAP_MEM_DEVICE, tcap, stream)
+            hist, m, _ = L.lyap_residual_norm(h, opt.maxit)
+            ph = L.lyap_phase_times(h)
+        finally:
+            L.lyap_destroy(h)
+        return st, t, m, hist, ph
+
+    return step, opt, (csrA, csrB)
+
+
+def timed(step, steps, warmup, flush, barrier=lambda: None):
+    import torch
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    times, phases, last = [], [], None
+    for _ in range(steps):
+        flush.zero_()  # L2 flush (512 MB write) outside the timed interval
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        last = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phases.append(last[4])
+    return times, phases, last
+
+
+def lanczos_rate(phases, alg_bytes):
+    lanczos_ms = float(np.mean([p[5] for p in phases]))
+    steps_run = float(np.mean([p[3] for p in phases]))
+    return alg_bytes * steps_run / (lanczos_ms * 1e-3) / 1e9
+
+
+def sylv_line(args):
+    """One JSON line for the Sylvester workload (a measured row, not the bench headline)."""
+    import torch
+
+    import workloads as wl
+    from paper_1602_05033_gb300 import _lib as L
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P = wl.config_c3(0)
+    step, opt, (ca, cb) = make_step(P, dev, L.LYAP_PREC_MIXED, 512, P.maxit)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    times, phases, last = timed(step, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    st, t, m, hist, ph = last
+    s = P.C1.shape[1]
+    alg = (ca.nnz + cb.nnz) * 8 + 5 * (ca.n + cb.n) * s * 4
+    ach = lanczos_rate(phases, alg)
+    peak, src = measured_peaks()
+    phase = {k: round(float(np.mean([p[i] for p in phases])), 3) for i, k in
+             enumerate(["create_ms", "solve_ms", "factor_ms", "lanczos_steps", "check_ms", "lanczos_ms"])}
+    print(json.dumps({
+        "metric": METRIC, "value": float(np.mean(times)) / 1000.0, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": False, "dtype": "f32 bulk / f64 reductions and reduced problem",
+        "data": "synthetic",
+        "config": {"workload": "Sylvester, A = -(3D var.-coeff. diffusion 80^3, log-normal sigma 1, fp32 CSR), "
+                               "B = -(2D Laplacian 500^2), s = 2, C1/C2 iid N(0,1), tol 1e-8, maxit 2000, mixed",
+                   "n1": ca.n, "n2": cb.n, "nnz1": ca.nnz, "nnz2": cb.nnz},
+        "status": int(st), "result": {"m": int(m), "t": int(t), "rel_residual": float(hist[m - 1])},
+        "roofline": {"kernel": "block Lanczos step of both operators", "bound": "hbm", "achieved": round(ach, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "bytes_per_unit": alg,
+                     "peak_source": src},
+        "phases_ms": phase, "gpu_launches": int(np.mean([p[6] for p in phases])), "clocks": clk}))
+    return 0
+
+
 def ours(args):
     import torch
 
@@ -339,6 +467,22 @@ def ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_arm(args, P, rp, cl, vl32, s, opt, dev)
+    f64 = None
+    if not args.no_f64_path:
+        # the same workload on the plain fp64 path (fp64 basis, SpMM and factor): the reference
+        # point of the mixed-precision form
+        del ws, Z
+        torch.cuda.empty_cache()
+        step64, opt64, _ = make_step(P, dev, L.LYAP_PREC_F64, tcap, 400)
+        t64, ph64, last64 = timed(step64, 2, 1, flush, barrier)
+        alg64 = nnz * 12 + 5 * n * s * 8
+        a64 = lanczos_rate(ph64, alg64)
+        f64 = {"value": float(np.mean(t64)) / 1000.0, "unit": UNIT, "m": int(last64[2]), "t": int(last64[1]),
+               "lanczos_GBps": round(a64, 1), "lanczos_frac": round(a64 / measured_peaks()[0], 4),
+               "lanczos_ms": round(float(np.mean([p[5] for p in ph64])), 3),
+               "check_ms": round(float(np.mean([p[4] for p in ph64])), 3),
+               "factor_ms": round(float(np.mean([p[2] for p in ph64])), 3),
+               "speedup_of_mixed": round(float(np.mean(t64)) / ms_per_step, 3)}
     parity = None
     if golden is not None:
         g = np.array(golden["history"])
@@ -374,6 +518,8 @@ def ours(args):
         line["cpu_baseline"] = cpu
     if e2e is not None:
         line["e2e"] = e2e
+    if f64 is not None:
+        line["plain_f64_path"] = f64
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -434,6 +580,14 @@ def profile_case(args):
     import workloads as wl
     from paper_1602_05033_gb300 import Solver
 
+    if args.profile_case == "sylv-check":
+        P = wl.config_c3(0)
+        sol = Solver(P.A, P.C1, B=P.B, C2=P.C2, tol=0.0, maxit=800, precision="mixed", val_dtype="f32")
+        sol.solve()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "steps": int(sol.phase_times()[3]),
+                          "phases": sol.phase_times()}))
+        return 0
     P = wl.config_c2(0, k=args.k)
     maxit = 6 if args.profile_case == "lanczos" else 64
     sol = Solver(P.A, P.C1, tol=0.0, maxit=maxit, precision="mixed",
@@ -448,6 +602,8 @@ def main():
     args = parse()
     if args.profile_case:
         return profile_case(args)
+    if args.workload == "sylv":
+        return sylv_line(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

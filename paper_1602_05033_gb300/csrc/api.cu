@@ -74,6 +74,7 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
   p.bulk_f32 = o.precision == LYAP_PREC_MIXED;
   p.maxit = o.maxit;
   p.check_batch = o.check_batch;
+  p.check_batch_req = o.check_batch;
   p.nmax = s * o.maxit;
   p.pass2_blocks = o.pass2_blocks;
   p.zcap = o.zcap;
@@ -323,7 +324,7 @@ int lyap_solve(lyap_handle* h, void* stream) {
   for (int k = 0; k < 1 + p.sylv; ++k) h->launches += launch_init_block(h->op[k], s, p.bulk_f32, p.sweep_grid, h->flags, st);
   int done = 0;        // Lanczos iterations completed (blocks V_1..V_{done+1} exist)
   int checked = 0;     // largest m already checked
-  int chunk = std::min(4, p.check_batch);
+  int chunk = std::min(4, p.check_batch_req);
   int result = LYAP_NOT_CONVERGED;
   int m_final = p.maxit;
   float t_lanczos = 0.f, t_check = 0.f;
@@ -337,8 +338,11 @@ int lyap_solve(lyap_handle* h, void* stream) {
     done = upto;
     h->lanczos_done = done;
     while (checked < done) {
+      // as many checks as fit in the check area with slots sized by the batch's largest m
       const int lo = checked + 1;
-      const int hi = std::min(done, checked + p.check_batch);
+      int hi = std::min(done, checked + p.check_batch_req);
+      while (hi > lo && (size_t)(1 + p.sylv) * (hi - lo + 1) * check_slot_bytes(s, batch_nmax(s, hi)) > p.check_bytes)
+        --hi;
       h->launches += launch_check_batch(h, lo, hi, st);
       checked = hi;
     }
@@ -370,7 +374,7 @@ int lyap_solve(lyap_handle* h, void* stream) {
       break;
     }
     if (done >= p.maxit) break;
-    chunk = std::min(2 * chunk, p.check_batch);
+    chunk = std::min(2 * chunk, p.check_batch_req);
   }
   h->m = m_final;
   h->converged = result == LYAP_OK;

@@ -36,13 +36,21 @@ constexpr int kBandThreads = 512;
 constexpr int kGroup = 8;    // lanes per concurrent Givens rotation
 constexpr int kDelta = 4;    // stage lag between consecutive sweeps (non-overlapping windows for b >= 2)
 constexpr int kMaxCluster = 16;
+// Members of a cluster of fp32 estimates larger than this (a spectrum far wider than its
+// smallest gaps, or near-duplicate Ritz values) get fp64 estimates by bisection with Sturm
+// counts on the fp64 band, and are then grouped at the fp64 tolerance.
+#ifndef LYAP_REFINE_AT
+#define LYAP_REFINE_AT 8
+#endif
+constexpr int kRefineAt = LYAP_REFINE_AT;
 constexpr int kMaxIters = 12; // inverse iterations at the estimate, then Rayleigh-quotient shifts, until converged
 constexpr int kMaxRounds = 4;  // cluster rounds (Rayleigh-Ritz between them)
 constexpr double kSettle = 1e-12;  // |change of the Rayleigh quotient| / ||T|| after which one more step is run
 constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||T||
 
 struct Slot {
-  double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] cluster tolerance
+  double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] fp32 cluster
+                 // tolerance, [6] fp64 cluster tolerance
   float* d32;    // nmax
   float* e32;    // nmax
   double* est;   // nmax   fp32 eigenvalue estimates (unscaled)
@@ -54,11 +62,14 @@ struct Slot {
   int* clist;    // [0] number of clusters, then (first index, size) pairs
   double* X;     // nmax x nmax, [k][i]: component k of eigenvector i
   double* U;     // nmax x (2s+1) x nmax, [k][e][i]: row k of the LU factor of thread i
+  double* etol;  // nmax   cluster tolerance of each estimate (fp32 one, or fp64 one once refined)
+  double* Xc;    // nmax x nmax, [i][k]: eigenvector i of a cluster member, contiguous
 };
 
 __host__ __device__ inline size_t slot_doubles(int s, int nmax) {
   return 8 + (size_t)nmax /* d32+e32 */ + 3 * (size_t)nmax + (size_t)(s + 1) * nmax + 2 * (size_t)s * nmax +
-         ((size_t)nmax + 16) /* cluster list */ + (size_t)nmax * nmax + (size_t)(2 * s + 1) * nmax * nmax;
+         ((size_t)nmax + 16) /* cluster list */ + (size_t)nmax * nmax + (size_t)(2 * s + 1) * nmax * nmax +
+         (size_t)nmax /* etol */ + (size_t)nmax * nmax /* Xc */;
 }
 
 __device__ inline Slot get_slot(double* base, int s, int nmax, int idx) {
@@ -76,7 +87,9 @@ __device__ inline Slot get_slot(double* base, int s, int nmax, int idx) {
   sl.w = p; p += (size_t)s * nmax;
   sl.clist = reinterpret_cast<int*>(p); p += (size_t)nmax + 16;
   sl.X = p; p += (size_t)nmax * nmax;
-  sl.U = p;
+  sl.U = p; p += (size_t)(2 * s + 1) * nmax * nmax;
+  sl.etol = p; p += nmax;
+  sl.Xc = p;
   return sl;
 }
 
@@ -118,38 +131,15 @@ __device__ __forceinline__ double tband(const double* __restrict__ Tb, int N, in
 }
 
 // lower band (with one extra diagonal for the bulge) in shared memory
-__device__ inline float& TB(float* tb, int N, int i, int c) { return tb[(size_t)(i - c) * N + c]; }
+template <typename R>
+__device__ inline R& TB(R* tb, int N, int i, int c) { return tb[(size_t)(i - c) * N + c]; }
 
-// 1. fp32 tridiagonalisation of T_m / scale (estimates only)
-__global__ void __launch_bounds__(kBandThreads) k_band32(CheckArgs g) {
-  extern __shared__ float smemf[];
-  __shared__ float red[kBandThreads / 32];
-  const int c_idx = blockIdx.x;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
-  const int s = g.s, b = s, N = s * m;
-  Slot sl = get_slot(g.slots, s, g.nmax, c_idx);
-  float* tb = smemf;  // (b + 2) x N
-  // scale = max |T_ij| over the band
-  float mx = 0.f;
-  for (int t = threadIdx.x; t < (b + 1) * N; t += blockDim.x) {
-    const int dd = t / N, c = t % N;
-    if (c + dd < N) mx = fmaxf(mx, (float)fabs(tval(g.log, s, c + dd, c)));
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  float scale = 0.f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) scale = fmaxf(scale, red[w]);
-  if (!(scale > 0.f)) scale = 1.f;
-  const double inv = 1.0 / (double)scale;
-  for (int t = threadIdx.x; t < (b + 2) * N; t += blockDim.x) {
-    const int dd = t / N, c = t % N;
-    const double v = (dd <= b && c + dd < N) ? tval(g.log, s, c + dd, c) : 0.0;
-    tb[t] = (float)(v * inv);
-    if (dd <= b) sl.Tb[t] = v;
-  }
-  __syncthreads();
+// Pipelined Givens reduction of the symmetric band (half-bandwidth b, lower band plus one bulge
+// diagonal in shared memory) to tridiagonal form: sweep k annihilates one sub-diagonal entry and
+// chases the bulge down in steps of b rows; consecutive sweeps run kDelta stages apart so their
+// windows never overlap, and kGroup lanes apply each rotation.
+template <typename R>
+__device__ void band_sweeps(R* tb, int N, int b) {
   if (b >= 2 && N >= 3) {
     const int lane = threadIdx.x & 31;
     const int glane = lane & (kGroup - 1);
@@ -183,25 +173,25 @@ __global__ void __launch_bounds__(kBandThreads) k_band32(CheckArgs g) {
           }
         }
         const int q = p + 1;
-        float cs = 1.f, sn = 0.f;
+        R cs = R(1), sn = R(0);
         if (valid && glane == 0) {
-          const float x = TB(tb, N, p, kc);
-          const float y = TB(tb, N, q, kc);
-          const float r2 = x * x + y * y;
-          if (r2 > 0.f) {
+          const R x = TB(tb, N, p, kc);
+          const R y = TB(tb, N, q, kc);
+          const R r2 = x * x + y * y;
+          if (r2 > R(0)) {
             // correctly rounded sqrt and divisions: the rotation stays orthogonal to
             // ~1 ulp, which the estimates' accuracy depends on
-            const float r = sqrtf(r2);
+            const R r = sqrt(r2);
             cs = x / r;
             sn = y / r;
             TB(tb, N, p, kc) = r;
-            TB(tb, N, q, kc) = 0.f;
+            TB(tb, N, q, kc) = R(0);
           }
         }
         const int src = lane & ~(kGroup - 1);
         cs = __shfl_sync(0xffffffffu, cs, src);
         sn = __shfl_sync(0xffffffffu, sn, src);
-        if (valid && sn != 0.f) {
+        if (valid && sn != R(0)) {
           // items: columns kc+1..p-1, the 2x2 block, rows q+1..min(N-1, p+b+1)
           const int ncols = p - kc - 1;
           const int rlast = min(N - 1, p + b + 1);
@@ -210,26 +200,26 @@ __global__ void __launch_bounds__(kBandThreads) k_band32(CheckArgs g) {
           for (int it = glane; it < nitems; it += kGroup) {
             if (it < ncols) {
               const int j = kc + 1 + it;
-              float& u = TB(tb, N, p, j);
-              float& v = TB(tb, N, q, j);
-              const float uu = u, vv = v;
+              R& u = TB(tb, N, p, j);
+              R& v = TB(tb, N, q, j);
+              const R uu = u, vv = v;
               u = cs * uu + sn * vv;
               v = -sn * uu + cs * vv;
             } else if (it == ncols) {
-              float& app = TB(tb, N, p, p);
-              float& aqp = TB(tb, N, q, p);
-              float& aqq = TB(tb, N, q, q);
-              const float A = app, B = aqp, D = aqq;
-              const float r0 = cs * A + sn * B, r1 = cs * B + sn * D;
-              const float s0 = -sn * A + cs * B, s1 = -sn * B + cs * D;
+              R& app = TB(tb, N, p, p);
+              R& aqp = TB(tb, N, q, p);
+              R& aqq = TB(tb, N, q, q);
+              const R A = app, B = aqp, D = aqq;
+              const R r0 = cs * A + sn * B, r1 = cs * B + sn * D;
+              const R s0 = -sn * A + cs * B, s1 = -sn * B + cs * D;
               app = cs * r0 + sn * r1;
               aqp = cs * s0 + sn * s1;
               aqq = -sn * s0 + cs * s1;
             } else {
               const int i = q + 1 + (it - ncols - 1);
-              float& u = TB(tb, N, i, p);
-              float& v = TB(tb, N, i, q);
-              const float uu = u, vv = v;
+              R& u = TB(tb, N, i, p);
+              R& v = TB(tb, N, i, q);
+              const R uu = u, vv = v;
               u = cs * uu + sn * vv;
               v = -sn * uu + cs * vv;
             }
@@ -240,6 +230,39 @@ __global__ void __launch_bounds__(kBandThreads) k_band32(CheckArgs g) {
       __syncthreads();
     }
   }
+}
+
+// 1. fp32 tridiagonalisation of T_m / scale (estimates only)
+__global__ void __launch_bounds__(kBandThreads) k_band32(CheckArgs g) {
+  extern __shared__ float smemf[];
+  __shared__ float red[kBandThreads / 32];
+  const int c_idx = blockIdx.x;
+  const int m = g.m_lo + c_idx;
+  if (!checked(g, m)) return;
+  const int s = g.s, b = s, N = s * m;
+  Slot sl = get_slot(g.slots, s, g.nmax, c_idx);
+  float* tb = smemf;  // (b + 2) x N
+  // scale = max |T_ij| over the band
+  float mx = 0.f;
+  for (int t = threadIdx.x; t < (b + 1) * N; t += blockDim.x) {
+    const int dd = t / N, c = t % N;
+    if (c + dd < N) mx = fmaxf(mx, (float)fabs(tval(g.log, s, c + dd, c)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float scale = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) scale = fmaxf(scale, red[w]);
+  if (!(scale > 0.f)) scale = 1.f;
+  const double inv = 1.0 / (double)scale;
+  for (int t = threadIdx.x; t < (b + 2) * N; t += blockDim.x) {
+    const int dd = t / N, c = t % N;
+    const double v = (dd <= b && c + dd < N) ? tval(g.log, s, c + dd, c) : 0.0;
+    tb[t] = (float)(v * inv);
+    if (dd <= b) sl.Tb[t] = v;
+  }
+  __syncthreads();
+  band_sweeps<float>(tb, N, b);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     sl.d32[i] = TB(tb, N, i, i);
     sl.e32[i] = (i + 1 < N) ? TB(tb, N, i + 1, i) : 0.f;
@@ -295,6 +318,102 @@ __global__ void k_bisect32(CheckArgs g) {
   sl.est[i] = 0.5 * ((double)lo + (double)hi) * sl.hdr[3];
 }
 
+// 2b. per-estimate cluster tolerance: members of fp32 clusters larger than kRefineAt get the
+// fp64 tolerance 8 sqrt(N) eps64 ||T|| (and are refined by 2c), all others the fp32 one
+__global__ void k_mark_refine(CheckArgs g) {
+  const int c_idx = blockIdx.x;
+  const int m = g.m_lo + c_idx;
+  if (!checked(g, m)) return;
+  const int N = g.s * m;
+  Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
+  const double tol32 = sl.hdr[4];
+  const double span = fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
+  const double tol64 = 8.0 * sqrt((double)N) * DBL_EPSILON * sl.hdr[3] * span;
+  if (threadIdx.x == 0) sl.hdr[6] = tol64;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    if (i > 0 && sl.est[i] - sl.est[i - 1] <= tol32) continue;
+    int c = 1;
+    while (i + c < N && sl.est[i + c] - sl.est[i + c - 1] <= tol32) ++c;
+    const double t = c > kRefineAt ? tol64 : tol32;
+    for (int v = 0; v < c; ++v) sl.etol[i + v] = t;
+  }
+}
+
+// Number of eigenvalues of T_m below x: inertia of the unpivoted LDL^T factorisation of
+// T_m - x I on the fp64 band (Sylvester's law of inertia), a tiny pivot replaced by -pivmin.
+// The last S rows of L and D stay in registers: w_r = (L D)[k][k-r], L[k][k-r] = w_r / d_{k-r},
+// d_k = T_kk - x - sum_r L[k][k-r] w_r.
+template <int S>
+__device__ int band_sturm(const double* __restrict__ Tb, int N, double x, double pivmin) {
+  double dinv[S], L[S][S];  // row r (= k-1-r) : 1/d and its sub-diagonal entries L[row][row-1-t]
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    dinv[r] = 0.0;
+#pragma unroll
+    for (int t = 0; t < S; ++t) L[r][t] = 0.0;
+  }
+  int cnt = 0;
+  for (int k = 0; k < N; ++k) {
+    double w[S], nl[S];
+    // columns k-S .. k-1 (r = S-1 .. 0 means column k-1-r)
+#pragma unroll
+    for (int r = S - 1; r >= 0; --r) {
+      const int j = k - 1 - r;
+      double v = j >= 0 ? __ldg(Tb + (size_t)(r + 1) * N + j) : 0.0;
+#pragma unroll
+      for (int q = S - 1; q > r; --q) v = fma(-w[q], L[r][q - r - 1], v);  // L[j][k-1-q]
+      w[r] = v;
+      nl[r] = v * dinv[r];
+    }
+    double dk = __ldg(Tb + k) - x;
+#pragma unroll
+    for (int r = 0; r < S; ++r) dk = fma(-nl[r], w[r], dk);
+    if (fabs(dk) <= pivmin) dk = -pivmin;
+    cnt += dk < 0.0;
+    // shift the window: the new row becomes row 0
+#pragma unroll
+    for (int r = S - 1; r > 0; --r) {
+      dinv[r] = dinv[r - 1];
+#pragma unroll
+      for (int t = 0; t < S; ++t) L[r][t] = L[r - 1][t];
+    }
+    dinv[0] = 1.0 / dk;
+#pragma unroll
+    for (int t = 0; t < S; ++t) L[0][t] = nl[t];
+  }
+  return cnt;
+}
+
+// 2c. fp64 bisection of the marked estimates, one thread per eigenvalue index, started from the
+// fp32 estimate +- the fp32 cluster tolerance (widened to the Gershgorin interval if the counts
+// show the eigenvalue outside it), stopped at 2 eps64 ||T||
+template <int S>
+__global__ void k_refine64(CheckArgs g) {
+  const int c_idx = blockIdx.y;
+  const int m = g.m_lo + c_idx;
+  if (!checked(g, m)) return;
+  const int N = S * m;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
+  const double tol32 = sl.hdr[4];
+  if (!(sl.etol[i] < tol32)) return;
+  const double sc = sl.hdr[3];
+  const double glo = sl.hdr[0] * sc, ghi = sl.hdr[1] * sc;
+  const double span = fmax(fabs(glo), fabs(ghi));
+  const double pivmin = DBL_MIN * fmax(1.0, span * span);
+  double lo = sl.est[i] - tol32, hi = sl.est[i] + tol32;
+  if (band_sturm<S>(sl.Tb, N, lo, pivmin) > i) lo = glo;
+  if (band_sturm<S>(sl.Tb, N, hi, pivmin) <= i) hi = ghi;
+  for (int it = 0; it < 128; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(hi - lo > 2.0 * DBL_EPSILON * span) || mid <= lo || mid >= hi) break;
+    if (band_sturm<S>(sl.Tb, N, mid, pivmin) <= i) lo = mid;
+    else hi = mid;
+  }
+  sl.est[i] = 0.5 * (lo + hi);
+}
+
 __device__ inline double hash_unit(unsigned int k, unsigned int i) {
   unsigned int x = k * 0x9E3779B1u ^ (i + 0x7F4A7C15u) * 0x85EBCA77u;
   x ^= x >> 15;
@@ -324,7 +443,7 @@ __device__ __forceinline__ double mval(const double* __restrict__ Tb, int N, dou
 // compile-time constant.  U rows go to per-thread scratch ([k][e][tid] layout, coalesced).
 template <int S>
 __device__ void solve1(const double* __restrict__ Tb, int N, double sigma, double tiny, double xscale,
-                       double* __restrict__ X, size_t ld, int col, double* __restrict__ U, int tid) {
+                       double* __restrict__ X, size_t ld, int col, double* __restrict__ U, int tid, size_t ldu) {
   constexpr int W = 2 * S + 1;
   double win[S + 1][W];
   double yw[S + 1];
@@ -367,7 +486,7 @@ __device__ void solve1(const double* __restrict__ Tb, int N, double sigma, doubl
       yw[r] = fma(-l, yw[0], yw[r]);
     }
 #pragma unroll
-    for (int c = 0; c < W; ++c) U[((size_t)k * W + c) * ld + tid] = win[0][c];
+    for (int c = 0; c < W; ++c) U[((size_t)k * W + c) * ldu + tid] = win[0][c];
     X[(size_t)k * ld + col] = yw[0];
 #pragma unroll
     for (int r = 0; r < S; ++r) {
@@ -389,12 +508,12 @@ __device__ void solve1(const double* __restrict__ Tb, int N, double sigma, doubl
       const int kp = k - kPf;
       prefetch_l2(X + (size_t)kp * ld + col);
 #pragma unroll
-      for (int e = 0; e < W; ++e) prefetch_l2(U + ((size_t)kp * W + e) * ld + tid);
+      for (int e = 0; e < W; ++e) prefetch_l2(U + ((size_t)kp * W + e) * ldu + tid);
     }
     double t = X[(size_t)k * ld + col];
 #pragma unroll
-    for (int e = 1; e < W; ++e) t = fma(-U[((size_t)k * W + e) * ld + tid], xs[e - 1], t);
-    const double xk = t / U[((size_t)k * W) * ld + tid];
+    for (int e = 1; e < W; ++e) t = fma(-U[((size_t)k * W + e) * ldu + tid], xs[e - 1], t);
+    const double xk = t / U[((size_t)k * W) * ldu + tid];
     X[(size_t)k * ld + col] = xk;
 #pragma unroll
     for (int e = W - 2; e > 0; --e) xs[e] = xs[e - 1];
@@ -500,13 +619,13 @@ __global__ void k_invit(CheckArgs g) {
   if (i >= N) return;
   Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   const size_t ld = (size_t)g.nmax;
-  const double tolc = sl.hdr[4];
+  const double tolc = sl.etol[i];
   const double tnorm = sl.hdr[3] * fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
   const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
-  // cluster membership from the fp32 estimates
-  if (i > 0 && sl.est[i] - sl.est[i - 1] <= tolc) return;  // not a leader
+  // groups: consecutive estimates closer than the larger of their two tolerances
+  if (i > 0 && sl.est[i] - sl.est[i - 1] <= fmax(tolc, sl.etol[i - 1])) return;  // not a leader
   int c = 1;
-  while (i + c < N && sl.est[i + c] - sl.est[i + c - 1] <= tolc) ++c;
+  while (i + c < N && sl.est[i + c] - sl.est[i + c - 1] <= fmax(sl.etol[i + c], sl.etol[i + c - 1])) ++c;
   if (c > kMaxCluster) {
     atomicOr(g.chk_err + m - 1, DERR_EIGEN);
     c = kMaxCluster;
@@ -515,10 +634,11 @@ __global__ void k_invit(CheckArgs g) {
     for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i + v] = hash_unit((unsigned)k, (unsigned)(i + v));
   if (c == 1) {
     const double est = sl.est[i];
+    const bool refined = tolc < sl.hdr[4];
     double sigma = est, rq = est, res = 0.0, prev = est, xscale = 1.0;
     int extra = -1;  // iterations still to run after the Rayleigh quotient settled
     for (int it = 0; it < kMaxIters; ++it) {
-      solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i);
+      solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i, ld);
       double num, den;
       rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
       rq = num / den;
@@ -528,8 +648,10 @@ __global__ void k_invit(CheckArgs g) {
       // settled: one more Rayleigh-quotient step brings the vector to full precision
       if (extra < 0 && it >= 1 && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
       prev = rq;
-      // Rayleigh-quotient shifts once the iterate is dominated by the wanted eigenvector
-      if (it >= 1 && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
+      // Rayleigh-quotient shifts once the iterate is dominated by the wanted eigenvector; an
+      // fp64-refined estimate is already within a few eps ||T|| and stays the shift, so the
+      // iteration cannot drift to a neighbour closer than the fp32 tolerance
+      if (!refined && it >= 1 && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
     }
     for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
     rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
@@ -560,36 +682,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// x_u^T T x_v over the rows the lane owns
+// x_u^T T x_v over the rows the lane owns (contiguous vectors)
 template <int S>
-__device__ double lane_xTy(const double* __restrict__ Tb, int N, const double* __restrict__ X, size_t ld, int cu, int cv,
-                           int lane) {
+__device__ double lane_xTy(const double* __restrict__ Tb, int N, const double* __restrict__ xu,
+                           const double* __restrict__ xv, int lane) {
   double acc = 0.0;
   for (int k = lane; k < N; k += 32) {
     double tx = 0.0;
-    for (int c = max(0, k - S); c <= min(N - 1, k + S); ++c) tx = fma(tband(Tb, N, S, k, c), X[(size_t)c * ld + cv], tx);
-    acc = fma(X[(size_t)k * ld + cu], tx, acc);
+    for (int c = max(0, k - S); c <= min(N - 1, k + S); ++c) tx = fma(tband(Tb, N, S, k, c), xv[c], tx);
+    acc = fma(xu[k], tx, acc);
   }
   return acc;
 }
 
-// ||T x_v - theta x_v||^2 over the rows the lane owns
+// ||T x - theta x||^2 over the rows the lane owns (contiguous vector)
 template <int S>
-__device__ double lane_res2(const double* __restrict__ Tb, int N, const double* __restrict__ X, size_t ld, int cv,
-                            double theta, int lane) {
+__device__ double lane_res2(const double* __restrict__ Tb, int N, const double* __restrict__ x, double theta,
+                            int lane) {
   double r2 = 0.0;
   for (int k = lane; k < N; k += 32) {
     double tx = 0.0;
-    for (int c = max(0, k - S); c <= min(N - 1, k + S); ++c) tx = fma(tband(Tb, N, S, k, c), X[(size_t)c * ld + cv], tx);
-    const double d = tx - theta * X[(size_t)k * ld + cv];
+    for (int c = max(0, k - S); c <= min(N - 1, k + S); ++c) tx = fma(tband(Tb, N, S, k, c), x[c], tx);
+    const double d = tx - theta * x[k];
     r2 = fma(d, d, r2);
   }
   return r2;
 }
 
-// 3b. clusters of fp32 estimates, one warp each: lane v iterates member v at its own shift;
-// the warp re-orthonormalises (MGS, twice) after every step and splits the cluster by
-// Rayleigh-Ritz between rounds, so the vectors of near-equal eigenvalues stay orthonormal.
+// 3b. groups of close estimates, one warp each: lane v iterates member v at its own shift; the
+// warp re-orthonormalises (MGS, twice) after every step and splits the group by Rayleigh-Ritz
+// between rounds, so the vectors of near-equal eigenvalues stay orthonormal.  The members'
+// vectors live contiguously in Xc (member i at Xc + i nmax), so the warp's row loops coalesce.
 template <int S>
 __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   constexpr int WPB = 4;
@@ -613,37 +736,39 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   int* ord = ords[w];
   for (int e = blockIdx.x * WPB + w; e < ncl; e += gridDim.x * WPB) {
     const int i = sl.clist[2 + 2 * e], c = sl.clist[3 + 2 * e];
+    double* xc = sl.Xc + (size_t)i * ld;  // member v at xc + v ld
     if (lane < c) shift[lane] = sl.est[i + lane];
-    for (int k = lane; k < N; k += 32)
-      for (int v = 0; v < c; ++v) sl.X[(size_t)k * ld + i + v] = hash_unit((unsigned)k, (unsigned)(i + v));
+    for (int v = 0; v < c; ++v)
+      for (int k = lane; k < N; k += 32) xc[(size_t)v * ld + k] = hash_unit((unsigned)k, (unsigned)(i + v));
     __syncwarp();
     bool done = false;
     for (int round = 0; round < kMaxRounds && !done; ++round) {
       for (int it = 0; it < 2; ++it) {
-        if (lane < c) solve1<S>(sl.Tb, N, shift[lane], tiny, 1.0, sl.X, ld, i + lane, sl.U, i + lane);
+        if (lane < c) solve1<S>(sl.Tb, N, shift[lane], tiny, 1.0, xc + (size_t)lane * ld, 1, 0, sl.U, i + lane, ld);
         __syncwarp();
         for (int pass = 0; pass < 2; ++pass)
           for (int v = 0; v < c; ++v) {
+            double* xv = xc + (size_t)v * ld;
             for (int u = 0; u < v; ++u) {
+              const double* xu = xc + (size_t)u * ld;
               double d = 0.0;
-              for (int k = lane; k < N; k += 32) d = fma(sl.X[(size_t)k * ld + i + u], sl.X[(size_t)k * ld + i + v], d);
+              for (int k = lane; k < N; k += 32) d = fma(xu[k], xv[k], d);
               d = warp_sum(d);
-              for (int k = lane; k < N; k += 32)
-                sl.X[(size_t)k * ld + i + v] = fma(-d, sl.X[(size_t)k * ld + i + u], sl.X[(size_t)k * ld + i + v]);
+              for (int k = lane; k < N; k += 32) xv[k] = fma(-d, xu[k], xv[k]);
               __syncwarp();
             }
             double n2 = 0.0;
-            for (int k = lane; k < N; k += 32) n2 = fma(sl.X[(size_t)k * ld + i + v], sl.X[(size_t)k * ld + i + v], n2);
+            for (int k = lane; k < N; k += 32) n2 = fma(xv[k], xv[k], n2);
             n2 = warp_sum(n2);
             const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-            for (int k = lane; k < N; k += 32) sl.X[(size_t)k * ld + i + v] *= inv;
+            for (int k = lane; k < N; k += 32) xv[k] *= inv;
             __syncwarp();
           }
       }
       // Rayleigh-Ritz
       for (int u = 0; u < c; ++u)
         for (int v = u; v < c; ++v) {
-          const double h = warp_sum(lane_xTy<S>(sl.Tb, N, sl.X, ld, i + u, i + v, lane));
+          const double h = warp_sum(lane_xTy<S>(sl.Tb, N, xc + (size_t)u * ld, xc + (size_t)v * ld, lane));
           if (lane == 0) {
             H[u][v] = h;
             H[v][u] = h;
@@ -697,32 +822,37 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
       __syncwarp();
       for (int k = lane; k < N; k += 32) {
         double row[kMaxCluster], out[kMaxCluster];
-        for (int v = 0; v < c; ++v) row[v] = sl.X[(size_t)k * ld + i + v];
+        for (int v = 0; v < c; ++v) row[v] = xc[(size_t)v * ld + k];
         for (int v = 0; v < c; ++v) {
           double t = 0.0;
           for (int u = 0; u < c; ++u) t = fma(row[u], V[u][ord[v]], t);
           out[v] = t;
         }
-        for (int v = 0; v < c; ++v) sl.X[(size_t)k * ld + i + v] = out[v];
+        for (int v = 0; v < c; ++v) xc[(size_t)v * ld + k] = out[v];
       }
       __syncwarp();
       if (round == 0) continue;
       // converged once every member's residual passes
       bool ok = true;
       for (int v = 0; v < c; ++v) {
-        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, sl.X, ld, i + v, shift[v], lane));
+        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xc + (size_t)v * ld, shift[v], lane));
         ok = ok && sqrt(r2) <= kResTol * tnorm;
       }
       done = ok;
     }
-    // final Rayleigh quotients and residual test, then the a and w rows
+    // final Rayleigh quotients and residual test; the first and last S rows go back to X for
+    // the a and w rows
     for (int v = 0; v < c; ++v) {
-      const double num = warp_sum(lane_xTy<S>(sl.Tb, N, sl.X, ld, i + v, i + v, lane));
-      const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, sl.X, ld, i + v, num, lane));
+      const double* xv = xc + (size_t)v * ld;
+      const double num = warp_sum(lane_xTy<S>(sl.Tb, N, xv, xv, lane));
+      const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xv, num, lane));
+      if (lane < S) {
+        sl.X[(size_t)lane * ld + i + v] = xv[lane];
+        sl.X[(size_t)(N - S + lane) * ld + i + v] = xv[N - S + lane];
+      }
       if (lane == 0) {
         sl.lam[i + v] = num;
-        const double tolc = sl.hdr[4];
-        const bool inside = num >= sl.est[i] - 0.5 * tolc && num <= sl.est[i + c - 1] + 0.5 * tolc;
+        const bool inside = num >= sl.est[i] - 0.5 * sl.etol[i] && num <= sl.est[i + c - 1] + 0.5 * sl.etol[i + c - 1];
         if (!(sqrt(r2) <= kResTol * tnorm) || !isfinite(num) || !inside) {
           atomicOr(g.chk_err + m - 1, DERR_EIGEN);
 #ifdef LYAP_DEBUG
@@ -731,6 +861,7 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
         }
       }
     }
+    __syncwarp();
     if (lane == 0) write_aw<S>(g, sl, m, N, ld, i, c);
     __syncwarp();
   }
@@ -858,13 +989,14 @@ __global__ void k_finalize(CheckArgs ga, CheckArgs gb, int sylv, double* hist, d
   }
 }
 
-CheckArgs make_args(lyap_handle* h, int opi, int m_lo, int nchk, int every, int slot_base) {
+// nslots slots of leading dimension nmax per operator, operator 1's after operator 0's
+CheckArgs make_args(lyap_handle* h, int opi, int m_lo, int nchk, int every, int nmax, int nslots) {
   CheckArgs g;
   g.log = h->op[opi].log;
   g.s = h->s;
-  g.nmax = h->plan.nmax;
-  const size_t sd = slot_doubles(h->s, h->plan.nmax);
-  g.slots = reinterpret_cast<double*>(h->check_ws) + sd * (size_t)(opi * h->plan.check_batch + slot_base);
+  g.nmax = nmax;
+  const size_t sd = slot_doubles(h->s, nmax);
+  g.slots = reinterpret_cast<double*>(h->check_ws) + sd * (size_t)(opi * nslots);
   g.m_lo = m_lo;
   g.nchk = nchk;
   g.every = every;
@@ -879,6 +1011,15 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
   k_band32<<<g.nchk, kBandThreads, smem, st>>>(g);
   dim3 gv((nmax_batch + 31) / 32, g.nchk);
   k_bisect32<<<gv, 32, 0, st>>>(g);
+  // fp64 estimates for the members of oversized fp32 clusters
+  k_mark_refine<<<g.nchk, 256, 0, st>>>(g);
+  switch (g.s) {
+    case 1: k_refine64<1><<<gv, 32, 0, st>>>(g); break;
+    case 2: k_refine64<2><<<gv, 32, 0, st>>>(g); break;
+    case 3: k_refine64<3><<<gv, 32, 0, st>>>(g); break;
+    case 4: k_refine64<4><<<gv, 32, 0, st>>>(g); break;
+    case 8: k_refine64<8><<<gv, 32, 0, st>>>(g); break;
+  }
   // clusters: 16 blocks of 4 warps per check, each warp takes clusters from the list in turn
   dim3 gc(16, g.nchk);
   switch (g.s) {
@@ -888,26 +1029,31 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
     case 4: k_invit<4><<<gv, 32, 0, st>>>(g); k_invit_clusters<4><<<gc, 128, 0, st>>>(g); break;
     case 8: k_invit<8><<<gv, 32, 0, st>>>(g); k_invit_clusters<8><<<gc, 128, 0, st>>>(g); break;
   }
-  return 4;
+  return 6;
 }
 
 }  // namespace
 
 size_t check_slot_bytes(int s, int nmax) { return slot_doubles(s, nmax) * sizeof(double); }
 
-// Evaluates the checks for m = m_lo..m_hi (at most plan.check_batch of them).
+// leading dimension of the slots of a batch whose largest check is at m_hi
+int batch_nmax(int s, int m_hi) { return (s * m_hi + 7) / 8 * 8; }
+
+// Evaluates the checks for m = m_lo..m_hi; the slots of the batch have leading dimension
+// batch_nmax(s, m_hi) and must fit in the check area (the caller sizes the batch).
 int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
   int nl = 0;
   const int nchk = m_hi - m_lo + 1;
   const int every = h->opt.check_every > 0 ? h->opt.check_every : 1;
   const int nmax_batch = h->s * m_hi;
-  CheckArgs ga = make_args(h, 0, m_lo, nchk, every, 0);
+  const int nb = batch_nmax(h->s, m_hi);
+  CheckArgs ga = make_args(h, 0, m_lo, nchk, every, nb, nchk);
   nl += eigen_pipeline(ga, nmax_batch, st);
   CheckArgs gb = ga;
   const int wpb = 8;
   dim3 gc((nmax_batch + wpb - 1) / wpb, nchk);
   if (h->plan.sylv) {
-    gb = make_args(h, 1, m_lo, nchk, every, 0);
+    gb = make_args(h, 1, m_lo, nchk, every, nb, nchk);
     nl += eigen_pipeline(gb, nmax_batch, st);
     k_cauchy_sylv<<<gc, wpb * 32, 0, st>>>(ga, gb, 0);
     k_cauchy_sylv<<<gc, wpb * 32, 0, st>>>(ga, gb, 1);
@@ -922,7 +1068,7 @@ int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
 
 // Eigenvalues and a, w rows of T_m (slot 0 of operator opi) for the factor step.
 int launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st) {
-  CheckArgs g = make_args(h, opi, m, 1, 1, 0);
+  CheckArgs g = make_args(h, opi, m, 1, 1, h->plan.nmax, h->plan.check_batch);
   return eigen_pipeline(g, h->s * m, st);
 }
 
@@ -957,7 +1103,7 @@ constexpr int kNoAllocMaxS = 4;
 constexpr int kNoAllocMaxN = 256;  // s * m
 constexpr size_t kNoAllocSlot = 8 + 4 * (size_t)kNoAllocMaxN + (size_t)(kNoAllocMaxS + 1) * kNoAllocMaxN +
                                 2 * (size_t)kNoAllocMaxS * kNoAllocMaxN + ((size_t)kNoAllocMaxN + 16) +
-                                (size_t)(2 * kNoAllocMaxS + 2) * kNoAllocMaxN * kNoAllocMaxN;
+                                (size_t)(2 * kNoAllocMaxS + 3) * kNoAllocMaxN * kNoAllocMaxN + (size_t)kNoAllocMaxN;
 constexpr size_t kNoAllocLog = (size_t)(kNoAllocMaxN + 1) * LOG_NREC * kNoAllocMaxS * kNoAllocMaxS;
 constexpr size_t kNoAllocInts = 4 + kNoAllocMaxN;  // flags, per-m error bits
 constexpr size_t kNoAllocDoubles = kNoAllocSlot + kNoAllocLog + kNoAllocMaxN + (kNoAllocInts + 1) / 2;
@@ -965,7 +1111,8 @@ constexpr size_t kNoAllocDoubles = kNoAllocSlot + kNoAllocLog + kNoAllocMaxN + (
 static_assert(kNoAllocSlot >= 8 + (size_t)kNoAllocMaxN + 3 * (size_t)kNoAllocMaxN +
                                    (size_t)(kNoAllocMaxS + 1) * kNoAllocMaxN + 2 * (size_t)kNoAllocMaxS * kNoAllocMaxN +
                                    ((size_t)kNoAllocMaxN + 16) + (size_t)kNoAllocMaxN * kNoAllocMaxN +
-                                   (size_t)(2 * kNoAllocMaxS + 1) * kNoAllocMaxN * kNoAllocMaxN,
+                                   (size_t)(2 * kNoAllocMaxS + 1) * kNoAllocMaxN * kNoAllocMaxN +
+                                   (size_t)kNoAllocMaxN + (size_t)kNoAllocMaxN * kNoAllocMaxN,
               "scratch slot must hold a check slot of the largest supported size");
 
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];

@@ -70,7 +70,8 @@ struct Plan {
   int bulk_f32 = 0;
   int maxit = 1000;
   int sweep_grid = 0;     // CTAs of every row sweep
-  int check_batch = 32;
+  int check_batch = 32;   // full-size (nmax) slots that fit in the check area (the factor uses one)
+  int check_batch_req = 32;  // checks per batch asked for; a batch's slots are sized by its largest m
   int nmax = 0;           // largest reduced dimension s * maxit
   int pass2_blocks = 16;
   int zcap = 0;
@@ -96,6 +97,7 @@ struct CheckSlot {
 };
 
 size_t check_slot_bytes(int s, int nmax);
+int batch_nmax(int s, int m_hi);
 
 struct lyap_handle {
   Plan plan;

@@ -120,14 +120,15 @@ __global__ void __launch_bounds__(kPcThreads) k_pivoted_cholesky(const double* _
   if (tid == 0) f.tcount[0] = k;
 }
 
-// K = L^T L  (t x t), L rows are the pivoted columns
-__global__ void k_gram_L(FactorWs f, int nn, int tmax) {
+// out = L(:, lo:lo+cnt)^T L(:, lo:lo+cnt)  (t x t); the rows of f.L are the pivoted columns of
+// the factor, so this is the Gram matrix of the factor's rows lo..lo+cnt-1
+__global__ void k_gram_L(FactorWs f, int nn, int lo, int cnt, int tmax, double* __restrict__ out) {
   const int t = f.tcount[0];
   const int a = blockIdx.x, b = blockIdx.y * blockDim.x + threadIdx.x;
   if (a >= t || b >= t) return;
   double acc = 0.0;
-  for (int i = 0; i < nn; ++i) acc += f.L[(size_t)a * nn + i] * f.L[(size_t)b * nn + i];
-  f.K[(size_t)a * tmax + b] = acc;
+  for (int i = lo; i < lo + cnt; ++i) acc += f.L[(size_t)a * nn + i] * f.L[(size_t)b * nn + i];
+  out[(size_t)a * tmax + b] = acc;
 }
 
 // cyclic parallel Jacobi (round-robin pairing) on the symmetric t x t matrix K, one CTA
@@ -311,6 +312,176 @@ __global__ void k_form_M(FactorWs f, int nrows, int tmax, const int* __restrict_
   M[(size_t)r * ldm + c] = acc;
 }
 
+// C[r][c] = scale[c] * sum_k op(A)[r][k] op(B)[k][bcol(c)], op = identity or transpose,
+// bcol(c) = order ? order[c] : c; rows x cols outputs, inner dimension read from *kdim (a
+// device count).  Small dense products of the factor step (t <= 2000), one thread per output.
+__global__ void k_small_gemm(const double* __restrict__ A, int lda, int transA, const double* __restrict__ B,
+                             int ldb, int transB, const int* __restrict__ order, const double* __restrict__ scale,
+                             double* __restrict__ C, int ldc, int rows, int cols, const int* __restrict__ kdim) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (r >= rows || c >= cols) return;
+  const int K = *kdim;
+  const int bc = order ? order[c] : c;
+  const size_t sa_r = transA ? 1 : (size_t)lda, sa_k = transA ? (size_t)lda : 1;
+  const size_t sb_k = transB ? 1 : (size_t)ldb, sb_c = transB ? (size_t)ldb : 1;
+  double acc = 0.0;
+  for (int k = 0; k < K; ++k) acc = fma(A[r * sa_r + k * sa_k], B[k * sb_k + bc * sb_c], acc);
+  C[(size_t)r * ldc + c] = scale ? acc * scale[c] : acc;
+}
+
+void small_gemm(const double* A, int lda, int transA, const double* B, int ldb, int transB, const int* order,
+                const double* scale, double* C, int ldc, int rows, int cols, const int* kdim, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return;
+  k_small_gemm<<<dim3((rows + 127) / 128, cols), 128, 0, st>>>(A, lda, transA, B, ldb, transB, order, scale, C, ldc,
+                                                                rows, cols, kdim);
+}
+
+// fixed-order block sum (all threads get the result); red holds one slot per warp
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// R factors of the Householder QR of the two N x t blocks of the stacked pivoted-Cholesky
+// factor (block 0: rows 0..N-1, block 1: rows N..2N-1; f.L row k holds column k).  The
+// columns are copied to W (column k at W + k N) and reduced in place; R (t x t, row-major,
+// rows >= N zero) is written out.  Only R is needed: Y~ = L_A L_B^T = U_A (R_A R_B^T) U_B^T.
+__global__ void __launch_bounds__(1024) k_householder_r(const double* __restrict__ Lrows, int nn, int N,
+                                                        const int* __restrict__ tcount, double* __restrict__ Wa,
+                                                        double* __restrict__ Wb, double* __restrict__ Ra,
+                                                        double* __restrict__ Rb, int tmax) {
+  __shared__ double red[32];
+  __shared__ double s_vn2;
+  const int t = *tcount;
+  const int lo = blockIdx.x == 0 ? 0 : N;
+  double* W = blockIdx.x == 0 ? Wa : Wb;
+  double* R = blockIdx.x == 0 ? Ra : Rb;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (size_t idx = tid; idx < (size_t)t * N; idx += blockDim.x) {
+    const int k = (int)(idx / N), i = (int)(idx % N);
+    W[idx] = Lrows[(size_t)k * nn + lo + i];
+  }
+  for (int idx = tid; idx < t * t; idx += blockDim.x) R[(size_t)(idx / t) * tmax + idx % t] = 0.0;
+  __syncthreads();
+  const int kend = t < N ? t : N;
+  for (int k = 0; k < kend; ++k) {
+    double* x = W + (size_t)k * N;
+    double ss = 0.0;
+    for (int i = k + tid; i < N; i += blockDim.x) ss = fma(x[i], x[i], ss);
+    const double tot = block_sum(ss, red);
+    if (tid == 0) {
+      const double xk = x[k], nrm = sqrt(tot);
+      const double alpha = xk >= 0.0 ? -nrm : nrm;
+      const double vk = xk - alpha;
+      x[k] = vk;
+      s_vn2 = tot - xk * xk + vk * vk;
+      R[(size_t)k * tmax + k] = alpha;
+    }
+    __syncthreads();
+    const double vn2 = s_vn2;
+    if (vn2 > 0.0) {
+      for (int j = k + 1 + warp; j < t; j += nw) {
+        double* y = W + (size_t)j * N;
+        double d = 0.0;
+        for (int i = k + lane; i < N; i += 32) d = fma(x[i], y[i], d);
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const double fct = 2.0 * d / vn2;
+        for (int i = k + lane; i < N; i += 32) y[i] = fma(-fct, x[i], y[i]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < t * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx % t;
+    if (i < j && i < N) R[(size_t)i * tmax + j] = W[(size_t)j * N + i];
+  }
+}
+
+// One-sided (Hestenes) Jacobi SVD of the t x t matrix G stored by columns (column j at
+// G + j tmax): columns are rotated in round-robin pairs until mutually orthogonal, so G V =
+// U Sigma with V accumulated by columns; sig[j] = ||G(:, j)||.  Singular values come out with
+// absolute error ~ eps ||G||, without squaring the condition as a Gram matrix would.
+__global__ void __launch_bounds__(1024) k_onesided_jacobi(double* __restrict__ G, double* __restrict__ V,
+                                                          const int* __restrict__ tcount, int tmax,
+                                                          double* __restrict__ sig) {
+  __shared__ int s_rot;
+  const int t = *tcount;
+  const int tp = t + (t & 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int idx = tid; idx < t * t; idx += blockDim.x) V[(size_t)(idx / t) * tmax + idx % t] = (idx / t == idx % t);
+  __syncthreads();
+  for (int sweep = 0; sweep < 60 && t > 1; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < tp - 1; ++round) {
+      for (int k = warp; k < tp / 2; k += nw) {
+        const int i0 = k == 0 ? 0 : 1 + (k - 1 + round) % (tp - 1);
+        const int j0 = 1 + (tp - 2 - k + round) % (tp - 1);
+        const int p = min(i0, j0), q = max(i0, j0);
+        if (q >= t) continue;
+        double* gp = G + (size_t)p * tmax;
+        double* gq = G + (size_t)q * tmax;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < t; i += 32) {
+          al = fma(gp[i], gp[i], al);
+          be = fma(gq[i], gq[i], be);
+          ga = fma(gp[i], gq[i], ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (!(ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be))) continue;
+        const double ze = (be - al) / (2.0 * ga);
+        const double tt = (ze >= 0.0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(1.0 + ze * ze));
+        const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+        double* vp = V + (size_t)p * tmax;
+        double* vq = V + (size_t)q * tmax;
+        for (int i = lane; i < t; i += 32) {
+          const double a = gp[i], b = gq[i];
+          gp[i] = c * a - sn * b;
+          gq[i] = sn * a + c * b;
+          const double va = vp[i], vb = vq[i];
+          vp[i] = c * va - sn * vb;
+          vq[i] = sn * va + c * vb;
+        }
+        if (lane == 0) atomicAdd(&s_rot, 1);
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (rot == 0) break;
+  }
+  for (int j = warp; j < t; j += nw) {
+    double n2 = 0.0;
+    for (int i = lane; i < t; i += 32) n2 = fma(G[(size_t)j * tmax + i], G[(size_t)j * tmax + i], n2);
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    if (lane == 0) sig[j] = sqrt(n2);
+  }
+}
+
+// stacked nodes mu = [lambda; upsilon] and rows c = [a; b] of the 2N x 2N PSD kernel
+// -(c_x . c_y)/(mu_x + mu_y), whose off-diagonal block is the Sylvester Y~
+__global__ void k_stack(const double* __restrict__ la, const double* __restrict__ aa, const double* __restrict__ lb,
+                        const double* __restrict__ ab, int N, int s, double* __restrict__ mu,
+                        double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * N) return;
+  const bool A = i < N;
+  const int r = A ? i : i - N;
+  mu[i] = A ? la[r] : lb[r];
+  for (int k = 0; k < s; ++k) c[(size_t)i * s + k] = A ? aa[(size_t)r * s + k] : ab[(size_t)r * s + k];
+}
+
 // ---- Z += Vbuf (n x K) * Mg (K x t) -------------------------------------------
 template <typename TV, typename TZ>
 __global__ void __launch_bounds__(256) k_gemm_accum(int64_t n, int K, int t, const TV* __restrict__ Vb, int64_t ldv,
@@ -409,8 +580,9 @@ int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void*
   const int64_t n = op.n;
   const int64_t ldb = (int64_t)kb * s;
   char* buf[2] = {reinterpret_cast<char*>(op.V[0]) + 0, nullptr};
-  // the pass-2 buffers sit after the factor scratch, one pair per operator
-  buf[0] = h->factor_ws + h->plan.factor_bytes + (size_t)opi * 2 * lyap_align256((int64_t)(n * ldb * w));
+  // the pass-2 buffers sit after the factor scratch: operator 0's pair, then operator 1's
+  buf[0] = h->factor_ws + h->plan.factor_bytes +
+           (opi ? 2 * (size_t)lyap_align256((int64_t)(h->op[0].n * ldb * w)) : 0);
   buf[1] = buf[0] + lyap_align256((int64_t)(n * ldb * w));
   auto pos = [&](int j) -> char* {  // block j (1-based)
     const int g = (j - 1) / kb, c = (j - 1) % kb;
@@ -460,6 +632,13 @@ size_t factor_ws_bytes(int s, int nmax, int sylv) {
   add(sizeof(double) * (size_t)nmax2 * tmax);
   add(sizeof(double) * (size_t)nmax2);  // diagonal scratch of the pivoted Cholesky
   add(sizeof(int) * (size_t)tmax);      // kept-column order
+  if (sylv) {
+    add(sizeof(double) * (size_t)nmax2);          // stacked nodes
+    add(sizeof(double) * (size_t)nmax2 * s);      // stacked rows
+    for (int k = 0; k < 6; ++k) add(sizeof(double) * (size_t)tmax * tmax);  // R_A, R_B, G, V_G, R1, R2
+    for (int k = 0; k < 2; ++k) add(sizeof(double) * (size_t)tmax * nmax);  // Householder work
+    add(sizeof(double) * 3 * (size_t)tmax);       // column scales, singular values
+  }
   return b;
 }
 
@@ -468,12 +647,116 @@ size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32) {
   return 2 * (size_t)lyap_align256((int64_t)(n * (int64_t)kb * s * w));
 }
 
+// Sylvester factors (Sec. 5.1): Y~_ij = -(a_i . b_j)/(lambda_i + upsilon_j) is the off-diagonal
+// block of the 2N x 2N positive semidefinite kernel -(c_x . c_y)/(mu_x + mu_y) on the stacked
+// nodes mu = [lambda; upsilon] and rows c = [a; b] (a Schur product of a Gram matrix and the
+// Cauchy matrix -1/(mu_x + mu_y), all mu < 0).  Its pivoted Cholesky factor [L_A; L_B] gives
+// Y~ ~= L_A L_B^T with an error below the remainder's trace.  With the Householder R factors
+// L_A = U_A R_A, L_B = U_B R_B and the SVD R_A R_B^T = U_G Sigma V_G^T (one-sided Jacobi),
+//   Y1 = L_A R_B^T V_G,t Sigma_t^{-1/2},   Y2 = L_B R_A^T U_G,t Sigma_t^{1/2}
+//                                             = L_B R_A^T (G V_G)_t Sigma_t^{-1/2} Sigma_t^{-1},
+// so Y1 Y2^T is the truncated SVD of L_A L_B^T and only kept singular values are divided by.
+// As in the Lyapunov case Q L_A and P L_B come from shifted band solves, so M1 = Q Y1 and
+// M2 = P Y2 are formed without Q or P; the truncation keeps the fewest singular values whose
+// discarded tail has Frobenius norm <= eps = trunc_eps ||C1||_F ||C2||_F.
+int run_factor_sylv(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
+                    cudaStream_t st) {
+  const int s = h->s, m = h->m, N = s * m, N2 = 2 * N;
+  const int nmax = h->plan.nmax, nmax2 = 2 * nmax;
+  const int tmax = nmax2 < kTmaxCap ? nmax2 : kTmaxCap;
+  FactorWs f = carve(h->factor_ws, s, nmax2, tmax, nmax);
+  char* p = reinterpret_cast<char*>(f.M) + lyap_align256((int64_t)(sizeof(double) * (size_t)nmax2 * tmax));
+  auto take = [&](size_t bytes) { char* r = p; p += lyap_align256((int64_t)bytes); return r; };
+  double* dg = (double*)take(sizeof(double) * nmax2);
+  int* order_d = (int*)take(sizeof(int) * tmax);
+  double* mu = (double*)take(sizeof(double) * nmax2);
+  double* cst = (double*)take(sizeof(double) * (size_t)nmax2 * s);
+  const size_t tt = (size_t)tmax * tmax;
+  double* RA = (double*)take(sizeof(double) * tt);
+  double* RB = (double*)take(sizeof(double) * tt);
+  double* Gc = (double*)take(sizeof(double) * tt);
+  double* VG = (double*)take(sizeof(double) * tt);
+  double* R1 = (double*)take(sizeof(double) * tt);
+  double* R2 = (double*)take(sizeof(double) * tt);
+  double* WA = (double*)take(sizeof(double) * (size_t)tmax * nmax);
+  double* WBh = (double*)take(sizeof(double) * (size_t)tmax * nmax);
+  double* scl = (double*)take(sizeof(double) * 3 * (size_t)tmax);
+  double* sig_d = scl + 2 * (size_t)tmax;
+
+  // 1. eigenvalues and first-block rows of both projected matrices (Alg. 4 steps 1-4)
+  h->launches += launch_eigen_for_factor(h, 0, m, st);
+  h->launches += launch_eigen_for_factor(h, 1, m, st);
+  double *la, *aa, *wa, *lb, *ab, *wb;
+  check_slot0(h, 0, &la, &aa, &wa);
+  check_slot0(h, 1, &lb, &ab, &wb);
+  k_stack<<<(N2 + 127) / 128, 128, 0, st>>>(la, aa, lb, ab, N, s, mu, cst);
+  // 2. pivoted Cholesky of the stacked kernel
+  const double eps_abs = h->opt.trunc_eps * h->op[0].beta * h->op[1].beta;
+  k_pivoted_cholesky<<<1, kPcThreads, 0, st>>>(mu, cst, N2, s, tmax, 1e-2 * eps_abs, f, dg);
+  h->launches += 2;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  const int tpc = h->flags_host[2];
+  if (tpc <= 0) {
+    *t_out = 0;
+    return LYAP_OK;
+  }
+  // 3. [Q L_A; P L_B] by shifted band solves with T_m (rows 0..N-1) and J_m (rows N..2N-1)
+  const int nthr = 64;
+  k_shifted_solves<<<(tpc + nthr - 1) / nthr, nthr, 0, st>>>(h->op[0].log, s, m, mu, cst, f, tmax, nmax, 0, 0, N2,
+                                                             h->flags);
+  k_shifted_solves<<<(tpc + nthr - 1) / nthr, nthr, 0, st>>>(h->op[1].log, s, m, mu, cst, f, tmax, nmax, N * tmax,
+                                                             0, N2, h->flags);
+  k_apply_lpp<<<(N2 + 127) / 128, 128, 0, st>>>(f, N2, N2, tmax);
+  // 4. R_A, R_B; G = R_A R_B^T by columns (G(:, j) = R_A R_B(j, :)^T); its one-sided Jacobi SVD
+  k_householder_r<<<2, 1024, 0, st>>>(f.L, N2, N, f.tcount, WA, WBh, RA, RB, tmax);
+  small_gemm(RB, tmax, 0, RA, tmax, 1, nullptr, nullptr, Gc, tmax, tpc, tpc, f.tcount, st);
+  k_onesided_jacobi<<<1, 1024, 0, st>>>(Gc, VG, f.tcount, tmax, sig_d);
+  h->launches += 6;
+  std::vector<double> sig(tpc);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(sig.data(), sig_d, sizeof(double) * tpc, cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  // 5. truncation on the singular values, non-increasing (eq. 2.5 applied to the SVD of Y~)
+  std::vector<int> order(tpc);
+  for (int i = 0; i < tpc; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sig[x] > sig[y]; });
+  std::vector<double> tail(tpc + 1, 0.0);
+  for (int i = tpc - 1; i >= 0; --i) tail[i] = tail[i + 1] + sig[order[i]] * sig[order[i]];
+  int tk = 0;
+  while (tk < tpc && !(sqrt(tail[tk]) <= eps_abs)) ++tk;
+  while (tk > 0 && !(sig[order[tk - 1]] > 0.0)) --tk;
+  *t_out = tk;
+  if (tk > tcap) return LYAP_ERR_TCAP;
+  std::vector<double> sc(2 * (size_t)tmax, 0.0);
+  for (int c = 0; c < tk; ++c) {
+    const double sg = sig[order[c]];
+    sc[c] = 1.0 / sqrt(sg);
+    sc[tmax + c] = 1.0 / (sg * sqrt(sg));
+  }
+  if (tk > 0) {
+    LYAP_CUDA_TRY(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * tk, cudaMemcpyHostToDevice, st));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(scl, sc.data(), sizeof(double) * 2 * tmax, cudaMemcpyHostToDevice, st));
+    // 6. R1 = R_B^T V_G,t Sigma^{-1/2}, R2 = R_A^T (G V_G)_t Sigma^{-3/2}; M1 = (Q L_A) R1, M2 = (P L_B) R2
+    small_gemm(RB, tmax, 1, VG, tmax, 1, order_d, scl, R1, tmax, tpc, tk, f.tcount, st);
+    small_gemm(RA, tmax, 1, Gc, tmax, 1, order_d, scl + tmax, R2, tmax, tpc, tk, f.tcount, st);
+    small_gemm(f.B, tmax, 0, R1, tmax, 0, nullptr, nullptr, f.M, tmax, N, tk, f.tcount, st);
+    small_gemm(f.B + (size_t)N * tmax, tmax, 0, R2, tmax, 0, nullptr, nullptr, f.M + (size_t)N * tmax, tmax, N, tk,
+               f.tcount, st);
+    h->launches += 4;
+  }
+  // 7. second passes: Z1 = V_m M1, Z2 = U_m M2
+  int rc = second_pass(h, 0, f.M, tmax, tk, Z1, ldz1, z_dtype == LYAP_F32, st);
+  if (rc != LYAP_OK) return rc;
+  rc = second_pass(h, 1, f.M + (size_t)N * tmax, tmax, tk, Z2, ldz2, z_dtype == LYAP_F32, st);
+  if (rc != LYAP_OK) return rc;
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // keeps the host vectors alive until the copies ran
+  return LYAP_OK;
+}
+
 int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
                cudaStream_t st) {
-  (void)Z2;
-  (void)ldz2;
+  if (h->plan.sylv) return run_factor_sylv(h, Z1, ldz1, Z2, ldz2, z_dtype, tcap, t_out, st);
   const int s = h->s, m = h->m, N = s * m;
-  if (h->plan.sylv) return LYAP_ERR_ARG;
   const int nmax = h->plan.nmax;
   const int tmax = nmax < kTmaxCap ? nmax : kTmaxCap;
   FactorWs f = carve(h->factor_ws, s, nmax, tmax, nmax);
@@ -504,7 +787,7 @@ int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, i
   k_apply_lpp<<<(N + 127) / 128, 128, 0, st>>>(f, N, N, tmax);
   h->launches += 2;
   // 4. K = L^T L and its eigendecomposition (eigenpairs of L L^T)
-  k_gram_L<<<dim3(tpc, (tpc + 127) / 128), 128, 0, st>>>(f, N, tmax);
+  k_gram_L<<<dim3(tpc, (tpc + 127) / 128), 128, 0, st>>>(f, N, 0, N, tmax, f.K);
   k_jacobi<<<1, 1024, 0, st>>>(f, tmax);
   h->launches += 2;
   std::vector<double> ev(tpc);
