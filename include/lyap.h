@@ -187,6 +187,60 @@ int lyap_residual_noalloc(int s, int m, const double* ab, int ldab, const double
 
 const char* lyap_status_string(int status);
 
+/* ---- batched solves ------------------------------------------------------------------
+ * Many independent Lyapunov equations A_b X + X A_b + C_b C_b^T = 0 (b < count) of uneven
+ * size and block size, solved together: every block Lanczos sweep (Alg. 2 with CholQR2) of all
+ * instances with the same s is one persistent launch over a list of row tiles of all of them,
+ * one iteration of all groups is replayed from a CUDA graph, and the convergence checks
+ * (Prop. 3.1, Alg. 3) of the instances run on several streams.  Each instance follows the
+ * same method and stopping test as a single lyap_solve; its results (history, m, factor)
+ * are read per instance.  The paper treats one equation at a time; the batch is an addition.
+ *  A        : count CSR operators (host or device memory, read during lyap_batch_create)
+ *  C        : count pointers to n_b x s_b row-major fp64 blocks, memory kind c_mem
+ *  s        : count block sizes (1, 2, 3, 4 or 8)
+ *  tol      : count tolerances on ||R||_F / ||C||_F^2
+ *  opt      : shared options (maxit, precision, check_batch, pass2_blocks; sell_sigma must be 1)
+ * The workspace (one caller-owned device buffer, 256-byte aligned) holds every instance's
+ * state plus a few shared scratch pools for the checks and the factor; its size comes from
+ * lyap_batch_workspace_size with the same arguments. */
+typedef struct lyap_batch lyap_batch;
+
+int lyap_batch_workspace_size(int count, const lyap_csr* A, const int* s, const lyap_options* opt,
+                              size_t* bytes);
+int lyap_batch_create(int count, const lyap_csr* A, const double* const* C, int c_mem, const int* s,
+                      const double* tol, const lyap_options* opt, void* workspace, size_t ws_bytes,
+                      void* stream, lyap_batch** out);
+
+/* Solves every instance to its tolerance or maxit.  autotune != 0 first times the batched
+ * sweeps for each block size over a set of row-tile heights and CTAs per SM (by running
+ * iteration 1, which any configuration recomputes identically) and keeps the fastest;
+ * otherwise the previous choice, or the default (4096 rows, full occupancy), is used.
+ * Returns LYAP_OK when every instance converged, LYAP_NOT_CONVERGED when some reached
+ * maxit, or the first error status of an instance (per-instance statuses: lyap_batch_status). */
+int lyap_batch_solve(lyap_batch* b, int autotune, void* stream);
+
+/* status[i] and m[i] (iterations) of every instance after lyap_batch_solve (either may be NULL). */
+int lyap_batch_status(lyap_batch* b, int* status, int* m);
+
+/* Relative residual history of instance i (as lyap_residual_norm). */
+int lyap_batch_residual_norm(lyap_batch* b, int i, double* hist_host, int cap, int* m_out);
+
+/* Low-rank factor of instance i into device memory Z (n_i x tcap row-major, leading dimension
+ * ldz >= tcap), as lyap_factor; instances are factored one call at a time. */
+int lyap_batch_factor(lyap_batch* b, int i, void* Z, int64_t ldz, int z_dtype, int tcap, int* t_out,
+                      void* stream);
+
+/* Chosen sweep configuration per block-size group: out[3g] = s, out[3g+1] = rows per tile,
+ * out[3g+2] = CTAs per SM; returns the number of groups written. */
+int lyap_batch_tuning(lyap_batch* b, int* out, int cap);
+
+/* out[0] create ms, [1] solve ms, [2] Lanczos sweep ms (graph replays), [3] check ms,
+ * [4] instance-iterations run, [5] kernels launched (graph replays count their kernels),
+ * [6] graph replays. */
+int lyap_batch_phase_times(lyap_batch* b, double* out, int cap);
+
+int lyap_batch_destroy(lyap_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

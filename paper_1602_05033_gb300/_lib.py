@@ -41,6 +41,15 @@ EXPORTED = (
     "lyap_destroy",
     "lyap_status_string",
     "lyap_residual_noalloc",
+    "lyap_batch_workspace_size",
+    "lyap_batch_create",
+    "lyap_batch_solve",
+    "lyap_batch_status",
+    "lyap_batch_residual_norm",
+    "lyap_batch_factor",
+    "lyap_batch_tuning",
+    "lyap_batch_phase_times",
+    "lyap_batch_destroy",
 )
 
 
@@ -105,6 +114,18 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_phase_times.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int]
     lib.lyap_destroy.argtypes = [P]
     lib.lyap_residual_noalloc.argtypes = [ct.c_int, ct.c_int, P, ct.c_int, P, P, ct.c_double, P, P, P]
+    CSRP = ct.POINTER(lyap_csr)
+    IP = ct.POINTER(ct.c_int)
+    lib.lyap_batch_workspace_size.argtypes = [ct.c_int, CSRP, IP, ct.POINTER(lyap_options), ct.POINTER(ct.c_size_t)]
+    lib.lyap_batch_create.argtypes = [ct.c_int, CSRP, ct.POINTER(ct.c_void_p), ct.c_int, IP, ct.POINTER(ct.c_double),
+                                      ct.POINTER(lyap_options), P, ct.c_size_t, P, ct.POINTER(P)]
+    lib.lyap_batch_solve.argtypes = [P, ct.c_int, P]
+    lib.lyap_batch_status.argtypes = [P, IP, IP]
+    lib.lyap_batch_residual_norm.argtypes = [P, ct.c_int, ct.POINTER(ct.c_double), ct.c_int, IP]
+    lib.lyap_batch_factor.argtypes = [P, ct.c_int, P, ct.c_int64, ct.c_int, ct.c_int, IP, P]
+    lib.lyap_batch_tuning.argtypes = [P, IP, ct.c_int]
+    lib.lyap_batch_phase_times.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int]
+    lib.lyap_batch_destroy.argtypes = [P]
     lib.lyap_status_string.argtypes = [ct.c_int]
     lib.lyap_status_string.restype = ct.c_char_p
     for name in EXPORTED:
@@ -205,6 +226,84 @@ def lyap_residual_noalloc(s: int, m: int, ab_ptr: int, ldab: int, gamma_ptr: int
                                       ct.c_void_p(stream))
     if st != LYAP_OK:
         raise LyapError(st, "lyap_residual_noalloc")
+
+
+def _arr(ctype, vals):
+    return (ctype * len(vals))(*vals)
+
+
+def lyap_batch_workspace_size(csrs, s, opt) -> int:
+    nb = ct.c_size_t(0)
+    st = load().lyap_batch_workspace_size(len(csrs), _arr(lyap_csr, csrs), _arr(ct.c_int, s),
+                                          ct.byref(opt) if opt is not None else None, ct.byref(nb))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_batch_workspace_size")
+    return int(nb.value)
+
+
+def lyap_batch_create(csrs, c_ptrs, c_mem: int, s, tol, opt, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ct.c_void_p(0)
+    st = load().lyap_batch_create(len(csrs), _arr(lyap_csr, csrs), _arr(ct.c_void_p, c_ptrs), int(c_mem),
+                                  _arr(ct.c_int, s), _arr(ct.c_double, tol),
+                                  ct.byref(opt) if opt is not None else None, ct.c_void_p(ws_ptr),
+                                  ct.c_size_t(ws_bytes), ct.c_void_p(stream), ct.byref(h))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_batch_create")
+    return h.value
+
+
+def lyap_batch_solve(b: int, autotune: bool, stream: int) -> int:
+    st = load().lyap_batch_solve(ct.c_void_p(b), int(bool(autotune)), ct.c_void_p(stream))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_batch_solve")
+    return st
+
+
+def lyap_batch_status(b: int, count: int):
+    stt = (ct.c_int * count)()
+    m = (ct.c_int * count)()
+    st = load().lyap_batch_status(ct.c_void_p(b), stt, m)
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_batch_status")
+    return list(stt), list(m)
+
+
+def lyap_batch_residual_norm(b: int, i: int, cap: int):
+    import numpy as np
+
+    buf = np.full(max(cap, 1), np.nan)
+    m = ct.c_int(0)
+    st = load().lyap_batch_residual_norm(ct.c_void_p(b), int(i), buf.ctypes.data_as(ct.POINTER(ct.c_double)), int(cap),
+                                         ct.byref(m))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_batch_residual_norm")
+    return buf[: m.value].copy(), m.value
+
+
+def lyap_batch_factor(b: int, i: int, Z_ptr: int, ldz: int, z_dtype: int, tcap: int, stream: int) -> int:
+    t = ct.c_int(0)
+    st = load().lyap_batch_factor(ct.c_void_p(b), int(i), ct.c_void_p(Z_ptr), ct.c_int64(ldz), int(z_dtype), int(tcap),
+                                  ct.byref(t), ct.c_void_p(stream))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_batch_factor")
+    return t.value
+
+
+def lyap_batch_tuning(b: int):
+    out = (ct.c_int * 48)()
+    n = load().lyap_batch_tuning(ct.c_void_p(b), out, 48)
+    return [tuple(out[3 * g:3 * g + 3]) for g in range(max(n, 0))]
+
+
+def lyap_batch_phase_times(b: int):
+    out = (ct.c_double * 8)()
+    load().lyap_batch_phase_times(ct.c_void_p(b), out, 8)
+    return list(out)
+
+
+def lyap_batch_destroy(b: int) -> None:
+    if b:
+        load().lyap_batch_destroy(ct.c_void_p(b))
 
 
 def lyap_destroy(h: int) -> None:

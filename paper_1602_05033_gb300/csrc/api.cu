@@ -18,7 +18,6 @@ int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col,
 
 namespace {
 
-constexpr int kMaxSweepGrid = 2048;
 
 // one wave of the row sweeps on this device (at least 256 rows per CTA); the reduction
 // order depends on the grid, so results are reproducible run to run on a given GPU model
@@ -68,7 +67,14 @@ size_t staging_bytes(const lyap_csr* A) {
          lyap_align256((int64_t)(vw * A->nnz));
 }
 
-int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p) {
+}  // namespace
+
+lyap_options resolve_options(const lyap_options* opt) { return resolve(opt); }
+int valid_block(int s) { return valid_s(s); }
+int validate_csr(const lyap_csr* A) { return check_csr(A); }
+
+// external: the check slots, factor scratch and host staging of Z are lent by a caller (a batch)
+int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external) {
   p.s = s;
   p.sylv = B != nullptr;
   p.bulk_f32 = o.precision == LYAP_PREC_MIXED;
@@ -113,6 +119,15 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
   p.flags = take(256);
   p.chk_err = take(sizeof(int) * (size_t)o.maxit);
   // the check slots hold per-eigenpair fp64 scratch (O(nmax^2) each): cap their total at 16 GiB
+  if (external) {
+    p.check_batch = 1;
+    p.check_bytes = 0;
+    p.factor_bytes = factor_ws_bytes(s, p.nmax, p.sylv);  // lent: the pass-2 buffers follow it
+    p.staging_bytes = staging_bytes(A) + staging_bytes(B);
+    p.staging = take(p.staging_bytes);
+    p.total = off;
+    return LYAP_OK;
+  }
   {
     const size_t per = (size_t)(1 + p.sylv) * check_slot_bytes(s, p.nmax);
     const size_t cap = (size_t)16 << 30;
@@ -130,6 +145,8 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
   p.total = off;
   return LYAP_OK;
 }
+
+namespace {
 
 template <typename T>
 T* at(char* ws, size_t off) {
@@ -201,15 +218,18 @@ int lyap_workspace_size(const lyap_csr* A, const lyap_csr* B, int s, const lyap_
   lyap_options o = resolve(opt);
   if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
   Plan p;
-  rc = make_plan(A, B, s, o, p);
+  rc = make_plan(A, B, s, o, p, 0);
   if (rc != LYAP_OK) return rc;
   *bytes = p.total;
   return LYAP_OK;
 }
 
-int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
-                double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream,
-                lyap_handle** out) {
+}  // extern "C"
+
+// lyap_create's work; external = 1 leaves the check, factor and Z staging areas to the caller
+int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
+                  double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream, int external,
+                  lyap_handle** out) {
   if (!out || !valid_s(s) || !C1 || !(tol >= 0.0)) return LYAP_ERR_ARG;
   if ((B == nullptr) != (C2 == nullptr)) return LYAP_ERR_ARG;
   if (c_mem != LYAP_MEM_DEVICE && c_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
@@ -219,7 +239,7 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
   lyap_options o = resolve(opt);
   if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
   Plan p;
-  rc = make_plan(A, B, s, o, p);
+  rc = make_plan(A, B, s, o, p, external);
   if (rc != LYAP_OK) return rc;
   if (!workspace || ws_bytes < p.total || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LYAP_ERR_WORKSPACE;
   *out = nullptr;
@@ -313,15 +333,63 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
   return LYAP_OK;
 }
 
+// resets the history and flags and builds V_1 (CholQR2 of C) for every operator
+void solve_begin(lyap_handle* h, cudaStream_t st) {
+  const Plan& p = h->plan;
+  k_init_flags<<<(p.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, h->chk_err, p.maxit);
+  h->launches += 1;
+  for (int k = 0; k < 1 + p.sylv; ++k)
+    h->launches += launch_init_block(h->op[k], h->s, p.bulk_f32, p.sweep_grid, h->flags, st);
+}
+
+// records the outcome of a solve (m, convergence, iterations run), copies the history to
+// the host and reads beta for the factor; records ev[1] and synchronises the stream
+int solve_end(lyap_handle* h, int done, int m_final, int result, cudaStream_t st) {
+  const Plan& p = h->plan;
+  h->m = m_final;
+  h->converged = result == LYAP_OK;
+  h->lanczos_done = done;
+  h->solved = 1;
+  h->factored = 0;
+  h->op[0].beta = 0.0;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(h->hist_host, h->hist, sizeof(double) * p.maxit, cudaMemcpyDeviceToHost, st));
+  double betas[2] = {0.0, 0.0};
+  for (int k = 0; k < 1 + p.sylv; ++k)
+    LYAP_CUDA_TRY(
+        cudaMemcpyAsync(&betas[k], h->op[k].log + REC_TDIAG * h->s * h->s, sizeof(double), cudaMemcpyDeviceToHost, st));
+  cudaEventRecord(h->ev[1], st);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < 1 + p.sylv; ++k) h->op[k].beta = betas[k];
+  return LYAP_OK;
+}
+
+// status of a check round: error bits, or the first failed check before the first converged m
+int round_status(lyap_handle* h) {
+  int rc = status_from_bits(h->flags_host[0]);
+  if (rc == LYAP_OK && h->flags_host[2] < h->flags_host[1]) {
+    int eb = 0;
+    LYAP_CUDA_TRY(cudaMemcpy(&eb, h->chk_err + h->flags_host[2] - 1, sizeof(int), cudaMemcpyDeviceToHost));
+    rc = status_from_bits(eb);
+    if (rc == LYAP_OK) rc = LYAP_ERR_EIGEN;
+  }
+  return rc;
+}
+
+extern "C" {
+
+int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
+                double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream,
+                lyap_handle** out) {
+  return create_handle(A, B, C1, C2, c_mem, s, tol, opt, workspace, ws_bytes, stream, 0, out);
+}
+
 int lyap_solve(lyap_handle* h, void* stream) {
   if (!h) return LYAP_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan& p = h->plan;
   const int s = h->s;
   cudaEventRecord(h->ev[0], st);
-  k_init_flags<<<(p.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, h->chk_err, p.maxit);
-  h->launches += 1;
-  for (int k = 0; k < 1 + p.sylv; ++k) h->launches += launch_init_block(h->op[k], s, p.bulk_f32, p.sweep_grid, h->flags, st);
+  solve_begin(h, st);
   int done = 0;        // Lanczos iterations completed (blocks V_1..V_{done+1} exist)
   int checked = 0;     // largest m already checked
   int chunk = std::min(4, p.check_batch_req);
@@ -355,15 +423,8 @@ int lyap_solve(lyap_handle* h, void* stream) {
     cudaEventElapsedTime(&b, h->ev[3], h->ev[4]);
     t_lanczos += a;
     t_check += b;
-    const int bits = h->flags_host[0];
-    int rc = status_from_bits(bits);
-    if (rc == LYAP_OK && h->flags_host[2] < h->flags_host[1]) {
-      // a check failed before (or without) convergence: that failure is the result
-      int eb = 0;
-      LYAP_CUDA_TRY(cudaMemcpy(&eb, h->chk_err + h->flags_host[2] - 1, sizeof(int), cudaMemcpyDeviceToHost));
-      rc = status_from_bits(eb);
-      if (rc == LYAP_OK) rc = LYAP_ERR_EIGEN;
-    }
+    // a check that failed before (or without) convergence is the result
+    int rc = round_status(h);
     if (rc != LYAP_OK) {
       h->solved = 0;
       return rc;
@@ -376,19 +437,8 @@ int lyap_solve(lyap_handle* h, void* stream) {
     if (done >= p.maxit) break;
     chunk = std::min(2 * chunk, p.check_batch_req);
   }
-  h->m = m_final;
-  h->converged = result == LYAP_OK;
-  h->lanczos_done = done;
-  h->solved = 1;
-  h->factored = 0;
-  h->op[0].beta = 0.0;
-  LYAP_CUDA_TRY(cudaMemcpyAsync(h->hist_host, h->hist, sizeof(double) * p.maxit, cudaMemcpyDeviceToHost, st));
-  double betas[2] = {0.0, 0.0};
-  for (int k = 0; k < 1 + p.sylv; ++k)
-    LYAP_CUDA_TRY(cudaMemcpyAsync(&betas[k], h->op[k].log + REC_TDIAG * s * s, sizeof(double), cudaMemcpyDeviceToHost, st));
-  cudaEventRecord(h->ev[1], st);
-  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
-  for (int k = 0; k < 1 + p.sylv; ++k) h->op[k].beta = betas[k];
+  int rc_end = solve_end(h, done, m_final, result, st);
+  if (rc_end != LYAP_OK) return rc_end;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
   h->times_ms[1] = ms;

@@ -319,7 +319,7 @@ __global__ void k_bisect32(CheckArgs g) {
 }
 
 // 2b. per-estimate cluster tolerance: members of fp32 clusters larger than kRefineAt get the
-// fp64 tolerance 8 sqrt(N) eps64 ||T|| (and are refined by 2c), all others the fp32 one
+// fp64 grouping tolerance (and are refined by 2c), all others the fp32 one
 __global__ void k_mark_refine(CheckArgs g) {
   const int c_idx = blockIdx.x;
   const int m = g.m_lo + c_idx;
@@ -328,7 +328,12 @@ __global__ void k_mark_refine(CheckArgs g) {
   Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
   const double tol32 = sl.hdr[4];
   const double span = fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
-  const double tol64 = 8.0 * sqrt((double)N) * DBL_EPSILON * sl.hdr[3] * span;
+  // refined estimates are accurate to a few eps64 ||T||; they are grouped at 1e-7 ||T|| (at
+  // least 8 sqrt(N) eps64 ||T||), far above the splitting of near-degenerate eigenvalues by the
+  // recurrence's rounding (~1e-10 ||T||), so such eigenvalues stay in one group whose subspace
+  // converges fast, while groups stay far below the fp32 tolerance (~1e-6 ||T|| and more)
+  const double tnorm = sl.hdr[3] * span;
+  const double tol64 = fmax(8.0 * sqrt((double)N) * DBL_EPSILON * tnorm, 1e-7 * tnorm);
   if (threadIdx.x == 0) sl.hdr[6] = tol64;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     if (i > 0 && sl.est[i] - sl.est[i - 1] <= tol32) continue;
@@ -415,13 +420,13 @@ __global__ void k_refine64(CheckArgs g) {
 }
 
 __device__ inline double hash_unit(unsigned int k, unsigned int i) {
-  unsigned int x = k * 0x9E3779B1u ^ (i + 0x7F4A7C15u) * 0x85EBCA77u;
-  x ^= x >> 15;
-  x *= 0x2C1B3C6Du;
-  x ^= x >> 12;
-  x *= 0x297A2D39u;
-  x ^= x >> 15;
-  return (double)(x & 0xFFFFFF) / (double)0x800000 - 1.0;  // in [-1, 1)
+  // splitmix64 (Steele, Lea and Flood's mixing function) of the key (i, k): start vectors with
+  // no structure along the rows, so no eigenvector of T_m is nearly missing from them
+  unsigned long long z = ((unsigned long long)i << 32 | k) + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-52 - 1.0;  // in [-1, 1)
 }
 
 // the per-eigenvalue scratch (U rows, vector entries) is far larger than L2, so every
@@ -709,16 +714,19 @@ __device__ double lane_res2(const double* __restrict__ Tb, int N, const double* 
   return r2;
 }
 
-// 3b. groups of close estimates, one warp each: lane v iterates member v at its own shift; the
-// warp re-orthonormalises (MGS, twice) after every step and splits the group by Rayleigh-Ritz
-// between rounds, so the vectors of near-equal eigenvalues stay orthonormal.  The members'
-// vectors live contiguously in Xc (member i at Xc + i nmax), so the warp's row loops coalesce.
+// 3b. groups of close estimates, one warp each: lane v iterates member v with its own estimate
+// as a fixed shift (a Rayleigh-quotient shift could carry the last member to the eigenvalue
+// just outside the group); the warp re-orthonormalises (MGS, twice) after every step and splits
+// the group by Rayleigh-Ritz between rounds, so the vectors of near-equal eigenvalues stay
+// orthonormal.  The members' vectors live contiguously in Xc (member i at Xc + i nmax), so the
+// warp's row loops coalesce.
 template <int S>
 __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   constexpr int WPB = 4;
   __shared__ double Hs[WPB][kMaxCluster][kMaxCluster];
   __shared__ double Vs[WPB][kMaxCluster][kMaxCluster];
   __shared__ double sh[WPB][kMaxCluster];
+  __shared__ double th[WPB][kMaxCluster];
   __shared__ int ords[WPB][kMaxCluster];
   const int c_idx = blockIdx.y;
   const int m = g.m_lo + c_idx;
@@ -733,6 +741,7 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   double (*H)[kMaxCluster] = Hs[w];
   double (*V)[kMaxCluster] = Vs[w];
   double* shift = sh[w];
+  double* theta = th[w];
   int* ord = ords[w];
   for (int e = blockIdx.x * WPB + w; e < ncl; e += gridDim.x * WPB) {
     const int i = sl.clist[2 + 2 * e], c = sl.clist[3 + 2 * e];
@@ -742,8 +751,22 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
       for (int k = lane; k < N; k += 32) xc[(size_t)v * ld + k] = hash_unit((unsigned)k, (unsigned)(i + v));
     __syncwarp();
     bool done = false;
-    for (int round = 0; round < kMaxRounds && !done; ++round) {
-      for (int it = 0; it < 2; ++it) {
+#ifdef LYAP_DEBUG
+    double dbg_res[kMaxRounds] = {0, 0, 0, 0};
+#endif
+    // rounds at the fixed shifts until every member's residual passes, then one polishing round
+    // at the Ritz values (Rayleigh-quotient shifts once the subspace is right)
+    bool polish = false;
+    for (int round = 0; round < kMaxRounds + 1; ++round) {
+      if (done) {
+        if (polish) break;
+        polish = true;
+        if (lane < c) shift[lane] = theta[lane];
+        __syncwarp();
+      } else if (round == kMaxRounds) {
+        break;
+      }
+      for (int it = 0; it < (polish ? 1 : 2); ++it) {
         if (lane < c) solve1<S>(sl.Tb, N, shift[lane], tiny, 1.0, xc + (size_t)lane * ld, 1, 0, sl.U, i + lane, ld);
         __syncwarp();
         for (int pass = 0; pass < 2; ++pass)
@@ -817,7 +840,7 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
           }
           ord[b + 1] = t;
         }
-        for (int v = 0; v < c; ++v) shift[v] = H[ord[v]][ord[v]];
+        for (int v = 0; v < c; ++v) theta[v] = H[ord[v]][ord[v]];
       }
       __syncwarp();
       for (int k = lane; k < N; k += 32) {
@@ -831,12 +854,15 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
         for (int v = 0; v < c; ++v) xc[(size_t)v * ld + k] = out[v];
       }
       __syncwarp();
-      if (round == 0) continue;
+      if (round == 0 || polish) continue;
       // converged once every member's residual passes
       bool ok = true;
       for (int v = 0; v < c; ++v) {
-        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xc + (size_t)v * ld, shift[v], lane));
+        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xc + (size_t)v * ld, theta[v], lane));
         ok = ok && sqrt(r2) <= kResTol * tnorm;
+#ifdef LYAP_DEBUG
+        dbg_res[round] = fmax(dbg_res[round], sqrt(r2));
+#endif
       }
       done = ok;
     }
@@ -856,7 +882,11 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
         if (!(sqrt(r2) <= kResTol * tnorm) || !isfinite(num) || !inside) {
           atomicOr(g.chk_err + m - 1, DERR_EIGEN);
 #ifdef LYAP_DEBUG
-          printf("eig fail m=%d N=%d i=%d c=%d v=%d rq=%.17g res=%.3e tnorm=%.3e\n", m, N, i, c, v, num, sqrt(r2), tnorm);
+          printf("eig fail m=%d N=%d i=%d c=%d v=%d rq=%.17g res=%.3e tnorm=%.3e est[i-1..i+c]=%.6f %.6f %.6f %.6f etol=%.4g "
+                 "rounds %.3e %.3e %.3e %.3e shifts %.6f %.6f theta %.6f %.6f\n",
+                 m, N, i, c, v, num, sqrt(r2), tnorm, i > 0 ? sl.est[i - 1] : 0.0, sl.est[i], sl.est[i + c - 1],
+                 i + c < N ? sl.est[i + c] : 0.0, sl.etol[i], dbg_res[0], dbg_res[1], dbg_res[2], dbg_res[3],
+                 shift[0], shift[c - 1], theta[0], theta[c - 1]);
 #endif
         }
       }

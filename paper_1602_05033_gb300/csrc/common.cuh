@@ -81,7 +81,8 @@ struct Plan {
     size_t slice_ptr, slice_w, sell_col, sell_val, perm, V[3], W, C, log, partials, counter;
     int64_t n, nslices, sell_nnz;
   } op[2];
-  size_t hist, flags, chk_err, check, check_bytes, factor, factor_bytes, zstage, staging, staging_bytes;
+  size_t hist = 0, flags = 0, chk_err = 0, check = 0, check_bytes = 0, factor = 0, factor_bytes = 0, zstage = 0,
+         staging = 0, staging_bytes = 0;
 };
 
 // per-check scratch (fp64 unless noted), one slot per check in a batch
@@ -125,6 +126,23 @@ struct lyap_handle {
   int64_t launches = 0;          // kernels launched since lyap_create
 };
 
+// CTAs (or row tiles) of one sweep over one operator: the size of its partials area
+constexpr int kMaxSweepGrid = 2048;
+
+// ---- batched solves: per-instance state and row tiles (device resident) --------
+struct BInst {
+  OpDev op;       // the instance's operator (its log, ring blocks, partials and counter)
+  int* flags;     // its error bits
+  int* step;      // [0] next iteration j (1-based), [1] 1 while the instance iterates
+  int ntiles;     // tiles of this instance in its group's list
+  int maxit;
+};
+struct BTile {
+  int inst;       // index into the BInst array
+  int local;      // tile index within the instance (its partials slot)
+  int64_t lo, hi; // rows [lo, hi), lo a multiple of the SELL slice height
+};
+
 // ---- launch helpers implemented in the .cu files --------------------------
 // sell.cu
 int sell_plan_host(const lyap_csr* A, int sigma, int64_t* nslices, int64_t* sell_nnz);
@@ -134,12 +152,29 @@ int max_nacc(int s);
 int sweep_blocks_per_sm(int s, int bulk_f32);
 int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
 int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
+int launch_batch_step(int s, int bulk_f32, const BInst* d_inst, const BTile* d_tiles, int ntiles, int grid,
+                      cudaStream_t st);
+int batch_blocks_per_sm(int s, int bulk_f32);
 
 // check.cu
 int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st);
 int launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st);
 
+// api.cu (used by the batched solver)
+lyap_options resolve_options(const lyap_options* opt);
+int valid_block(int s);
+int validate_csr(const lyap_csr* A);
+int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
+                  double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream, int external,
+                  lyap_handle** out);
+int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external);
+void solve_begin(lyap_handle* h, cudaStream_t st);
+int solve_end(lyap_handle* h, int done, int m_final, int result, cudaStream_t st);
+int round_status(lyap_handle* h);
+
 // factor.cu
+size_t factor_ws_bytes(int s, int nmax, int sylv);
+size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32);
 int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
                cudaStream_t st);
 

@@ -214,7 +214,8 @@ __device__ void load_coefs(Coefs<T, S>& co, const double* __restrict__ rec, int 
 // ---- deterministic block reduction + last-CTA finalisation ------------------------
 template <typename Acc, int NACC>
 __device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials, unsigned int* counter,
-                                double* __restrict__ tot /*smem NACC*/, double* __restrict__ scratch /*smem kWarps*NACC*/) {
+                                double* __restrict__ tot /*smem NACC*/, double* __restrict__ scratch /*smem kWarps*NACC*/,
+                                unsigned int slot, unsigned int count) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NACC; ++k) {
@@ -227,20 +228,20 @@ __device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials,
   for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
     double t = 0.0;
     for (int w = 0; w < kWarps; ++w) t += scratch[w * NACC + k];
-    partials[(size_t)blockIdx.x * NACC + k] = t;
+    partials[(size_t)slot * NACC + k] = t;
   }
   __threadfence();
   __shared__ unsigned int ticket;
   __syncthreads();
   if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
   __syncthreads();
-  if (ticket != gridDim.x - 1) return false;
+  if (ticket != count - 1) return false;
   __threadfence();
   // warp w sums coefficients k = w, w + kWarps, ...; its lanes stride over the CTAs and
   // combine in a fixed shuffle order, so the result does not depend on timing
   for (int k = warp; k < NACC; k += kWarps) {
     double t = 0.0;
-    for (unsigned int b = lane; b < gridDim.x; b += 32) t += __ldcg(partials + (size_t)b * NACC + k);
+    for (unsigned int b = lane; b < count; b += 32) t += __ldcg(partials + (size_t)b * NACC + k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) tot[k] = t;
@@ -283,6 +284,80 @@ __device__ bool all_finite(const double* A, int n) {
   for (int i = 0; i < n; ++i)
     if (!isfinite(A[i])) return false;
   return true;
+}
+
+// ---- per-iteration finalisations (one thread, after the reduction) -------------
+// S1: alpha_{j-1} = V_{j-1}^T W, alpha_j = V_j^T W - (V_j^T V_{j-1}) alpha_{j-1}
+template <int S>
+__device__ void finalize_s1(double* rec, const double* tot, int has_prev, int* flags) {
+  constexpr int SS = S * S;
+  double ap[SS], ad[SS], cr[SS], t[SS];
+  for (int k = 0; k < SS; ++k) {
+    ap[k] = has_prev ? tot[k] : 0.0;
+    cr[k] = has_prev ? tot[2 * SS + k] : 0.0;
+  }
+  matmul<S>(cr, ap, t);
+  for (int k = 0; k < SS; ++k) ad[k] = tot[SS + k] - t[k];
+  for (int k = 0; k < SS; ++k) {
+    rec[REC_APREV * SS + k] = ap[k];
+    rec[REC_ADIAG * SS + k] = ad[k];
+    rec[REC_CROSS * SS + k] = cr[k];
+  }
+  if (!all_finite<S>(ad, SS) || !all_finite<S>(ap, SS)) atomicOr(flags, DERR_NONFINITE);
+}
+
+// S2: second MGS coefficients, combined tau_{j-1,j}, tau_jj, and R1 = chol(G1)
+template <int S>
+__device__ void finalize_s2(double* rw, const double* tot, int hp, int* flags) {
+  constexpr int SS = S * S;
+  double bp[SS], bd[SS], cr[SS], t[SS], G[SS], R1[SS];
+  for (int k = 0; k < SS; ++k) {
+    bp[k] = hp ? tot[k] : 0.0;
+    cr[k] = rw[REC_CROSS * SS + k];
+  }
+  matmul<S>(cr, bp, t);
+  for (int k = 0; k < SS; ++k) bd[k] = tot[SS + k] - t[k];
+  // G1 = w1^T w1 - bp^T bp - bd^T bd: Gram of w2 = w1 - V beta (V orthonormal up to rounding)
+  for (int a = 0, e = 2 * SS; a < S; ++a)
+    for (int b = a; b < S; ++b, ++e) {
+      double v = tot[e];
+      for (int k = 0; k < S; ++k) v -= bp[k * S + a] * bp[k * S + b] + bd[k * S + a] * bd[k * S + b];
+      G[a * S + b] = v;
+      G[b * S + a] = v;
+    }
+  for (int k = 0; k < SS; ++k) {
+    rw[REC_BPREV * SS + k] = bp[k];
+    rw[REC_BDIAG * SS + k] = bd[k];
+    rw[REC_TPREV * SS + k] = rw[REC_APREV * SS + k] + bp[k];
+    rw[REC_TDIAG * SS + k] = rw[REC_ADIAG * SS + k] + bd[k];
+  }
+  const bool finite = all_finite<S>(G, SS);
+  if (!finite) atomicOr(flags, DERR_NONFINITE);
+  if (!chol_upper<S>(G, R1)) {
+    if (finite) atomicOr(flags, DERR_BREAKDOWN);
+    for (int k = 0; k < SS; ++k) R1[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
+  }
+  for (int k = 0; k < SS; ++k) rw[REC_R1 * SS + k] = R1[k];
+}
+
+// S3: R2 = chol(x^T x), tau_{j+1,j} = R2 R1
+template <int S>
+__device__ void finalize_s3(double* rw, const double* tot, int* flags) {
+  constexpr int SS = S * S;
+  double G[SS], R2[SS], R1[SS], Tn[SS];
+  for (int a = 0; a < S; ++a)
+    for (int b = 0; b < S; ++b) G[a * S + b] = 0.5 * (tot[a * S + b] + tot[b * S + a]);
+  if (!chol_upper<S>(G, R2)) {
+    atomicOr(flags, all_finite<S>(G, SS) ? DERR_BREAKDOWN : DERR_NONFINITE);
+    for (int k = 0; k < SS; ++k) R2[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
+  }
+  for (int k = 0; k < SS; ++k) R1[k] = rw[REC_R1 * SS + k];
+  matmul<S>(R2, R1, Tn);
+  for (int k = 0; k < SS; ++k) {
+    rw[REC_R2 * SS + k] = R2[k];
+    rw[REC_TNEXT * SS + k] = Tn[k];
+  }
+  if (!all_finite<S>(Tn, SS)) atomicOr(flags, DERR_NONFINITE);
 }
 
 // ---- sweep kernels -----------------------------------------------------------
@@ -337,24 +412,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_spmm_proj(Swe
   }
   __shared__ double tot[NACC];
   __shared__ double scratch[kWarps * NACC];
-  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
-  if (threadIdx.x == 0) {
-    constexpr int SS = S * S;
-    double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
-    double ap[SS], ad[SS], cr[SS], t[SS];
-    for (int k = 0; k < SS; ++k) {
-      ap[k] = g.has_prev ? tot[k] : 0.0;
-      cr[k] = g.has_prev ? tot[2 * SS + k] : 0.0;
-    }
-    matmul<S>(cr, ap, t);
-    for (int k = 0; k < SS; ++k) ad[k] = tot[SS + k] - t[k];
-    for (int k = 0; k < SS; ++k) {
-      rec[REC_APREV * SS + k] = ap[k];
-      rec[REC_ADIAG * SS + k] = ad[k];
-      rec[REC_CROSS * SS + k] = cr[k];
-    }
-    if (!all_finite<S>(ad, SS) || !all_finite<S>(ap, SS)) atomicOr(g.flags, DERR_NONFINITE);
-  }
+  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch, blockIdx.x, gridDim.x)) return;
+  if (threadIdx.x == 0) finalize_s1<S>(g.op.log + (size_t)g.j * LOG_NREC * S * S, tot, g.has_prev, g.flags);
 }
 
 // S2: second MGS projections + first Gram
@@ -399,38 +458,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_proj2_gram1(S
   }
   __shared__ double tot[NACC];
   __shared__ double scratch[kWarps * NACC];
-  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
-  if (threadIdx.x == 0) {
-    double* rw = g.op.log + (size_t)g.j * LOG_NREC * SS;
-    double bp[SS], bd[SS], cr[SS], t[SS], G[SS], R1[SS];
-    for (int k = 0; k < SS; ++k) {
-      bp[k] = hp ? tot[k] : 0.0;
-      cr[k] = rw[REC_CROSS * SS + k];
-    }
-    matmul<S>(cr, bp, t);
-    for (int k = 0; k < SS; ++k) bd[k] = tot[SS + k] - t[k];
-    // G1 = w1^T w1 - bp^T bp - bd^T bd: Gram of w2 = w1 - V beta (V orthonormal up to rounding)
-    for (int a = 0, e = 2 * SS; a < S; ++a)
-      for (int b = a; b < S; ++b, ++e) {
-        double v = tot[e];
-        for (int k = 0; k < S; ++k) v -= bp[k * S + a] * bp[k * S + b] + bd[k * S + a] * bd[k * S + b];
-        G[a * S + b] = v;
-        G[b * S + a] = v;
-      }
-    for (int k = 0; k < SS; ++k) {
-      rw[REC_BPREV * SS + k] = bp[k];
-      rw[REC_BDIAG * SS + k] = bd[k];
-      rw[REC_TPREV * SS + k] = rw[REC_APREV * SS + k] + bp[k];
-      rw[REC_TDIAG * SS + k] = rw[REC_ADIAG * SS + k] + bd[k];
-    }
-    const bool finite = all_finite<S>(G, SS);
-    if (!finite) atomicOr(g.flags, DERR_NONFINITE);
-    if (!chol_upper<S>(G, R1)) {
-      if (finite) atomicOr(g.flags, DERR_BREAKDOWN);
-      for (int k = 0; k < SS; ++k) R1[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
-    }
-    for (int k = 0; k < SS; ++k) rw[REC_R1 * SS + k] = R1[k];
-  }
+  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch, blockIdx.x, gridDim.x)) return;
+  if (threadIdx.x == 0) finalize_s2<S>(g.op.log + (size_t)g.j * LOG_NREC * SS, tot, hp, g.flags);
 }
 
 // S3: second Gram (CholQR2's second pass)
@@ -467,24 +496,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_gram2(SweepAr
   }
   __shared__ double tot[NACC];
   __shared__ double scratch[kWarps * NACC];
-  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
-  if (threadIdx.x == 0) {
-    double* rw = g.op.log + (size_t)g.j * LOG_NREC * SS;
-    double G[SS], R2[SS], R1[SS], Tn[SS];
-    for (int a = 0; a < S; ++a)
-      for (int b = 0; b < S; ++b) G[a * S + b] = 0.5 * (tot[a * S + b] + tot[b * S + a]);
-    if (!chol_upper<S>(G, R2)) {
-      atomicOr(g.flags, all_finite<S>(G, SS) ? DERR_BREAKDOWN : DERR_NONFINITE);
-      for (int k = 0; k < SS; ++k) R2[k] = (k % (S + 1) == 0) ? 1.0 : 0.0;
-    }
-    for (int k = 0; k < SS; ++k) R1[k] = rw[REC_R1 * SS + k];
-    matmul<S>(R2, R1, Tn);
-    for (int k = 0; k < SS; ++k) {
-      rw[REC_R2 * SS + k] = R2[k];
-      rw[REC_TNEXT * SS + k] = Tn[k];
-    }
-    if (!all_finite<S>(Tn, SS)) atomicOr(g.flags, DERR_NONFINITE);
-  }
+  if (!reduce_partials<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch, blockIdx.x, gridDim.x)) return;
+  if (threadIdx.x == 0) finalize_s3<S>(g.op.log + (size_t)g.j * LOG_NREC * SS, tot, g.flags);
 }
 
 // S4: write V_{j+1}
@@ -573,7 +586,7 @@ __global__ void __launch_bounds__(kThreads) k_init_gram(SweepArgs g, int stage) 
   }
   __shared__ double tot[SS];
   __shared__ double scratch[kWarps * SS];
-  if (!reduce_partials<double, SS>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  if (!reduce_partials<double, SS>(acc, g.op.partials, g.op.counter, tot, scratch, blockIdx.x, gridDim.x)) return;
   if (threadIdx.x == 0) {
     double G[SS], R[SS];
     for (int a = 0; a < S; ++a)
@@ -627,6 +640,232 @@ __global__ void __launch_bounds__(kThreads) k_init_write(SweepArgs g) {
     for (int a = 0; a < S; ++a) v[a] = T(w[a]);
     store_row<S>(Vn, g.ldn, row, v);
   }
+}
+
+
+// ---- batched sweeps: many independent instances of one block size per launch ---------
+// A persistent grid walks a list of row tiles (instance, rows [lo, hi)); each tile's CTA
+// reduces its s x s partial sums into the instance's partials slot `local`, and the last tile
+// of an instance to finish (per-instance counter) finalises that instance's coefficients,
+// exactly as the last CTA does for a single instance.  Instances that stopped are skipped.
+struct BatchArgs {
+  const BInst* inst;
+  const BTile* tiles;
+  int ntiles;
+};
+
+template <typename T, int S>
+__device__ __forceinline__ void ring(const BInst& in, int j, const T*& Vp, const T*& Vc, T*& Vn) {
+  Vp = static_cast<const T*>(in.op.V[(j + 1) % 3]);
+  Vc = static_cast<const T*>(in.op.V[(j + 2) % 3]);
+  Vn = static_cast<T*>(in.op.V[j % 3]);
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) kb_spmm_proj(BatchArgs b) {
+  using Acc = typename AccT<T>::type;
+  constexpr int NACC = 3 * S * S;
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const BTile tile = b.tiles[t];
+    const BInst& in = b.inst[tile.inst];
+    const int j = in.step[0];
+    if (!in.step[1]) continue;
+    const bool hp = j > 1;
+    const T *Vp, *Vc;
+    T* Vn;
+    ring<T, S>(in, j, Vp, Vc, Vn);
+    T* W = static_cast<T*>(in.op.W);
+    Acc acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = Acc(0);
+    const int64_t s_lo = tile.lo / LYAP_SLICE, s_hi = (tile.hi + LYAP_SLICE - 1) / LYAP_SLICE;
+    for (int64_t sl = s_lo + warp; sl < s_hi; sl += kWarps) {
+      const int64_t row = sl * LYAP_SLICE + lane;
+      if (row < in.op.n) {
+        T w[S];
+        sell_row<T, S>(in.op, sl, lane, Vc, (int64_t)S, w);
+        store_row<S>(W, (int64_t)S, row, w);
+        T q[S], p[S];
+        load_row<S>(Vc, (int64_t)S, row, q);
+        if (hp) load_row<S>(Vp, (int64_t)S, row, p);
+        else {
+#pragma unroll
+          for (int a = 0; a < S; ++a) p[a] = T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < S; ++a)
+#pragma unroll
+          for (int c = 0; c < S; ++c) {
+            acc[a * S + c] = fma((Acc)p[a], (Acc)w[c], acc[a * S + c]);
+            acc[S * S + a * S + c] = fma((Acc)q[a], (Acc)w[c], acc[S * S + a * S + c]);
+            acc[2 * S * S + a * S + c] = fma((Acc)q[a], (Acc)p[c], acc[2 * S * S + a * S + c]);
+          }
+      }
+    }
+    if (reduce_partials<Acc, NACC>(acc, in.op.partials, in.op.counter, tot, scratch, tile.local, in.ntiles) &&
+        threadIdx.x == 0)
+      finalize_s1<S>(in.op.log + (size_t)j * LOG_NREC * S * S, tot, hp, in.flags);
+    __syncthreads();
+  }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) kb_proj2_gram1(BatchArgs b) {
+  using Acc = typename AccT<T>::type;
+  constexpr int SS = S * S;
+  constexpr int NSYM = S * (S + 1) / 2;
+  constexpr int NACC = 2 * SS + NSYM;
+  __shared__ Coefs<T, S> co;
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const BTile tile = b.tiles[t];
+    const BInst& in = b.inst[tile.inst];
+    const int j = in.step[0];
+    if (!in.step[1]) continue;
+    const bool hp = j > 1;
+    const T *Vp, *Vc;
+    T* Vn;
+    ring<T, S>(in, j, Vp, Vc, Vn);
+    const T* W = static_cast<const T*>(in.op.W);
+    double* rec = in.op.log + (size_t)j * LOG_NREC * SS;
+    load_coefs<T, S>(co, rec, 1);
+    Acc acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = Acc(0);
+    const int64_t hi = tile.hi < in.op.n ? tile.hi : in.op.n;
+    for (int64_t row = tile.lo + threadIdx.x; row < hi; row += blockDim.x) {
+      T w[S], p[S], q[S];
+      load_row<S>(W, (int64_t)S, row, w);
+      load_row<S>(Vc, (int64_t)S, row, q);
+      if (hp) load_row<S>(Vp, (int64_t)S, row, p);
+      else {
+#pragma unroll
+        for (int a = 0; a < S; ++a) p[a] = T(0);
+      }
+      mgs_row<T, S>(p, q, co.ap, co.ad, w, hp);
+#pragma unroll
+      for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+          acc[a * S + c] = fma((Acc)p[a], (Acc)w[c], acc[a * S + c]);
+          acc[SS + a * S + c] = fma((Acc)q[a], (Acc)w[c], acc[SS + a * S + c]);
+        }
+      int e = 2 * SS;
+#pragma unroll
+      for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int c = a; c < S; ++c, ++e) acc[e] = fma((Acc)w[a], (Acc)w[c], acc[e]);
+    }
+    if (reduce_partials<Acc, NACC>(acc, in.op.partials, in.op.counter, tot, scratch, tile.local, in.ntiles) &&
+        threadIdx.x == 0)
+      finalize_s2<S>(rec, tot, hp, in.flags);
+    __syncthreads();
+  }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) kb_gram2(BatchArgs b) {
+  using Acc = typename AccT<T>::type;
+  constexpr int SS = S * S;
+  constexpr int NACC = SS;
+  __shared__ Coefs<T, S> co;
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const BTile tile = b.tiles[t];
+    const BInst& in = b.inst[tile.inst];
+    const int j = in.step[0];
+    if (!in.step[1]) continue;
+    const bool hp = j > 1;
+    const T *Vp, *Vc;
+    T* Vn;
+    ring<T, S>(in, j, Vp, Vc, Vn);
+    const T* W = static_cast<const T*>(in.op.W);
+    double* rec = in.op.log + (size_t)j * LOG_NREC * SS;
+    load_coefs<T, S>(co, rec, 2);
+    Acc acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = Acc(0);
+    const int64_t hi = tile.hi < in.op.n ? tile.hi : in.op.n;
+    for (int64_t row = tile.lo + threadIdx.x; row < hi; row += blockDim.x) {
+      T w[S], p[S], q[S];
+      load_row<S>(W, (int64_t)S, row, w);
+      load_row<S>(Vc, (int64_t)S, row, q);
+      if (hp) load_row<S>(Vp, (int64_t)S, row, p);
+      else {
+#pragma unroll
+        for (int a = 0; a < S; ++a) p[a] = T(0);
+      }
+      mgs_row<T, S>(p, q, co.tp, co.td, w, hp);
+      trsm_row<T, S>(co.r1, co.r1i, w);
+#pragma unroll
+      for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc[a * S + c] = fma((Acc)w[a], (Acc)w[c], acc[a * S + c]);
+    }
+    if (reduce_partials<Acc, NACC>(acc, in.op.partials, in.op.counter, tot, scratch, tile.local, in.ntiles) &&
+        threadIdx.x == 0)
+      finalize_s3<S>(rec, tot, in.flags);
+    __syncthreads();
+  }
+}
+
+// writes V_{j+1}; the last tile of an instance advances its iteration counter (and stops it
+// after maxit iterations)
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) kb_write_next(BatchArgs b) {
+  constexpr int SS = S * S;
+  __shared__ Coefs<T, S> co;
+  __shared__ unsigned int ticket;
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const BTile tile = b.tiles[t];
+    const BInst& in = b.inst[tile.inst];
+    const int j = in.step[0];
+    if (!in.step[1]) continue;
+    const bool hp = j > 1;
+    const T *Vp, *Vc;
+    T* Vn;
+    ring<T, S>(in, j, Vp, Vc, Vn);
+    const T* W = static_cast<const T*>(in.op.W);
+    load_coefs<T, S>(co, in.op.log + (size_t)j * LOG_NREC * SS, 3);
+    const int64_t hi = tile.hi < in.op.n ? tile.hi : in.op.n;
+    for (int64_t row = tile.lo + threadIdx.x; row < hi; row += blockDim.x) {
+      T w[S], p[S], q[S];
+      load_row<S>(W, (int64_t)S, row, w);
+      load_row<S>(Vc, (int64_t)S, row, q);
+      if (hp) load_row<S>(Vp, (int64_t)S, row, p);
+      else {
+#pragma unroll
+        for (int a = 0; a < S; ++a) p[a] = T(0);
+      }
+      next_row<T, S>(co, p, q, w, hp);
+      store_row<S>(Vn, (int64_t)S, row, w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      ticket = atomicAdd(in.op.counter, 1u);
+      if (ticket == (unsigned int)in.ntiles - 1) {
+        *in.op.counter = 0u;
+        in.step[0] = j + 1;
+        if (j + 1 > in.maxit) in.step[1] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int S>
+void batch_step_impl(const BInst* d_inst, const BTile* d_tiles, int ntiles, int grid, cudaStream_t st) {
+  BatchArgs b{d_inst, d_tiles, ntiles};
+  kb_spmm_proj<T, S><<<grid, kThreads, 0, st>>>(b);
+  kb_proj2_gram1<T, S><<<grid, kThreads, 0, st>>>(b);
+  kb_gram2<T, S><<<grid, kThreads, 0, st>>>(b);
+  kb_write_next<T, S><<<grid, kThreads, 0, st>>>(b);
 }
 
 // ---- dispatch ---------------------------------------------------------------
@@ -741,6 +980,41 @@ int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cu
   if (bulk_f32) init_T<float>(op, s, grid, d_flags, st);
   else init_T<double>(op, s, grid, d_flags, st);
   return 3;
+}
+
+int launch_batch_step(int s, int bulk_f32, const BInst* d_inst, const BTile* d_tiles, int ntiles, int grid,
+                      cudaStream_t st) {
+#define LYAP_BS(TT, SS_) batch_step_impl<TT, SS_>(d_inst, d_tiles, ntiles, grid, st)
+  if (bulk_f32) {
+    switch (s) { case 1: LYAP_BS(float, 1); break; case 2: LYAP_BS(float, 2); break; case 3: LYAP_BS(float, 3); break;
+                 case 4: LYAP_BS(float, 4); break; case 8: LYAP_BS(float, 8); break; default: return 0; }
+  } else {
+    switch (s) { case 1: LYAP_BS(double, 1); break; case 2: LYAP_BS(double, 2); break; case 3: LYAP_BS(double, 3); break;
+                 case 4: LYAP_BS(double, 4); break; case 8: LYAP_BS(double, 8); break; default: return 0; }
+  }
+#undef LYAP_BS
+  return 4;
+}
+
+// CTAs of the batched sweep kernels that fit on one SM together
+int batch_blocks_per_sm(int s, int bulk_f32) {
+  int best = 1 << 30;
+  auto q = [&](const void* f) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kThreads, 0) == cudaSuccess && b > 0) best = std::min(best, b);
+  };
+#define LYAP_OCC(TT, SS_)                                                                    \
+  q((const void*)kb_spmm_proj<TT, SS_>); q((const void*)kb_proj2_gram1<TT, SS_>);         \
+  q((const void*)kb_gram2<TT, SS_>); q((const void*)kb_write_next<TT, SS_>)
+  if (bulk_f32) {
+    switch (s) { case 1: LYAP_OCC(float, 1); break; case 2: LYAP_OCC(float, 2); break; case 3: LYAP_OCC(float, 3); break;
+                 case 4: LYAP_OCC(float, 4); break; case 8: LYAP_OCC(float, 8); break; }
+  } else {
+    switch (s) { case 1: LYAP_OCC(double, 1); break; case 2: LYAP_OCC(double, 2); break; case 3: LYAP_OCC(double, 3); break;
+                 case 4: LYAP_OCC(double, 4); break; case 8: LYAP_OCC(double, 8); break; }
+  }
+#undef LYAP_OCC
+  return best == (1 << 30) ? 1 : best;
 }
 
 int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st) {

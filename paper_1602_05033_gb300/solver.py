@@ -143,3 +143,81 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many Lyapunov equations solved together through lyap_batch_create/solve/factor.
+
+    ``problems`` is a list of (A, C) with scipy CSR A and n x s C; all share ``maxit`` and
+    ``precision``; ``tol`` is a scalar or one value per instance.
+    """
+
+    def __init__(self, problems, *, tol=1e-8, maxit=1000, precision="mixed", check_batch=32, pass2_blocks=16,
+                 inputs="device", device="cuda:0", val_dtype="f32"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.count = len(problems)
+        self.maxit = int(maxit)
+        self.precision = L.LYAP_PREC_MIXED if precision == "mixed" else L.LYAP_PREC_F64
+        opt = L.lyap_default_options()
+        opt.maxit = self.maxit
+        opt.precision = self.precision
+        opt.check_batch = int(check_batch)
+        opt.pass2_blocks = int(pass2_blocks)
+        self.opt = opt
+        self.s = [int(C.shape[1]) for _, C in problems]
+        self.n = [int(A.shape[0]) for A, _ in problems]
+        tols = list(tol) if hasattr(tol, "__len__") else [float(tol)] * self.count
+        vdt = np.float32 if val_dtype == "f32" else np.float64
+        self._keep = []
+        helper = Solver.__new__(Solver)
+        helper.torch, helper.device, helper._keep = torch, self.device, self._keep
+        csrs = [Solver._make_csr(helper, A, inputs, vdt) for A, _ in problems]
+        cptrs = [Solver._make_rhs(helper, C, inputs) for _, C in problems]
+        self.ws_bytes = L.lyap_batch_workspace_size(csrs, self.s, opt)
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device).cuda_stream
+        c_mem = L.LYAP_MEM_HOST if inputs == "host" else L.LYAP_MEM_DEVICE
+        self.h = L.lyap_batch_create(csrs, cptrs, c_mem, self.s, tols, opt, self.ws.data_ptr(), self.ws_bytes,
+                                     self.stream)
+        self._keep.clear()
+
+    def solve(self, autotune=False) -> int:
+        return L.lyap_batch_solve(self.h, autotune, self.stream)
+
+    def status(self):
+        return L.lyap_batch_status(self.h, self.count)
+
+    def history(self, i):
+        return L.lyap_batch_residual_norm(self.h, i, self.maxit)[0]
+
+    def factor(self, i, tcap=None, z_dtype=None):
+        t = self.torch
+        if tcap is None:
+            tcap = max(1, self.s[i] * self.status()[1][i])
+        if z_dtype is None:
+            z_dtype = "f32" if self.precision == L.LYAP_PREC_MIXED else "f64"
+        zd = L.LYAP_F32 if z_dtype == "f32" else L.LYAP_F64
+        Z = t.zeros((self.n[i], tcap), dtype=t.float32 if zd == L.LYAP_F32 else t.float64, device=self.device)
+        tk = L.lyap_batch_factor(self.h, i, Z.data_ptr(), tcap, zd, tcap, self.stream)
+        return Z[:, :tk]
+
+    def tuning(self):
+        return L.lyap_batch_tuning(self.h)
+
+    def phase_times(self):
+        return L.lyap_batch_phase_times(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lyap_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -32,6 +32,7 @@ __all__ = [
     "config_c1",
     "config_c2",
     "config_c3",
+    "config_c4",
 ]
 
 
@@ -231,6 +232,18 @@ def batched_instances(count: int = 256, seed: int = 0, kmin: int = 64, kmax: int
     ds = rng.uniform(0.0, 10.0, size=count)
     ss = rng.choice(np.array([1, 2, 4]), size=count)
     return [(int(k), float(d), int(s)) for k, d, s in zip(ks, ds, ss)]
+
+
+def config_c4(seed: int = 0, count: int = 256, kmin: int = 64, kmax: int = 512) -> list:
+    """Batched Lyapunov: instance i is A_i = -(2D Laplacian on k_i x k_i) - d_i I with
+    (k_i, d_i, s_i) from batched_instances, values rounded to fp32 (both the GPU's fp32 operator
+    and the fp64 oracle see the same A_i), C_i = rhs(k_i^2, s_i, seed + 1 + i), tol 1e-8."""
+    out = []
+    for i, (k, d, s) in enumerate(batched_instances(count, seed, kmin, kmax)):
+        A = laplacian_2d(k, shift=d)
+        A.data = A.data.astype(np.float32).astype(np.float64)
+        out.append(Problem(f"lyap_lap2d_{k}_d{d:.3f}_s{s}", A, rhs(k * k, s, seed + 1 + i), tol=1e-8, maxit=1000))
+    return out
 
 
 def config_c1(seed: int = 0) -> Problem:
