@@ -253,8 +253,10 @@ def lyap_batch_create(csrs, c_ptrs, c_mem: int, s, tol, opt, ws_ptr: int, ws_byt
 
 
 def lyap_batch_solve(b: int, autotune: bool, stream: int) -> int:
+    """Returns the batch status; an instance's own failure (breakdown, eigensolver, ...) is
+    reported through lyap_batch_status, only failures of the call itself raise."""
     st = load().lyap_batch_solve(ct.c_void_p(b), int(bool(autotune)), ct.c_void_p(stream))
-    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+    if st in (LYAP_ERR_ARG, LYAP_ERR_CUDA, LYAP_ERR_WORKSPACE):
         raise LyapError(st, "lyap_batch_solve")
     return st
 

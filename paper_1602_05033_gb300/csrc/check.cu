@@ -328,12 +328,12 @@ __global__ void k_mark_refine(CheckArgs g) {
   Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
   const double tol32 = sl.hdr[4];
   const double span = fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
-  // refined estimates are accurate to a few eps64 ||T||; they are grouped at 1e-7 ||T|| (at
-  // least 8 sqrt(N) eps64 ||T||), far above the splitting of near-degenerate eigenvalues by the
-  // recurrence's rounding (~1e-10 ||T||), so such eigenvalues stay in one group whose subspace
-  // converges fast, while groups stay far below the fp32 tolerance (~1e-6 ||T|| and more)
+  // refined estimates are accurate to a few eps64 ||T||, so a refined singleton converges to its
+  // own eigenvalue within a few steps whenever its neighbours are more than 1e-9 ||T|| away; closer
+  // ones (near-duplicate Ritz values of the finite-precision recurrence reach 1e-10 ||T||) are
+  // grouped and resolved together
   const double tnorm = sl.hdr[3] * span;
-  const double tol64 = fmax(8.0 * sqrt((double)N) * DBL_EPSILON * tnorm, 1e-7 * tnorm);
+  const double tol64 = fmax(8.0 * sqrt((double)N) * DBL_EPSILON * tnorm, 1e-9 * tnorm);
   if (threadIdx.x == 0) sl.hdr[6] = tol64;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     if (i > 0 && sl.est[i] - sl.est[i - 1] <= tol32) continue;
