@@ -241,6 +241,45 @@ int lyap_batch_phase_times(lyap_batch* b, double* out, int cap);
 
 int lyap_batch_destroy(lyap_batch* b);
 
+/* ---- extended Krylov space with preconditioned inner solves (Sec. 4) --------------------------
+ * Galerkin projection onto K_m(A, C) + K_m(A^{-1}, A^{-1} C): blocks of 2s columns, W =
+ * [A V_j^(1), A^{-1} V_j^(2)], block Gram-Schmidt against every stored block (twice; Sec. 4's
+ * three-term version loses orthogonality quickly in floating point) and CholQR2; T_m by explicit
+ * projection; the convergence check is Prop. 3.1 / Alg. 3 with block size 2s.  The solves with A
+ * are conjugate gradients on -A (SPD) to relative residual inner_tol, preconditioned by Jacobi
+ * scaling or by a convolutional network on the operator's nx x ny grid (three 3x3 convolutions,
+ * 1 -> 16 -> 16 -> 1 channels, ReLU, bf16 activations) trained on the solve pairs (b, A^{-1} b) of
+ * the method's first inner solves with the energy-norm loss.  The paper uses direct solves; the
+ * iterative solves and the network are additions.
+ *  A : CSR with fp64 values (host or device memory, read during create); s in {1, 2, 4}
+ *  C : n x s row-major fp64, memory kind c_mem
+ *  nx, ny : grid of the unknowns (x fastest, nx * ny = n) for the network; 0, 0 for none
+ * The basis is stored (n x 2s per iteration, maxit + 1 blocks) and the factor is formed from it. */
+typedef struct lyap_ek lyap_ek;
+
+int lyap_ek_workspace_size(const lyap_csr* A, int s, int maxit, int nx, int ny, size_t* bytes);
+int lyap_ek_create(const lyap_csr* A, const double* C, int c_mem, int s, double tol, int maxit,
+                   double inner_tol, int nx, int ny, void* workspace, size_t ws_bytes, void* stream,
+                   lyap_ek** out);
+/* precond 0: Jacobi; 1: the network, trained with train_iters Adam steps (learning rate lr)
+ * once train_steps inner solves (with Jacobi) have produced its training pairs. */
+int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, float lr, void* stream);
+int lyap_ek_residual_norm(lyap_ek* e, double* hist_host, int cap, int* m_out);
+/* Z: device fp64, n x tcap row-major, leading dimension ldz >= tcap */
+int lyap_ek_factor(lyap_ek* e, double* Z, int64_t ldz, int tcap, int* t_out, void* stream);
+/* out[0] solve ms, [1] training ms, [2] training loss before, [3] after, [4] inner solves,
+ * [5] network-preconditioned solves that were redone with Jacobi (non-finite, or more than 3x the
+ * last Jacobi solve's iterations), then each inner solve's iteration count (negative when the
+ * network's solve was kept) */
+int lyap_ek_stats(lyap_ek* e, double* out, int cap);
+/* Energy-norm loss and gradient of the network for caller parameters (host floats, length
+ * lyap_ek_param_count()) over K device pairs (n x K column-major B and X with A X = B); grad
+ * is a host array of the same length.  Exposes the training kernels for testing. */
+int lyap_ek_cnn_grad(lyap_ek* e, const float* params, int K, const double* B, const double* X,
+                     double* loss, double* grad, void* stream);
+int lyap_ek_param_count(void);
+int lyap_ek_destroy(lyap_ek* e);
+
 #ifdef __cplusplus
 }
 #endif

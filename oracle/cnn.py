@@ -105,18 +105,22 @@ def loss_and_grad(p: dict, R: np.ndarray, X: np.ndarray, shape):
     return L, g
 
 
-def energy_loss_and_grad(p: dict, A, R: np.ndarray, X: np.ndarray, shape):
-    """L = (1/K) sum_k ||CNN(r_k) - x_k||^2_{-A} / ||x_k||^2_{-A} over solve pairs A x_k = r_k
+def energy_loss_and_grad(p: dict, A, R: np.ndarray, X: np.ndarray, shape, jacobi: bool = False):
+    """L = (1/K) sum_k ||y_k - x_k||^2_{-A} / ||x_k||^2_{-A} over solve pairs A x_k = r_k
     (A symmetric negative definite, so -A defines the energy norm conjugate gradients minimise),
-    each pair scaled to ||r_k|| = 1, and its gradient; d/dy of the k-th term is
-    2 (-A)(y - x) / ||x||^2_{-A} = 2 (r - A y) / ||x||^2_{-A}."""
+    each pair scaled to ||r_k|| = 1, and its gradient; y_k = CNN(r_k), or with ``jacobi``
+    y_k = r_k / diag(A) + CNN(r_k) (the network as a correction to Jacobi scaling).  d/dy of the
+    k-th term is 2 (-A)(y - x) / ||x||^2_{-A} = 2 (r - A y) / ||x||^2_{-A}."""
     K = R.shape[1]
     L = 0.0
     g = {k: np.zeros_like(v) for k, v in p.items()}
+    dA = A.diagonal()
     for k in range(K):
         nr = np.linalg.norm(R[:, k])
         r, x = R[:, k] / nr, X[:, k] / nr
         y, cache = forward(p, r, shape)
+        if jacobi:
+            y = y + r / dA
         d = y - x
         ex = float(x @ (-(A @ x)))
         L += float(d @ (-(A @ d))) / ex / K

@@ -50,6 +50,15 @@ EXPORTED = (
     "lyap_batch_tuning",
     "lyap_batch_phase_times",
     "lyap_batch_destroy",
+    "lyap_ek_workspace_size",
+    "lyap_ek_create",
+    "lyap_ek_solve",
+    "lyap_ek_residual_norm",
+    "lyap_ek_factor",
+    "lyap_ek_stats",
+    "lyap_ek_cnn_grad",
+    "lyap_ek_param_count",
+    "lyap_ek_destroy",
 )
 
 
@@ -126,6 +135,17 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_batch_tuning.argtypes = [P, IP, ct.c_int]
     lib.lyap_batch_phase_times.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int]
     lib.lyap_batch_destroy.argtypes = [P]
+    DP = ct.POINTER(ct.c_double)
+    lib.lyap_ek_workspace_size.argtypes = [CSRP, ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
+    lib.lyap_ek_create.argtypes = [CSRP, P, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double, ct.c_int, ct.c_int, P,
+                                   ct.c_size_t, P, ct.POINTER(P)]
+    lib.lyap_ek_solve.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, ct.c_float, P]
+    lib.lyap_ek_residual_norm.argtypes = [P, DP, ct.c_int, IP]
+    lib.lyap_ek_factor.argtypes = [P, P, ct.c_int64, ct.c_int, IP, P]
+    lib.lyap_ek_stats.argtypes = [P, DP, ct.c_int]
+    lib.lyap_ek_cnn_grad.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int, P, P, DP, DP, P]
+    lib.lyap_ek_param_count.argtypes = []
+    lib.lyap_ek_destroy.argtypes = [P]
     lib.lyap_status_string.argtypes = [ct.c_int]
     lib.lyap_status_string.restype = ct.c_char_p
     for name in EXPORTED:
@@ -306,6 +326,84 @@ def lyap_batch_phase_times(b: int):
 def lyap_batch_destroy(b: int) -> None:
     if b:
         load().lyap_batch_destroy(ct.c_void_p(b))
+
+
+def lyap_ek_workspace_size(A: lyap_csr, s: int, maxit: int, nx: int, ny: int) -> int:
+    nb = ct.c_size_t(0)
+    st = load().lyap_ek_workspace_size(ct.byref(A), int(s), int(maxit), int(nx), int(ny), ct.byref(nb))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_workspace_size")
+    return int(nb.value)
+
+
+def lyap_ek_create(A: lyap_csr, C_ptr: int, c_mem: int, s: int, tol: float, maxit: int, inner_tol: float, nx: int,
+                   ny: int, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ct.c_void_p(0)
+    st = load().lyap_ek_create(ct.byref(A), ct.c_void_p(C_ptr), int(c_mem), int(s), float(tol), int(maxit),
+                               float(inner_tol), int(nx), int(ny), ct.c_void_p(ws_ptr), ct.c_size_t(ws_bytes),
+                               ct.c_void_p(stream), ct.byref(h))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_create")
+    return h.value
+
+
+def lyap_ek_solve(h: int, precond: int, train_steps: int, train_iters: int, lr: float, stream: int) -> int:
+    st = load().lyap_ek_solve(ct.c_void_p(h), int(precond), int(train_steps), int(train_iters), float(lr),
+                              ct.c_void_p(stream))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_ek_solve")
+    return st
+
+
+def lyap_ek_residual_norm(h: int, cap: int):
+    import numpy as np
+
+    buf = np.full(max(cap, 1), np.nan)
+    m = ct.c_int(0)
+    st = load().lyap_ek_residual_norm(ct.c_void_p(h), buf.ctypes.data_as(ct.POINTER(ct.c_double)), int(cap), ct.byref(m))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_ek_residual_norm")
+    return buf[: m.value].copy(), m.value
+
+
+def lyap_ek_factor(h: int, Z_ptr: int, ldz: int, tcap: int, stream: int) -> int:
+    t = ct.c_int(0)
+    st = load().lyap_ek_factor(ct.c_void_p(h), ct.c_void_p(Z_ptr), ct.c_int64(ldz), int(tcap), ct.byref(t),
+                               ct.c_void_p(stream))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_factor")
+    return t.value
+
+
+def lyap_ek_stats(h: int, cap: int = 512):
+    out = (ct.c_double * cap)()
+    load().lyap_ek_stats(ct.c_void_p(h), out, cap)
+    return list(out)
+
+
+def lyap_ek_param_count() -> int:
+    return int(load().lyap_ek_param_count())
+
+
+def lyap_ek_cnn_grad(h: int, params, K: int, B_ptr: int, X_ptr: int, stream: int):
+    import numpy as np
+
+    nw = lyap_ek_param_count()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == nw
+    loss = ct.c_double(0.0)
+    grad = np.zeros(nw)
+    st = load().lyap_ek_cnn_grad(ct.c_void_p(h), p.ctypes.data_as(ct.POINTER(ct.c_float)), int(K), ct.c_void_p(B_ptr),
+                                 ct.c_void_p(X_ptr), ct.byref(loss), grad.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                 ct.c_void_p(stream))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_cnn_grad")
+    return loss.value, grad
+
+
+def lyap_ek_destroy(h: int) -> None:
+    if h:
+        load().lyap_ek_destroy(ct.c_void_p(h))
 
 
 def lyap_destroy(h: int) -> None:

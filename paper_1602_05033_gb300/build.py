@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblyap.so")
-SOURCES = ["api.cu", "sell.cu", "lanczos.cu", "check.cu", "factor.cu", "batch.cu"]
+SOURCES = ["api.cu", "sell.cu", "lanczos.cu", "check.cu", "factor.cu", "batch.cu", "ek.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE]
 

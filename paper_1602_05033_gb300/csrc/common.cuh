@@ -175,6 +175,8 @@ int round_status(lyap_handle* h);
 // factor.cu
 size_t factor_ws_bytes(int s, int nmax, int sylv);
 size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32);
+int run_factor_basis(lyap_handle* h, const double* basis, int64_t n, double* Z, int64_t ldz, int tcap, int* t_out,
+                     cudaStream_t st);
 int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
                cudaStream_t st);
 

@@ -753,9 +753,9 @@ int run_factor_sylv(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ld
   return LYAP_OK;
 }
 
-int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
-               cudaStream_t st) {
-  if (h->plan.sylv) return run_factor_sylv(h, Z1, ldz1, Z2, ldz2, z_dtype, tcap, t_out, st);
+// Lyapunov factor up to M = Q_m Ycheck (N x tk, leading dimension tmax, in the factor scratch):
+// steps 1-5 of the truncation; *t_out = tk (0: nothing to accumulate)
+int factor_core(lyap_handle* h, int tcap, int* t_out, double** M_out, int* ldm_out, cudaStream_t st) {
   const int s = h->s, m = h->m, N = s * m;
   const int nmax = h->plan.nmax;
   const int tmax = nmax < kTmaxCap ? nmax : kTmaxCap;
@@ -776,6 +776,8 @@ int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, i
   LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
   const int tpc = h->flags_host[2];
+  *M_out = f.M;
+  *ldm_out = tmax;
   if (tpc <= 0) {
     *t_out = 0;
     return LYAP_OK;
@@ -813,8 +815,38 @@ int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, i
     k_form_M<<<dim3((N + 127) / 128, tk), 128, 0, st>>>(f, N, tmax, order_d, tk, 0, f.M, tmax);
     h->launches += 1;
   }
-  int rc = second_pass(h, 0, f.M, tmax, tk, Z1, ldz1, z_dtype == LYAP_F32, st);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // the order vector above is a local host buffer
+  return LYAP_OK;
+}
+
+int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
+               cudaStream_t st) {
+  if (h->plan.sylv) return run_factor_sylv(h, Z1, ldz1, Z2, ldz2, z_dtype, tcap, t_out, st);
+  double* M = nullptr;
+  int ldm = 0;
+  int rc = factor_core(h, tcap, t_out, &M, &ldm, st);
+  if (rc != LYAP_OK || *t_out == 0) return rc;
+  rc = second_pass(h, 0, M, ldm, *t_out, Z1, ldz1, z_dtype == LYAP_F32, st);
   if (rc != LYAP_OK) return rc;
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // keeps the host vectors alive until the copies ran
   return LYAP_OK;
+}
+
+// factor from a stored basis (blocks of n x s, consecutive): Z = sum_j V_j M_j, fp64
+int run_factor_basis(lyap_handle* h, const double* basis, int64_t n, double* Z, int64_t ldz, int tcap, int* t_out,
+                     cudaStream_t st) {
+  double* M = nullptr;
+  int ldm = 0;
+  int rc = factor_core(h, tcap, t_out, &M, &ldm, st);
+  if (rc != LYAP_OK) return rc;
+  const int tk = *t_out, s = h->s;
+  if (tk > 0) {
+    const int64_t tot = n * tk;
+    k_zero_cols<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Z, n, ldz, tk);
+    for (int j = 0; j < h->m; ++j)
+      gemm_accum(0, 0, n, s, tk, basis + (size_t)j * n * s, s, M + (size_t)j * s * ldm, ldm, Z, ldz, st);
+    h->launches += 1 + h->m;
+  }
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
 }

@@ -221,3 +221,73 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class ExtendedKrylov:
+    """Extended Krylov projection (lyap_ek_*): inner solves by conjugate gradients with Jacobi or
+    the learned convolutional preconditioner on the nx x ny grid ``grid`` (x fastest)."""
+
+    def __init__(self, A, C, *, tol=1e-8, maxit=60, inner_tol=1e-10, grid=None, device="cuda:0"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = int(A.shape[0])
+        self.s = int(C.shape[1])
+        self.maxit = int(maxit)
+        rp, cl, vl = csr_arrays(A)
+        self._arrs = [torch.from_numpy(x).to(self.device) for x in (rp, cl, vl)]
+        c = L.lyap_csr()
+        c.n, c.nnz = self.n, cl.shape[0]
+        c.rowptr, c.col, c.val = (a.data_ptr() for a in self._arrs)
+        c.val_dtype, c.mem = L.LYAP_F64, L.LYAP_MEM_DEVICE
+        nx, ny = grid if grid is not None else (0, 0)
+        self.grid = (int(nx), int(ny))
+        self.ws_bytes = L.lyap_ek_workspace_size(c, self.s, self.maxit, nx, ny)
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device).cuda_stream
+        self._C = torch.from_numpy(np.ascontiguousarray(C, dtype=np.float64)).to(self.device)
+        self.h = L.lyap_ek_create(c, self._C.data_ptr(), L.LYAP_MEM_DEVICE, self.s, tol, self.maxit, inner_tol, nx, ny,
+                                  self.ws.data_ptr(), self.ws_bytes, self.stream)
+        self.m = 0
+
+    def solve(self, precond="jacobi", train_steps=2, train_iters=200, lr=2e-3) -> int:
+        st = L.lyap_ek_solve(self.h, 1 if precond == "cnn" else 0, train_steps, train_iters, lr, self.stream)
+        _, self.m = L.lyap_ek_residual_norm(self.h, 0)
+        return st
+
+    def history(self):
+        return L.lyap_ek_residual_norm(self.h, self.maxit)[0]
+
+    def factor(self, tcap=None):
+        t = self.torch
+        if tcap is None:
+            tcap = max(1, 2 * self.s * self.m)
+        Z = t.zeros((self.n, tcap), dtype=t.float64, device=self.device)
+        tk = L.lyap_ek_factor(self.h, Z.data_ptr(), tcap, tcap, self.stream)
+        return Z[:, :tk]
+
+    def stats(self):
+        v = L.lyap_ek_stats(self.h)
+        k = int(v[4])
+        inner = v[6:6 + k]
+        return {"solve_ms": v[0], "train_ms": v[1], "loss_before": v[2], "loss_after": v[3], "fallbacks": int(v[5]),
+                "inner_jacobi": [int(x) for x in inner if x > 0], "inner_cnn": [int(-x) for x in inner if x < 0]}
+
+    def cnn_grad(self, params, B, X):
+        t = self.torch
+        Bd = t.from_numpy(np.asfortranarray(B, dtype=np.float64).T.copy()).to(self.device)  # K x n: column k contiguous
+        Xd = t.from_numpy(np.asfortranarray(X, dtype=np.float64).T.copy()).to(self.device)
+        return L.lyap_ek_cnn_grad(self.h, params, B.shape[1], Bd.data_ptr(), Xd.data_ptr(), self.stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lyap_ek_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -73,18 +73,27 @@ def test_energy_loss_gradient_matches_finite_differences():
     X = rng.standard_normal((k * k, 2))
     R = A @ X
     p = cnn.init_params(C=3, seed=2, scale=0.5)
-    L, g = cnn.energy_loss_and_grad(p, A, R, X, (k, k))
-    for key in ("w1", "w2", "b2", "w3"):
-        idx = tuple(rng.integers(0, n) for n in p[key].shape)
-        h = 1e-6
-        q = {kk: v.copy() for kk, v in p.items()}
-        q[key][idx] += h
-        Lp, _ = cnn.energy_loss_and_grad(q, A, R, X, (k, k))
-        q[key][idx] -= 2 * h
-        Lm, _ = cnn.energy_loss_and_grad(q, A, R, X, (k, k))
-        fd = (Lp - Lm) / (2 * h)
-        assert abs(fd - g[key][idx]) <= 1e-6 * max(1.0, abs(fd)), (key, fd, g[key][idx])
-    # a zero network has loss exactly 1 (y = 0)
+    for jac in (False, True):
+        L, g = cnn.energy_loss_and_grad(p, A, R, X, (k, k), jacobi=jac)
+        for key in ("w1", "w2", "b2", "w3"):
+            idx = tuple(rng.integers(0, n) for n in p[key].shape)
+            h = 1e-6
+            q = {kk: v.copy() for kk, v in p.items()}
+            q[key][idx] += h
+            Lp, _ = cnn.energy_loss_and_grad(q, A, R, X, (k, k), jacobi=jac)
+            q[key][idx] -= 2 * h
+            Lm, _ = cnn.energy_loss_and_grad(q, A, R, X, (k, k), jacobi=jac)
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g[key][idx]) <= 1e-6 * max(1.0, abs(fd)), (key, jac, fd, g[key][idx])
+    # a zero network has loss exactly 1 (y = 0); with the Jacobi term, the loss of Jacobi scaling
     z = {kk: np.zeros_like(v) for kk, v in p.items()}
     L0, _ = cnn.energy_loss_and_grad(z, A, R, X, (k, k))
     assert abs(L0 - 1.0) <= 1e-12
+    LJ, _ = cnn.energy_loss_and_grad(z, A, R, X, (k, k), jacobi=True)
+    ref = 0.0
+    for c in range(2):
+        nr = np.linalg.norm(R[:, c])
+        r, x = R[:, c] / nr, X[:, c] / nr
+        d = r / A.diagonal() - x
+        ref += float(d @ (-(A @ d))) / float(x @ (-(A @ x))) / 2
+    assert abs(LJ - ref) <= 1e-12 * ref
