@@ -43,10 +43,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=100, help="grid edge (100 -> n = 1e6)")
-    ap.add_argument("--workload", choices=["lyap", "sylv", "batch"], default="lyap",
+    ap.add_argument("--workload", choices=["lyap", "sylv", "batch", "ek"], default="lyap",
                     help="lyap: the n = 1e6 Lyapunov workload (the bench line); sylv: the Sylvester workload "
                          "(A = -(3D var.-coeff. diffusion 80^3, fp32), B = -(2D Laplacian 500^2), s = 2); batch: "
                          "256 Lyapunov instances -(2D Laplacian k x k) - d I, k in [64, 512], s in {1, 2, 4}")
+    ap.add_argument("--ek-grid", type=int, default=1024, help="grid edge of the extended Krylov workload")
+    ap.add_argument("--ek-precond", choices=["jacobi", "cnn", "both"], default="both")
     ap.add_argument("--count", type=int, default=32,
                     help="instances of the batch workload (256 is the full workload; its per-instance checks take minutes)")
     ap.add_argument("--no-f64-path", action="store_true", help="skip the plain fp64 comparison solve")
@@ -362,6 +364,50 @@ def sylv_line(args):
     return 0
 
 
+def ek_line(args):
+    """One JSON line for the extended Krylov workload with conjugate-gradient inner solves."""
+    import torch
+
+    import workloads as wl
+    from paper_1602_05033_gb300 import ExtendedKrylov
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    k = args.ek_grid
+    kappa = np.exp(1.5 * wl.gaussian_field(k, 2, seed=1000, corr_len=32.0 * k / 1024))
+    A = wl.var_coeff_diffusion(kappa)
+    C = wl.rhs(A.shape[0], 2, 0)
+    out = {}
+    kinds = ["jacobi", "cnn"] if args.ek_precond == "both" else [args.ek_precond]
+    for kind in kinds:
+        e = ExtendedKrylov(A, C, tol=1e-8, maxit=60, inner_tol=1e-10, grid=(k, k))
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        st = e.solve(kind, train_steps=2, train_iters=200, lr=2e-3)
+        Z = e.factor(tcap=min(512, 4 * e.m))
+        t1.record()
+        torch.cuda.synchronize()
+        stt = e.stats()
+        h = e.history()
+        out[kind] = {"status": int(st), "seconds": t0.elapsed_time(t1) / 1000.0, "m": int(e.m), "t": int(Z.shape[1]),
+                     "rel_residual": float(h[-1]) if len(h) else None,
+                     "inner_iterations_jacobi": int(sum(stt["inner_jacobi"])), "inner_iterations_net": int(sum(stt["inner_cnn"])),
+                     "net_solves_redone_with_jacobi": stt["fallbacks"], "train_ms": stt["train_ms"],
+                     "loss_before": stt["loss_before"], "loss_after": stt["loss_after"]}
+        e.close()
+    first = out[kinds[0]]
+    print(json.dumps({
+        "metric": METRIC, "value": first["seconds"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "dtype": "f64 (network: bf16 activations, fp32 accumulation)", "data": "synthetic",
+        "config": {"workload": f"extended Krylov Lyapunov, A = -(2D var.-coeff. diffusion {k}^2, log-normal sigma 1.5, "
+                               "correlation length 32 cells at 1024^2), s = 2, tol 1e-8, inner CG tol 1e-10",
+                   "n": int(A.shape[0]), "nnz": int(A.nnz)},
+        "runs": out}))
+    return 0
+
+
 def batch_line(args):
     """One JSON line for the batched workload: create + solve (+ factor of every instance)."""
     import torch
@@ -674,6 +720,8 @@ def main():
         return sylv_line(args)
     if args.workload == "batch":
         return batch_line(args)
+    if args.workload == "ek":
+        return ek_line(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)

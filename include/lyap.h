@@ -176,7 +176,7 @@ int lyap_destroy(lyap_handle* h);
  *  status_out: device memory, receives LYAP_OK or the error status of the evaluation (an int)
  *  stream    : cudaStream_t the work is ordered on; the call returns after enqueueing
  * Limits: 1 <= s <= 4 and s*m <= 256; anything larger returns LYAP_ERR_ARG.  The array
- * (about 5.6 MiB) is held by every GPU that loads the library until the process exits.
+ * (about 6 MiB) is held by every GPU that loads the library until the process exits.
  * The first call on a device looks the array's address up (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  All calls share
  * the one array and each call clears what must start at zero, so calls whose work
