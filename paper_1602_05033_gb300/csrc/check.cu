@@ -44,7 +44,7 @@ constexpr int kMaxCluster = 16;
 #endif
 constexpr int kRefineAt = LYAP_REFINE_AT;
 constexpr int kMaxIters = 12; // inverse iterations at the estimate, then Rayleigh-quotient shifts, until converged
-constexpr int kMaxRounds = 4;  // cluster rounds (Rayleigh-Ritz between them)
+constexpr int kMaxRounds = 10;  // cluster rounds (Rayleigh-Ritz between them); converged clusters stop early
 constexpr double kSettle = 1e-12;  // |change of the Rayleigh quotient| / ||T|| after which one more step is run
 constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||T||
 
