@@ -43,7 +43,9 @@ constexpr int kMaxCluster = 16;
 #define LYAP_REFINE_AT 8
 #endif
 constexpr int kRefineAt = LYAP_REFINE_AT;
-constexpr int kMaxIters = 12; // inverse iterations at the estimate, then Rayleigh-quotient shifts, until converged
+constexpr int kIters32 = 3;   // fp32 inverse iterations at the estimate before the fp64 ones
+constexpr int kRounds32 = 2;  // fp32 rounds of a cluster before its fp64 rounds
+constexpr int kMaxIters = 12; // fp64 inverse iterations (Rayleigh-quotient shifts) until converged
 constexpr int kMaxRounds = 10;  // cluster rounds (Rayleigh-Ritz between them); converged clusters stop early
 constexpr double kSettle = 1e-12;  // |change of the Rayleigh quotient| / ||T|| after which one more step is run
 constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||T||
@@ -446,26 +448,32 @@ __device__ __forceinline__ double mval(const double* __restrict__ Tb, int N, dou
 // (bandwidth S; U gets 2S+1 diagonals).  The active (S+1) x (2S+1) window, the pivot swaps
 // (predicated selects) and the back-substitution window live in registers: every index is a
 // compile-time constant.  U rows go to per-thread scratch ([k][e][tid] layout, coalesced).
-template <int S>
-__device__ void solve1(const double* __restrict__ Tb, int N, double sigma, double tiny, double xscale,
-                       double* __restrict__ X, size_t ld, int col, double* __restrict__ U, int tid, size_t ldu) {
+// R is the arithmetic type: fp32 for the cheap first iterations (the entries of T_m - sigma I are
+// formed in fp64 and then rounded, so the shift stays exact), fp64 to finish.  U points at the
+// double scratch reinterpreted as R.
+template <int S, typename R = double>
+__device__ void solve1(const double* __restrict__ Tb, int N, double sigma, R tiny, double xscale,
+                       double* __restrict__ X, size_t ld, int col, R* __restrict__ U, int tid, size_t ldu) {
   constexpr int W = 2 * S + 1;
-  double win[S + 1][W];
-  double yw[S + 1];
+  // a thread's U entries are doubles at ((k W + e) ldu + tid); an fp32 solve stores its value in
+  // the first half of the same double, so no thread ever touches another's scratch
+  constexpr size_t us = sizeof(double) / sizeof(R);
+  R win[S + 1][W];
+  R yw[S + 1];
 #pragma unroll
   for (int r = 0; r <= S; ++r) {
 #pragma unroll
-    for (int c = 0; c < W; ++c) win[r][c] = mval<S>(Tb, N, sigma, r, c);
-    yw[r] = r < N ? X[(size_t)r * ld + col] * xscale : 0.0;
+    for (int c = 0; c < W; ++c) win[r][c] = (R)mval<S>(Tb, N, sigma, r, c);
+    yw[r] = r < N ? (R)(X[(size_t)r * ld + col] * xscale) : R(0);
   }
   for (int k = 0; k < N; ++k) {
     if (k + S + 1 + kPf < N) prefetch_l2(X + (size_t)(k + S + 1 + kPf) * ld + col);
     const int nr = min(S, N - 1 - k);
-    double best = fabs(win[0][0]);
+    R best = fabs(win[0][0]);
     int p = 0;
 #pragma unroll
     for (int r = 1; r <= S; ++r) {
-      const double a = fabs(win[r][0]);
+      const R a = fabs(win[r][0]);
       if (r <= nr && a > best) { best = a; p = r; }
     }
 #pragma unroll
@@ -473,53 +481,53 @@ __device__ void solve1(const double* __restrict__ Tb, int N, double sigma, doubl
       const bool sw = p == r;
 #pragma unroll
       for (int c = 0; c < W; ++c) {
-        const double a = win[0][c], b = win[r][c];
+        const R a = win[0][c], b = win[r][c];
         win[0][c] = sw ? b : a;
         win[r][c] = sw ? a : b;
       }
-      const double a = yw[0], b = yw[r];
+      const R a = yw[0], b = yw[r];
       yw[0] = sw ? b : a;
       yw[r] = sw ? a : b;
     }
     if (fabs(win[0][0]) < tiny) win[0][0] = win[0][0] < 0.0 ? -tiny : tiny;
-    const double pinv = 1.0 / win[0][0];
+    const R pinv = R(1) / win[0][0];
 #pragma unroll
     for (int r = 1; r <= S; ++r) {
-      const double l = r <= nr ? win[r][0] * pinv : 0.0;
+      const R l = r <= nr ? win[r][0] * pinv : R(0);
 #pragma unroll
       for (int c = 1; c < W; ++c) win[r][c] = fma(-l, win[0][c], win[r][c]);
       yw[r] = fma(-l, yw[0], yw[r]);
     }
 #pragma unroll
-    for (int c = 0; c < W; ++c) U[((size_t)k * W + c) * ldu + tid] = win[0][c];
-    X[(size_t)k * ld + col] = yw[0];
+    for (int c = 0; c < W; ++c) U[(((size_t)k * W + c) * ldu + tid) * us] = win[0][c];
+    X[(size_t)k * ld + col] = (double)yw[0];
 #pragma unroll
     for (int r = 0; r < S; ++r) {
 #pragma unroll
       for (int c = 0; c < W - 1; ++c) win[r][c] = win[r + 1][c + 1];
-      win[r][W - 1] = 0.0;
+      win[r][W - 1] = R(0);
       yw[r] = yw[r + 1];
     }
     const int rn = k + S + 1;
 #pragma unroll
-    for (int c = 0; c < W; ++c) win[S][c] = mval<S>(Tb, N, sigma, rn, k + 1 + c);
-    yw[S] = rn < N ? X[(size_t)rn * ld + col] * xscale : 0.0;
+    for (int c = 0; c < W; ++c) win[S][c] = (R)mval<S>(Tb, N, sigma, rn, k + 1 + c);
+    yw[S] = rn < N ? (R)(X[(size_t)rn * ld + col] * xscale) : R(0);
   }
-  double xs[W - 1];  // xs[e - 1] = x_{k+e}; entries beyond N stay 0 (so do their U coefficients)
+  R xs[W - 1];  // xs[e - 1] = x_{k+e}; entries beyond N stay 0 (so do their U coefficients)
 #pragma unroll
-  for (int e = 0; e < W - 1; ++e) xs[e] = 0.0;
+  for (int e = 0; e < W - 1; ++e) xs[e] = R(0);
   for (int k = N - 1; k >= 0; --k) {
     if (k >= kPf) {
       const int kp = k - kPf;
       prefetch_l2(X + (size_t)kp * ld + col);
 #pragma unroll
-      for (int e = 0; e < W; ++e) prefetch_l2(U + ((size_t)kp * W + e) * ldu + tid);
+      for (int e = 0; e < W; ++e) prefetch_l2(U + (((size_t)kp * W + e) * ldu + tid) * us);
     }
-    double t = X[(size_t)k * ld + col];
+    R t = (R)X[(size_t)k * ld + col];
 #pragma unroll
-    for (int e = 1; e < W; ++e) t = fma(-U[((size_t)k * W + e) * ldu + tid], xs[e - 1], t);
-    const double xk = t / U[((size_t)k * W) * ldu + tid];
-    X[(size_t)k * ld + col] = xk;
+    for (int e = 1; e < W; ++e) t = fma(-U[(((size_t)k * W + e) * ldu + tid) * us], xs[e - 1], t);
+    const R xk = t / U[(((size_t)k * W) * ldu + tid) * us];
+    X[(size_t)k * ld + col] = (double)xk;
 #pragma unroll
     for (int e = W - 2; e > 0; --e) xs[e] = xs[e - 1];
     xs[0] = xk;
@@ -641,6 +649,30 @@ __global__ void k_invit(CheckArgs g) {
     const double est = sl.est[i];
     const bool refined = tolc < sl.hdr[4];
     double sigma = est, rq = est, res = 0.0, prev = est, xscale = 1.0;
+    // fp32 inverse iterations at the estimate (fp32 rate, half the scratch traffic) bring the
+    // vector to fp32 accuracy; fp64 Rayleigh-quotient steps then finish it in one or two solves
+    // (near-duplicate eigenvalues of T_m can put several tiny pivots in one factorisation; their
+    // growth can overflow fp32, in which case the eigenpair restarts in fp64 from a fresh vector)
+    bool warm = true;
+    {
+      float* U32 = reinterpret_cast<float*>(sl.U);
+      const float tiny32 = FLT_EPSILON * (float)tnorm + FLT_MIN;
+      for (int it = 0; it < kIters32 && warm; ++it) {
+        solve1<S, float>(sl.Tb, N, est, tiny32, xscale, sl.X, ld, i, U32, i, ld);
+        double num, den;
+        rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
+        warm = isfinite(num) && isfinite(den) && den > 0.0;
+        rq = num / den;
+        xscale = 1.0 / sqrt(den);
+      }
+      if (!warm) {
+        for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] = hash_unit((unsigned)k, (unsigned)i);
+        rq = est;
+        xscale = 1.0;
+      }
+      prev = rq;
+      if (warm && !refined && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
+    }
     int extra = -1;  // iterations still to run after the Rayleigh quotient settled
     for (int it = 0; it < kMaxIters; ++it) {
       solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i, ld);
@@ -650,13 +682,14 @@ __global__ void k_invit(CheckArgs g) {
       xscale = 1.0 / sqrt(den);
       if (extra == 0) break;
       if (extra > 0) --extra;
-      // settled: one more Rayleigh-quotient step brings the vector to full precision
-      if (extra < 0 && it >= 1 && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
+      // settled: one more Rayleigh-quotient step brings the vector to full precision (from a
+      // fresh start the first step cannot count as settled)
+      if (extra < 0 && (warm || it >= 1) && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
       prev = rq;
-      // Rayleigh-quotient shifts once the iterate is dominated by the wanted eigenvector; an
+      // Rayleigh-quotient shifts while the iterate is dominated by the wanted eigenvector; an
       // fp64-refined estimate is already within a few eps ||T|| and stays the shift, so the
       // iteration cannot drift to a neighbour closer than the fp32 tolerance
-      if (!refined && it >= 1 && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
+      if (!refined && (warm || it >= 1) && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
     }
     for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
     rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
@@ -757,6 +790,8 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
     // rounds at the fixed shifts until every member's residual passes, then one polishing round
     // at the Ritz values (Rayleigh-quotient shifts once the subspace is right)
     bool polish = false;
+    int rounds32 = kRounds32;  // set to 0 (fresh fp64 start) if an fp32 round overflows
+    bool overflow = false;
     for (int round = 0; round < kMaxRounds + 1; ++round) {
       if (done) {
         if (polish) break;
@@ -767,7 +802,13 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
         break;
       }
       for (int it = 0; it < (polish ? 1 : 2); ++it) {
-        if (lane < c) solve1<S>(sl.Tb, N, shift[lane], tiny, 1.0, xc + (size_t)lane * ld, 1, 0, sl.U, i + lane, ld);
+        if (lane < c) {
+          if (round < rounds32 && !polish)
+            solve1<S, float>(sl.Tb, N, shift[lane], FLT_EPSILON * (float)tnorm + FLT_MIN, 1.0, xc + (size_t)lane * ld, 1, 0,
+                             reinterpret_cast<float*>(sl.U), i + lane, ld);
+          else
+            solve1<S>(sl.Tb, N, shift[lane], tiny, 1.0, xc + (size_t)lane * ld, 1, 0, sl.U, i + lane, ld);
+        }
         __syncwarp();
         for (int pass = 0; pass < 2; ++pass)
           for (int v = 0; v < c; ++v) {
@@ -786,7 +827,17 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
             const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
             for (int k = lane; k < N; k += 32) xv[k] *= inv;
             __syncwarp();
+            if (!isfinite(n2) && round < rounds32) overflow = true;
           }
+      }
+      if (overflow) {
+        // fp32 growth overflowed: restart the group in fp64 from fresh vectors
+        overflow = false;
+        rounds32 = 0;
+        for (int v = 0; v < c; ++v)
+          for (int k = lane; k < N; k += 32) xc[(size_t)v * ld + k] = hash_unit((unsigned)k, (unsigned)(i + v));
+        __syncwarp();
+        continue;
       }
       // Rayleigh-Ritz
       for (int u = 0; u < c; ++u)
@@ -854,7 +905,7 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
         for (int v = 0; v < c; ++v) xc[(size_t)v * ld + k] = out[v];
       }
       __syncwarp();
-      if (round == 0 || polish) continue;
+      if (round < rounds32 || polish) continue;
       // converged once every member's residual passes
       bool ok = true;
       for (int v = 0; v < c; ++v) {
@@ -994,6 +1045,25 @@ __global__ void k_finalize(CheckArgs ga, CheckArgs gb, int sylv, double* hist, d
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
+#ifdef LYAP_DEBUG
+  if (threadIdx.x == 0 && !isfinite(red[0])) {
+    int nl = 0, na = 0, nw = 0, np = 0;
+    for (int i = 0; i < N; ++i) {
+      nl += !isfinite(sa.lam[i]);
+      np += !isfinite(sa.part[i]);
+      for (int c = 0; c < s; ++c) {
+        na += !isfinite(sa.a[(size_t)i * s + c]);
+        nw += !isfinite(sa.w[(size_t)i * s + c]);
+      }
+    }
+    int first = -1;
+    for (int i = 0; i < N && first < 0; ++i)
+      if (!isfinite(sa.part[i])) first = i;
+    printf("nonfinite m=%d N=%d lam %d a %d w %d part %d first part %d lam %.6g est %.6g etol %.3g clist %d\n", m, N, nl,
+           na, nw, np, first, first >= 0 ? sa.lam[first] : 0.0, first >= 0 ? sa.est[first] : 0.0,
+           first >= 0 ? sa.etol[first] : 0.0, sa.clist[0]);
+  }
+#endif
   if (threadIdx.x == 0) {
     const int SS = s * s;
     const double betaA = ga.log[REC_TDIAG * SS];
