@@ -85,6 +85,10 @@ typedef struct {
   int check_batch;       /* most convergence checks evaluated per batch (default 32)        */
   int zcap;              /* columns of Z the workspace can stage for LYAP_MEM_HOST output of
                             lyap_factor (default 0: device output only)                    */
+  int fused_steps;       /* 1: run each chunk of block Lanczos iterations as one cooperative
+                            launch (grid barriers between the four sweeps, W kept in shared
+                            memory; s <= 4, sell_sigma 1); 0: four launches per iteration
+                            (default 0)                                                     */
 } lyap_options;
 
 typedef struct lyap_handle lyap_handle;

@@ -84,6 +84,7 @@ class lyap_options(ct.Structure):
         ("pass2_blocks", ct.c_int),
         ("check_batch", ct.c_int),
         ("zcap", ct.c_int),
+        ("fused_steps", ct.c_int),
     ]
 
 

@@ -55,6 +55,7 @@ lyap_options resolve(const lyap_options* opt) {
     if (opt->pass2_blocks >= 2) o.pass2_blocks = opt->pass2_blocks;
     if (opt->check_batch > 0) o.check_batch = opt->check_batch;
     if (opt->zcap > 0) o.zcap = opt->zcap;
+    o.fused_steps = opt->fused_steps == 1 ? 1 : 0;
   }
   if (o.check_batch > 256) o.check_batch = 256;
   return o;
@@ -110,7 +111,7 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
     q.W = take(w * (size_t)M->n * s);
     q.C = take(sizeof(double) * (size_t)M->n * s);
     q.log = take(sizeof(double) * (size_t)(o.maxit + 1) * LOG_NREC * s * s);
-    q.partials = take(sizeof(double) * (size_t)kMaxSweepGrid * 3 * s * s);
+    q.partials = take(sizeof(double) * (size_t)kMaxSweepGrid * 7 * s * s);  // the fused steps use three stages
     q.counter = take(256);
     nmaxop = std::max<int64_t>(nmaxop, M->n);
   }
@@ -191,6 +192,7 @@ void lyap_default_options(lyap_options* opt) {
   opt->pass2_blocks = 16;
   opt->check_batch = 32;
   opt->zcap = 0;
+  opt->fused_steps = 0;
 }
 
 const char* lyap_status_string(int status) {
@@ -399,9 +401,15 @@ int lyap_solve(lyap_handle* h, void* stream) {
   while (true) {
     const int upto = std::min(p.maxit, done + chunk);
     cudaEventRecord(h->ev[2], st);
-    for (int j = done + 1; j <= upto; ++j)
-      for (int k = 0; k < 1 + p.sylv; ++k)
+    for (int k = 0; k < 1 + p.sylv; ++k) {
+      if (h->opt.fused_steps == 1 && upto > done &&
+          launch_fused_steps(h->op[k], s, p.bulk_f32, done + 1, upto - done, h->flags, st)) {
+        h->launches += 1;
+        continue;
+      }
+      for (int j = done + 1; j <= upto; ++j)
         h->launches += launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, h->flags, st);
+    }
     cudaEventRecord(h->ev[3], st);
     done = upto;
     h->lanczos_done = done;

@@ -152,6 +152,7 @@ int max_nacc(int s);
 int sweep_blocks_per_sm(int s, int bulk_f32);
 int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
 int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
+int launch_fused_steps(OpDev& op, int s, int bulk_f32, int j0, int nsteps, int* d_flags, cudaStream_t st);
 int launch_batch_step(int s, int bulk_f32, const BInst* d_inst, const BTile* d_tiles, int ntiles, int grid,
                       cudaStream_t st);
 int batch_blocks_per_sm(int s, int bulk_f32);

@@ -141,6 +141,69 @@ __device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lan
   }
 }
 
+
+// loads through L2 only (ld.global.cg): rows written earlier in the same launch by other SMs
+template <int S>
+__device__ __forceinline__ void load_row_cg(const float* __restrict__ X, int64_t ld, int64_t i, float (&r)[S]) {
+  const float* p = X + i * ld;
+  if constexpr (S % 4 == 0) {
+#pragma unroll
+    for (int a = 0; a < S; a += 4) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(p + a));
+      r[a] = v.x; r[a + 1] = v.y; r[a + 2] = v.z; r[a + 3] = v.w;
+    }
+  } else if constexpr (S == 2) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    r[0] = v.x; r[1] = v.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) r[a] = __ldcg(p + a);
+  }
+}
+template <int S>
+__device__ __forceinline__ void load_row_cg(const double* __restrict__ X, int64_t ld, int64_t i, double (&r)[S]) {
+  const double* p = X + i * ld;
+  if constexpr (S % 2 == 0) {
+#pragma unroll
+    for (int a = 0; a < S; a += 2) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(p + a));
+      r[a] = v.x; r[a + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) r[a] = __ldcg(p + a);
+  }
+}
+
+// sell_row with the V rows loaded through L2 (same entry order, same bits)
+template <typename T, int S>
+__device__ __forceinline__ void sell_row_cg(const OpDev& op, int64_t slice, int lane, const T* __restrict__ Vc,
+                                            int64_t ldc, T (&w)[S]) {
+#pragma unroll
+  for (int a = 0; a < S; ++a) w[a] = T(0);
+  const int64_t base = op.slice_ptr[slice] + lane;
+  const int width = op.slice_w[slice];
+  const T* __restrict__ val = static_cast<const T*>(op.sell_val);
+  for (int j0 = 0; j0 < width; j0 += kUnroll) {
+    int32_t c[kUnroll];
+    T v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool in = j0 + u < width;
+      const int64_t e = base + (int64_t)(in ? j0 + u : 0) * LYAP_SLICE;
+      c[u] = __ldg(op.sell_col + e);
+      v[u] = in ? __ldg(val + e) : T(0);
+    }
+    T x[kUnroll][S];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) load_row_cg<S>(Vc, ldc, c[u], x[u]);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int a = 0; a < S; ++a) w[a] = fma(v[u], x[u][a], w[a]);
+  }
+}
+
 // ---- coefficient blocks in shared memory ---------------------------------------
 // co[k][a][b]: k-th s x s coefficient block, converted to the bulk type.
 template <typename T, int S>
@@ -868,6 +931,284 @@ void batch_step_impl(const BInst* d_inst, const BTile* d_tiles, int ntiles, int 
   kb_write_next<T, S><<<grid, kThreads, 0, st>>>(b);
 }
 
+
+// ---- fused persistent steps: the four sweeps of several iterations in one cooperative launch ----
+// Every CTA owns a fixed range of SELL slices for all four sweeps, so the rows of W it computes
+// in the first sweep stay in its shared memory for the other three (W never goes to DRAM).  The
+// sweeps are separated by a grid barrier; after each barrier every CTA sums all CTAs' partials
+// in the same fixed order, so all CTAs hold bit-identical coefficients without another barrier,
+// and CTA 0 writes them to the log.  The rows of V_{j+1} come from the same row recipe as the
+// second pass, which therefore still regenerates them bit for bit.
+constexpr long long kSpinCycles = 2000000000LL;  // ~1 s of SM clock, then the launch gives up
+
+struct FusedArgs {
+  OpDev op;
+  int j0, nsteps;
+  int* flags;
+  unsigned int* bar;  // [0] arrivals, [16] generation, [32] abort
+  int64_t spc;        // slices per CTA
+};
+
+// grid barrier with a bounded wait: on timeout it raises DERR_TIMEOUT and tells every CTA to stop
+__device__ bool grid_sync(unsigned int* bar, unsigned int nblocks, int* flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 16;
+    volatile unsigned int* stop = bar + 32;
+    int ok = *stop == 0u;
+    if (ok) {
+      const unsigned int g = *gen;
+      __threadfence();
+      const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+      if (arrived == nblocks) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(const_cast<unsigned int*>(gen), 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*gen == g) {
+          if (*stop != 0u) {
+            ok = 0;
+            break;
+          }
+          if (clock64() - t0 > kSpinCycles) {
+            atomicOr(flags, DERR_TIMEOUT);
+            atomicExch(const_cast<unsigned int*>(stop), 1u);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// this CTA's sums of the per-thread accumulators (fixed order) -> dst[NACC]
+template <typename Acc, int NACC>
+__device__ void cta_reduce_to(Acc (&acc)[NACC], double* __restrict__ dst, double* __restrict__ scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) {
+    Acc v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) scratch[warp * NACC + k] = (double)v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += scratch[w * NACC + k];
+    dst[k] = t;
+  }
+  __syncthreads();
+}
+
+// tot[k] = sum over CTAs b of P[b][k] in the order of the last-CTA reduction of the sweeps
+template <int NACC>
+__device__ void reduce_all(const double* __restrict__ P, unsigned int G, double* __restrict__ tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < NACC; k += kWarps) {
+    double t = 0.0;
+    for (unsigned int b = lane; b < G; b += 32) t += __ldcg(P + (size_t)b * NACC + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) tot[k] = t;
+  }
+  __syncthreads();
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_fused_steps(FusedArgs g) {
+  using Acc = typename AccT<T>::type;
+  constexpr int SS = S * S;
+  constexpr int NSYM = S * (S + 1) / 2;
+  constexpr int N1 = 3 * SS, N2 = 2 * SS + NSYM, N3 = SS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);  // this CTA's rows of W, S values per row
+  __shared__ Coefs<T, S> co;
+  __shared__ double tot[N1];
+  __shared__ double scratch[kWarps * N1];
+  __shared__ double rec[LOG_NREC * SS];
+  __shared__ int dummy_flags;
+  const OpDev& op = g.op;
+  const unsigned int G = gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t s_lo = (int64_t)blockIdx.x * g.spc;
+  const int64_t s_hi = s_lo + g.spc < op.nslices ? s_lo + g.spc : op.nslices;
+  const int64_t r_lo = s_lo * LYAP_SLICE;
+  const int64_t r_hi = s_hi * LYAP_SLICE < op.n ? s_hi * LYAP_SLICE : op.n;
+  double* P1 = op.partials;
+  double* P2 = P1 + (size_t)G * N1;
+  double* P3 = P2 + (size_t)G * N2;
+  int* fl = blockIdx.x == 0 ? g.flags : &dummy_flags;
+  for (int step = 0; step < g.nsteps; ++step) {
+    const int j = g.j0 + step;
+    const bool hp = j > 1;
+    const T* Vp = static_cast<const T*>(op.V[(j + 1) % 3]);
+    const T* Vc = static_cast<const T*>(op.V[(j + 2) % 3]);
+    T* Vn = static_cast<T*>(op.V[j % 3]);
+    // S1: W = A V_j (own slices, kept in shared memory) and the first projections
+    {
+      Acc acc[N1];
+#pragma unroll
+      for (int k = 0; k < N1; ++k) acc[k] = Acc(0);
+      for (int64_t sl = s_lo + warp; sl < s_hi; sl += kWarps) {
+        const int64_t row = sl * LYAP_SLICE + lane;
+        if (row < op.n) {
+          T w[S];
+          sell_row_cg<T, S>(op, sl, lane, Vc, (int64_t)S, w);
+#pragma unroll
+          for (int a = 0; a < S; ++a) Ws[(row - r_lo) * S + a] = w[a];
+          T q[S], p[S];
+          load_row_cg<S>(Vc, (int64_t)S, row, q);
+          if (hp) load_row_cg<S>(Vp, (int64_t)S, row, p);
+          else {
+#pragma unroll
+            for (int a = 0; a < S; ++a) p[a] = T(0);
+          }
+#pragma unroll
+          for (int a = 0; a < S; ++a)
+#pragma unroll
+            for (int c = 0; c < S; ++c) {
+              acc[a * S + c] = fma((Acc)p[a], (Acc)w[c], acc[a * S + c]);
+              acc[SS + a * S + c] = fma((Acc)q[a], (Acc)w[c], acc[SS + a * S + c]);
+              acc[2 * SS + a * S + c] = fma((Acc)q[a], (Acc)p[c], acc[2 * SS + a * S + c]);
+            }
+        }
+      }
+      cta_reduce_to<Acc, N1>(acc, P1 + (size_t)blockIdx.x * N1, scratch);
+    }
+    if (!grid_sync(g.bar, G, g.flags)) return;
+    reduce_all<N1>(P1, G, tot);
+    if (threadIdx.x == 0) finalize_s1<S>(rec, tot, hp, fl);
+    __syncthreads();
+    load_coefs<T, S>(co, rec, 1);
+    // S2: second projections and the first Gram matrix
+    {
+      Acc acc[N2];
+#pragma unroll
+      for (int k = 0; k < N2; ++k) acc[k] = Acc(0);
+      for (int64_t row = r_lo + threadIdx.x; row < r_hi; row += blockDim.x) {
+        T w[S], p[S], q[S];
+#pragma unroll
+        for (int a = 0; a < S; ++a) w[a] = Ws[(row - r_lo) * S + a];
+        load_row_cg<S>(Vc, (int64_t)S, row, q);
+        if (hp) load_row_cg<S>(Vp, (int64_t)S, row, p);
+        else {
+#pragma unroll
+          for (int a = 0; a < S; ++a) p[a] = T(0);
+        }
+        mgs_row<T, S>(p, q, co.ap, co.ad, w, hp);
+#pragma unroll
+        for (int a = 0; a < S; ++a)
+#pragma unroll
+          for (int c = 0; c < S; ++c) {
+            acc[a * S + c] = fma((Acc)p[a], (Acc)w[c], acc[a * S + c]);
+            acc[SS + a * S + c] = fma((Acc)q[a], (Acc)w[c], acc[SS + a * S + c]);
+          }
+        int e = 2 * SS;
+#pragma unroll
+        for (int a = 0; a < S; ++a)
+#pragma unroll
+          for (int c = a; c < S; ++c, ++e) acc[e] = fma((Acc)w[a], (Acc)w[c], acc[e]);
+      }
+      cta_reduce_to<Acc, N2>(acc, P2 + (size_t)blockIdx.x * N2, scratch);
+    }
+    if (!grid_sync(g.bar, G, g.flags)) return;
+    reduce_all<N2>(P2, G, tot);
+    if (threadIdx.x == 0) finalize_s2<S>(rec, tot, hp, fl);
+    __syncthreads();
+    load_coefs<T, S>(co, rec, 2);
+    // S3: second Gram matrix (CholQR2)
+    {
+      Acc acc[N3];
+#pragma unroll
+      for (int k = 0; k < N3; ++k) acc[k] = Acc(0);
+      for (int64_t row = r_lo + threadIdx.x; row < r_hi; row += blockDim.x) {
+        T w[S], p[S], q[S];
+#pragma unroll
+        for (int a = 0; a < S; ++a) w[a] = Ws[(row - r_lo) * S + a];
+        load_row_cg<S>(Vc, (int64_t)S, row, q);
+        if (hp) load_row_cg<S>(Vp, (int64_t)S, row, p);
+        else {
+#pragma unroll
+          for (int a = 0; a < S; ++a) p[a] = T(0);
+        }
+        mgs_row<T, S>(p, q, co.tp, co.td, w, hp);
+        trsm_row<T, S>(co.r1, co.r1i, w);
+#pragma unroll
+        for (int a = 0; a < S; ++a)
+#pragma unroll
+          for (int c = 0; c < S; ++c) acc[a * S + c] = fma((Acc)w[a], (Acc)w[c], acc[a * S + c]);
+      }
+      cta_reduce_to<Acc, N3>(acc, P3 + (size_t)blockIdx.x * N3, scratch);
+    }
+    if (!grid_sync(g.bar, G, g.flags)) return;
+    reduce_all<N3>(P3, G, tot);
+    if (threadIdx.x == 0) finalize_s3<S>(rec, tot, fl);
+    __syncthreads();
+    load_coefs<T, S>(co, rec, 3);
+    // S4: V_{j+1} for the own rows; CTA 0 logs the iteration's coefficients
+    for (int64_t row = r_lo + threadIdx.x; row < r_hi; row += blockDim.x) {
+      T w[S], p[S], q[S];
+#pragma unroll
+      for (int a = 0; a < S; ++a) w[a] = Ws[(row - r_lo) * S + a];
+      load_row_cg<S>(Vc, (int64_t)S, row, q);
+      if (hp) load_row_cg<S>(Vp, (int64_t)S, row, p);
+      else {
+#pragma unroll
+        for (int a = 0; a < S; ++a) p[a] = T(0);
+      }
+      next_row<T, S>(co, p, q, w, hp);
+      store_row<S>(Vn, (int64_t)S, row, w);
+    }
+    if (blockIdx.x == 0)
+      for (int k = threadIdx.x; k < LOG_NREC * SS; k += blockDim.x) op.log[(size_t)j * LOG_NREC * SS + k] = rec[k];
+    if (!grid_sync(g.bar, G, g.flags)) return;
+  }
+}
+
+template <typename T, int S>
+int fused_impl(OpDev& op, int j0, int nsteps, int* flags, cudaStream_t st) {
+  if (op.perm != nullptr || S > 4) return 0;  // s = 8 would spill its accumulators
+  int dev = 0, sms = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || sms <= 0) return 0;
+  const void* fn = (const void*)k_fused_steps<T, S>;
+  // shared memory for W rows: try the grid that gives every SM MinBlocks CTAs first
+  for (int bps = MinBlocks<T>::value; bps >= 1; --bps) {
+    const int G = std::min(sms * bps, kMaxSweepGrid);
+    const int64_t spc = (op.nslices + G - 1) / G;
+    const size_t smem = (size_t)spc * LYAP_SLICE * S * sizeof(T);
+    if (smem > (size_t)160 * 1024) continue;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) continue;
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kThreads, smem) != cudaSuccess || fit < bps) continue;
+    FusedArgs a;
+    a.op = op;
+    a.j0 = j0;
+    a.nsteps = nsteps;
+    a.flags = flags;
+    a.bar = op.counter + 16;
+    a.spc = spc;
+    void* args[] = {&a};
+    if (cudaMemsetAsync(op.counter + 48, 0, sizeof(unsigned int), st) != cudaSuccess) return 0;
+    if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, smem, st) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return 1;
+  }
+  return 0;
+}
+
 // ---- dispatch ---------------------------------------------------------------
 template <typename T, int S>
 void step_impl(OpDev& op, int grid, int j, int* flags, cudaStream_t st) {
@@ -1015,6 +1356,21 @@ int batch_blocks_per_sm(int s, int bulk_f32) {
   }
 #undef LYAP_OCC
   return best == (1 << 30) ? 1 : best;
+}
+
+// nsteps iterations from j0 in one cooperative launch; returns 1, or 0 when the fused kernel
+// cannot run here (the caller then uses launch_lanczos_step)
+int launch_fused_steps(OpDev& op, int s, int bulk_f32, int j0, int nsteps, int* d_flags, cudaStream_t st) {
+#define LYAP_FS(TT, SS_) return fused_impl<TT, SS_>(op, j0, nsteps, d_flags, st)
+  if (bulk_f32) {
+    switch (s) { case 1: LYAP_FS(float, 1); case 2: LYAP_FS(float, 2); case 3: LYAP_FS(float, 3);
+                 case 4: LYAP_FS(float, 4); }
+  } else {
+    switch (s) { case 1: LYAP_FS(double, 1); case 2: LYAP_FS(double, 2); case 3: LYAP_FS(double, 3);
+                 case 4: LYAP_FS(double, 4); }
+  }
+#undef LYAP_FS
+  return 0;
 }
 
 int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st) {

@@ -22,7 +22,7 @@ class Solver:
 
     def __init__(self, A, C1, B=None, C2=None, *, tol=1e-8, maxit=1000, check_every=1, trunc_eps=1e-12,
                  precision="f64", sell_sigma=1, pass2_blocks=16, check_batch=32, zcap=0, inputs="device",
-                 device="cuda:0", val_dtype="f64"):
+                 device="cuda:0", val_dtype="f64", fused_steps=0):
         import torch
 
         self.torch = torch
@@ -41,6 +41,7 @@ class Solver:
         opt.sell_sigma = int(sell_sigma)
         opt.pass2_blocks = int(pass2_blocks)
         opt.check_batch = int(check_batch)
+        opt.fused_steps = int(fused_steps)
         # host output of the factor is staged in the workspace; by default size it for any rank
         opt.zcap = int(zcap) if zcap else (self.s * int(maxit) if inputs == "host" else 0)
         self.opt = opt
