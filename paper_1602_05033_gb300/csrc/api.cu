@@ -388,62 +388,92 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
 int lyap_solve(lyap_handle* h, void* stream) {
   if (!h) return LYAP_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaStream_t sd = h->side;
   const Plan& p = h->plan;
   const int s = h->s;
   cudaEventRecord(h->ev[0], st);
   solve_begin(h, st);
-  int done = 0;        // Lanczos iterations completed (blocks V_1..V_{done+1} exist)
-  int checked = 0;     // largest m already checked
-  int chunk = std::min(4, p.check_batch_req);
-  int result = LYAP_NOT_CONVERGED;
-  int m_final = p.maxit;
-  float t_lanczos = 0.f, t_check = 0.f;
-  while (true) {
-    const int upto = std::min(p.maxit, done + chunk);
-    cudaEventRecord(h->ev[2], st);
+  // Lanczos chunks run on the caller's stream and the checks of a finished chunk on the side
+  // stream, so chunk c+1 (speculative: the checks of chunk c may find convergence) overlaps the
+  // checks of chunk c.  Step j writes only log record j and the checks of chunk c read records
+  // up to its last step, so the two never touch the same data.  Each chunk reports sweep errors
+  // in its own word (two words, alternating), so an error in a speculative chunk past the
+  // converged m does not fail the solve.
+  int* cw = h->flags + 8;
+  LYAP_CUDA_TRY(cudaMemsetAsync(cw, 0, 2 * sizeof(int), st));
+  cudaEvent_t c_beg[2] = {h->ev[2], h->ev[6]}, c_end[2] = {h->ev[3], h->ev[7]};
+  auto launch_chunk = [&](int from, int upto, int c) {
+    int* fw = cw + (c & 1);
+    cudaEventRecord(c_beg[c & 1], st);
     for (int k = 0; k < 1 + p.sylv; ++k) {
-      if (h->opt.fused_steps == 1 && upto > done &&
-          launch_fused_steps(h->op[k], s, p.bulk_f32, done + 1, upto - done, h->flags, st)) {
+      if (h->opt.fused_steps == 1 && upto > from &&
+          launch_fused_steps(h->op[k], s, p.bulk_f32, from + 1, upto - from, fw, st)) {
         h->launches += 1;
         continue;
       }
-      for (int j = done + 1; j <= upto; ++j)
-        h->launches += launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, h->flags, st);
+      for (int j = from + 1; j <= upto; ++j)
+        h->launches += launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, fw, st);
     }
-    cudaEventRecord(h->ev[3], st);
-    done = upto;
-    h->lanczos_done = done;
+    cudaEventRecord(c_end[c & 1], st);
+  };
+  int chunk = std::min(4, p.check_batch_req);
+  int done = std::min(p.maxit, chunk);  // last step of the chunk being checked
+  int checked = 0;                      // largest m already checked
+  int c = 0;                            // index of the chunk being checked
+  int result = LYAP_NOT_CONVERGED;
+  int m_final = p.maxit;
+  float t_lanczos = 0.f, t_check = 0.f;
+  launch_chunk(0, done, 0);
+  int rc = LYAP_OK;
+  while (true) {
+    LYAP_CUDA_TRY(cudaStreamWaitEvent(sd, c_end[c & 1], 0));
+    cudaEventRecord(h->ev[5], sd);
     while (checked < done) {
       // as many checks as fit in the check area with slots sized by the batch's largest m
       const int lo = checked + 1;
       int hi = std::min(done, checked + p.check_batch_req);
       while (hi > lo && (size_t)(1 + p.sylv) * (hi - lo + 1) * check_slot_bytes(s, batch_nmax(s, hi)) > p.check_bytes)
         --hi;
-      h->launches += launch_check_batch(h, lo, hi, st);
+      h->launches += launch_check_batch(h, lo, hi, sd);
       checked = hi;
     }
-    cudaEventRecord(h->ev[4], st);
+    cudaEventRecord(h->ev[4], sd);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sd));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 3, cw + (c & 1), sizeof(int), cudaMemcpyDeviceToHost, sd));
+    // the next chunk, while the checks run
+    chunk = std::min(2 * chunk, p.check_batch_req);
+    const int next = std::min(p.maxit, done + chunk);
+    if (next > done) {
+      LYAP_CUDA_TRY(cudaMemsetAsync(cw + ((c + 1) & 1), 0, sizeof(int), st));
+      launch_chunk(done, next, c + 1);
+    }
     LYAP_CUDA_TRY(cudaGetLastError());
-    LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
-    LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(sd));
     float a = 0.f, b = 0.f;
-    cudaEventElapsedTime(&a, h->ev[2], h->ev[3]);
-    cudaEventElapsedTime(&b, h->ev[3], h->ev[4]);
+    cudaEventElapsedTime(&a, c_beg[c & 1], c_end[c & 1]);
+    cudaEventElapsedTime(&b, h->ev[5], h->ev[4]);
     t_lanczos += a;
     t_check += b;
-    // a check that failed before (or without) convergence is the result
-    int rc = round_status(h);
-    if (rc != LYAP_OK) {
-      h->solved = 0;
-      return rc;
-    }
+    // a sweep error in the checked chunk, or a check that failed before (or without)
+    // convergence, is the result
+    h->flags_host[0] |= h->flags_host[3];
+    rc = round_status(h);
+    if (rc != LYAP_OK) break;
     if (h->flags_host[1] != INT_MAX) {
       m_final = h->flags_host[1];
       result = LYAP_OK;
       break;
     }
-    if (done >= p.maxit) break;
-    chunk = std::min(2 * chunk, p.check_batch_req);
+    if (next == done) break;
+    done = next;
+    ++c;
+  }
+  // the speculative chunk may still be running on the caller's stream
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (rc != LYAP_OK) {
+    h->lanczos_done = done;
+    h->solved = 0;
+    return rc;
   }
   int rc_end = solve_end(h, done, m_final, result, st);
   if (rc_end != LYAP_OK) return rc_end;

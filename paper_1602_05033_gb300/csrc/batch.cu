@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr int kPools = 4;
+constexpr int kPools = 12;  // most pools (streams with check and factor scratch)
 constexpr int kRowChoices[3] = {1024, 4096, 16384};
 constexpr size_t kPoolCheckMin = (size_t)2 << 30;  // check slots of one pool
 
@@ -35,6 +35,7 @@ struct Group {
 struct BatchPlan {
   std::vector<size_t> inst_off, inst_bytes;
   size_t pool_off = 0, pool_check = 0, pool_factor = 0;
+  int npools = 1;
   size_t inst_arr = 0, step_arr = 0, tile_arr = 0, tile_cap = 0;
   size_t total = 0;
 };
@@ -66,7 +67,8 @@ int plan_batch(int count, const lyap_csr* A, const int* s, const lyap_options& o
   }
   bp.pool_check = lyap_align256((int64_t)std::max(slot_full, kPoolCheckMin));
   bp.pool_factor = lyap_align256((int64_t)fac);
-  bp.pool_off = take(kPools * (bp.pool_check + bp.pool_factor));
+  bp.npools = std::min(kPools, count);
+  bp.pool_off = take(bp.npools * (bp.pool_check + bp.pool_factor));
   bp.inst_arr = take(sizeof(BInst) * (size_t)count);
   bp.step_arr = take(sizeof(int) * 2 * (size_t)count);
   bp.tile_arr = take(sizeof(BTile) * bp.tile_cap);
@@ -269,7 +271,7 @@ int lyap_batch_create(int count, const lyap_csr* A, const double* const* C, int 
   b->sms = sm_count();
   cudaStream_t user = static_cast<cudaStream_t>(stream);
   if (cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking) != cudaSuccess) return fail(LYAP_ERR_CUDA);
-  for (int p = 0; p < kPools; ++p) {
+  for (int p = 0; p < bp.npools; ++p) {
     if (cudaStreamCreateWithFlags(&b->streams[p], cudaStreamNonBlocking) != cudaSuccess) return fail(LYAP_ERR_CUDA);
     if (cudaEventCreateWithFlags(&b->join[p], cudaEventDisableTiming) != cudaSuccess) return fail(LYAP_ERR_CUDA);
     b->pool[p] = b->ws + bp.pool_off + (size_t)p * (bp.pool_check + bp.pool_factor);
@@ -371,7 +373,7 @@ int lyap_batch_solve(lyap_batch* b, int autotune_flag, void* stream) {
     t_lanczos += a;
     // checks of the new iterations, instance by instance on the pool streams
     cudaEventRecord(b->ev[2], st);
-    for (int p = 0; p < kPools; ++p) cudaStreamWaitEvent(b->streams[p], b->ev[2], 0);
+    for (int p = 0; p < b->plan.npools; ++p) cudaStreamWaitEvent(b->streams[p], b->ev[2], 0);
     int next = 0;
     std::vector<int> pending;
     for (int i = 0; i < K; ++i) {
@@ -379,7 +381,7 @@ int lyap_batch_solve(lyap_batch* b, int autotune_flag, void* stream) {
       lyap_handle* h = b->h[i];
       b->done[i] = std::min(b->h_step[2 * i] - 1, o.maxit);
       if (checked[i] >= b->done[i]) continue;
-      const int p = next++ % kPools;
+      const int p = next++ % b->plan.npools;
       cudaStream_t sp = b->streams[p];
       h->check_ws = b->pool[p];
       const int si = b->s[i];
@@ -394,7 +396,7 @@ int lyap_batch_solve(lyap_batch* b, int autotune_flag, void* stream) {
       LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sp));
       pending.push_back(i);
     }
-    for (int p = 0; p < kPools; ++p) {
+    for (int p = 0; p < b->plan.npools; ++p) {
       cudaEventRecord(b->join[p], b->streams[p]);
       cudaStreamWaitEvent(st, b->join[p], 0);
     }
