@@ -643,9 +643,8 @@ __global__ void k_invit(CheckArgs g) {
     atomicOr(g.chk_err + m - 1, DERR_EIGEN);
     c = kMaxCluster;
   }
-  for (int v = 0; v < c; ++v)
-    for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i + v] = hash_unit((unsigned)k, (unsigned)(i + v));
   if (c == 1) {
+    for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] = hash_unit((unsigned)k, (unsigned)i);
     const double est = sl.est[i];
     const bool refined = tolc < sl.hdr[4];
     double sigma = est, rq = est, res = 0.0, prev = est, xscale = 1.0;
@@ -747,20 +746,61 @@ __device__ double lane_res2(const double* __restrict__ Tb, int N, const double* 
   return r2;
 }
 
-// 3b. groups of close estimates, one warp each: lane v iterates member v with its own estimate
-// as a fixed shift (a Rayleigh-quotient shift could carry the last member to the eigenvalue
-// just outside the group); the warp re-orthonormalises (MGS, twice) after every step and splits
-// the group by Rayleigh-Ritz between rounds, so the vectors of near-equal eigenvalues stay
-// orthonormal.  The members' vectors live contiguously in Xc (member i at Xc + i nmax), so the
-// warp's row loops coalesce.
+// the pack list of a slot sits in the unused tail of its cluster list (the list itself takes at
+// most 2 + N ints of the 2 nmax + 32): [0] number of packs, then the first group of each pack
+// and the end of the list
+__device__ __forceinline__ int* pack_list(const Slot& sl, int nmax) { return sl.clist + nmax + 8; }
+
+// 3a. groups packed greedily, in list order, into packs of at most 32 members (one warp each
+// in k_invit_clusters); one warp per check, the sizes read 32 at a time
+__global__ void k_pack_clusters(CheckArgs g) {
+  const int c_idx = blockIdx.x;
+  const int m = g.m_lo + c_idx;
+  if (!checked(g, m)) return;
+  Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
+  const int lane = threadIdx.x;
+  const int ncl = sl.clist[0];
+  int* pk = pack_list(sl, g.nmax);
+  int np = 0, tot = 0;
+  for (int base = 0; base < ncl; base += 32) {
+    const int cv = base + lane < ncl ? sl.clist[3 + 2 * (base + lane)] : 0;
+    const int n = min(32, ncl - base);
+    for (int t = 0; t < n; ++t) {
+      const int c = __shfl_sync(0xffffffffu, cv, t);
+      if (np == 0 || tot + c > 32) {
+        if (lane == 0) pk[1 + np] = base + t;
+        ++np;
+        tot = 0;
+      }
+      tot += c;
+    }
+  }
+  if (lane == 0) {
+    pk[1 + np] = ncl;
+    pk[0] = np;
+  }
+}
+
+// 3b. groups of close estimates.  Lane v of a group iterates member v with its own estimate as
+// a fixed shift (a Rayleigh-quotient shift could carry the last member to the eigenvalue just
+// outside the group); after every step the group is re-orthonormalised (MGS, twice), and between
+// rounds it is split by Rayleigh-Ritz, so the vectors of near-equal eigenvalues stay orthonormal.
+// One warp takes a pack of groups (up to 32 members): the banded solves, which dominate, run on
+// all the pack's lanes at once (the fp64 pipe spends the same time on a warp instruction
+// whatever its active lanes), and the warp-wide orthonormalisation and Rayleigh-Ritz steps take
+// the pack's groups in turn.  Every group keeps its own round state, so its result does not
+// depend on the pack it lands in.  The members' vectors live contiguously in Xc (member i at
+// Xc + i nmax), so the row loops coalesce.
 template <int S>
 __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   constexpr int WPB = 4;
+  constexpr int kPackMax = 16;  // groups per pack (every group has at least two members)
+  enum : int { kDone = 1, kPolish = 2, kFin = 4, kOvf = 8, kF64 = 16 };
   __shared__ double Hs[WPB][kMaxCluster][kMaxCluster];
   __shared__ double Vs[WPB][kMaxCluster][kMaxCluster];
-  __shared__ double sh[WPB][kMaxCluster];
-  __shared__ double th[WPB][kMaxCluster];
+  __shared__ double ths[WPB][32];  // Ritz values by member lane
   __shared__ int ords[WPB][kMaxCluster];
+  __shared__ int qis[WPB][kPackMax], qcs[WPB][kPackMax], qos[WPB][kPackMax], qss[WPB][kPackMax];
   const int c_idx = blockIdx.y;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
@@ -770,181 +810,226 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const double tnorm = sl.hdr[3] * fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
   const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
-  const int ncl = sl.clist[0];
+  const int* pk = pack_list(sl, g.nmax);
+  const int npk = pk[0];
   double (*H)[kMaxCluster] = Hs[w];
   double (*V)[kMaxCluster] = Vs[w];
-  double* shift = sh[w];
-  double* theta = th[w];
+  double* theta = ths[w];
   int* ord = ords[w];
-  for (int e = blockIdx.x * WPB + w; e < ncl; e += gridDim.x * WPB) {
-    const int i = sl.clist[2 + 2 * e], c = sl.clist[3 + 2 * e];
-    double* xc = sl.Xc + (size_t)i * ld;  // member v at xc + v ld
-    if (lane < c) shift[lane] = sl.est[i + lane];
-    for (int v = 0; v < c; ++v)
-      for (int k = lane; k < N; k += 32) xc[(size_t)v * ld + k] = hash_unit((unsigned)k, (unsigned)(i + v));
-    __syncwarp();
-    bool done = false;
-#ifdef LYAP_DEBUG
-    double dbg_res[kMaxRounds] = {0, 0, 0, 0};
-#endif
-    // rounds at the fixed shifts until every member's residual passes, then one polishing round
-    // at the Ritz values (Rayleigh-quotient shifts once the subspace is right)
-    bool polish = false;
-    int rounds32 = kRounds32;  // set to 0 (fresh fp64 start) if an fp32 round overflows
-    bool overflow = false;
-    for (int round = 0; round < kMaxRounds + 1; ++round) {
-      if (done) {
-        if (polish) break;
-        polish = true;
-        if (lane < c) shift[lane] = theta[lane];
-        __syncwarp();
-      } else if (round == kMaxRounds) {
-        break;
+  int* qi = qis[w];  // first eigenvalue index of each group of the pack
+  int* qc = qcs[w];  // its size
+  int* qo = qos[w];  // its first lane
+  int* qs = qss[w];  // its state bits
+  for (int p = blockIdx.x * WPB + w; p < npk; p += gridDim.x * WPB) {
+    const int e0 = pk[1 + p], nq = pk[2 + p] - e0;
+    int myq = -1, myv = 0, off = 0;
+    for (int q = 0; q < nq; ++q) {
+      const int i = sl.clist[2 + 2 * (e0 + q)], c = sl.clist[3 + 2 * (e0 + q)];
+      if (lane >= off && lane < off + c) {
+        myq = q;
+        myv = lane - off;
       }
-      for (int it = 0; it < (polish ? 1 : 2); ++it) {
-        if (lane < c) {
-          if (round < rounds32 && !polish)
-            solve1<S, float>(sl.Tb, N, shift[lane], FLT_EPSILON * (float)tnorm + FLT_MIN, 1.0, xc + (size_t)lane * ld, 1, 0,
-                             reinterpret_cast<float*>(sl.U), i + lane, ld);
-          else
-            solve1<S>(sl.Tb, N, shift[lane], tiny, 1.0, xc + (size_t)lane * ld, 1, 0, sl.U, i + lane, ld);
-        }
-        __syncwarp();
-        for (int pass = 0; pass < 2; ++pass)
-          for (int v = 0; v < c; ++v) {
-            double* xv = xc + (size_t)v * ld;
-            for (int u = 0; u < v; ++u) {
-              const double* xu = xc + (size_t)u * ld;
-              double d = 0.0;
-              for (int k = lane; k < N; k += 32) d = fma(xu[k], xv[k], d);
-              d = warp_sum(d);
-              for (int k = lane; k < N; k += 32) xv[k] = fma(-d, xu[k], xv[k]);
-              __syncwarp();
-            }
-            double n2 = 0.0;
-            for (int k = lane; k < N; k += 32) n2 = fma(xv[k], xv[k], n2);
-            n2 = warp_sum(n2);
-            const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-            for (int k = lane; k < N; k += 32) xv[k] *= inv;
-            __syncwarp();
-            if (!isfinite(n2) && round < rounds32) overflow = true;
-          }
-      }
-      if (overflow) {
-        // fp32 growth overflowed: restart the group in fp64 from fresh vectors
-        overflow = false;
-        rounds32 = 0;
-        for (int v = 0; v < c; ++v)
-          for (int k = lane; k < N; k += 32) xc[(size_t)v * ld + k] = hash_unit((unsigned)k, (unsigned)(i + v));
-        __syncwarp();
-        continue;
-      }
-      // Rayleigh-Ritz
-      for (int u = 0; u < c; ++u)
-        for (int v = u; v < c; ++v) {
-          const double h = warp_sum(lane_xTy<S>(sl.Tb, N, xc + (size_t)u * ld, xc + (size_t)v * ld, lane));
-          if (lane == 0) {
-            H[u][v] = h;
-            H[v][u] = h;
-          }
-        }
-      __syncwarp();
       if (lane == 0) {
-        for (int u = 0; u < c; ++u)
-          for (int v = 0; v < c; ++v) V[u][v] = u == v ? 1.0 : 0.0;
-        for (int sweep = 0; sweep < 30; ++sweep) {
-          double off = 0.0, tot = 0.0;
-          for (int u = 0; u < c; ++u)
+        qi[q] = i;
+        qc[q] = c;
+        qo[q] = off;
+        qs[q] = 0;
+      }
+      off += c;
+    }
+    __syncwarp();
+    const int me = myq >= 0 ? qi[myq] + myv : 0;  // eigenvalue index of the lane's member
+    double shift = myq >= 0 ? sl.est[me] : 0.0;
+    double* xme = sl.Xc + (size_t)me * ld;
+    for (int q = 0; q < nq; ++q)
+      for (int v = 0; v < qc[q]; ++v)
+        for (int k = lane; k < N; k += 32)
+          sl.Xc[(size_t)(qi[q] + v) * ld + k] = hash_unit((unsigned)k, (unsigned)(qi[q] + v));
+    __syncwarp();
+    // rounds at the fixed shifts until every member's residual passes, then one polishing round
+    // at the Ritz values (Rayleigh-quotient shifts once the subspace is right); a group whose
+    // fp32 round overflows restarts in fp64 from fresh vectors
+    for (int round = 0; round < kMaxRounds + 1; ++round) {
+      bool any = false;
+      for (int q = 0; q < nq; ++q) {
+        int st = qs[q];
+        if (!(st & kFin)) {
+          if (st & kDone) st |= (st & kPolish) ? kFin : kPolish;
+          else if (round == kMaxRounds) st |= kFin;
+        }
+        any = any || !(st & kFin);
+        __syncwarp();
+        if (lane == 0) qs[q] = st;
+      }
+      __syncwarp();
+      if (!any) break;
+      const int mst = myq >= 0 ? qs[myq] : kFin;
+      const bool live = !(mst & kFin);
+      const bool pol = live && (mst & kPolish);
+      const int r32 = (mst & kF64) ? 0 : kRounds32;
+      if (pol) shift = theta[lane];
+      for (int it = 0; it < 2; ++it) {
+        if (live && (it == 0 || !pol)) {
+          if (round < r32 && !pol)
+            solve1<S, float>(sl.Tb, N, shift, FLT_EPSILON * (float)tnorm + FLT_MIN, 1.0, xme, 1, 0,
+                             reinterpret_cast<float*>(sl.U), me, ld);
+          else
+            solve1<S>(sl.Tb, N, shift, tiny, 1.0, xme, 1, 0, sl.U, me, ld);
+        }
+        __syncwarp();
+        for (int q = 0; q < nq; ++q) {
+          const int st = qs[q];
+          if ((st & kFin) || (it == 1 && (st & kPolish))) continue;
+          const int c = qc[q];
+          const bool low = round < ((st & kF64) ? 0 : kRounds32);
+          double* xc = sl.Xc + (size_t)qi[q] * ld;
+          bool ovf = false;
+          for (int pass = 0; pass < 2; ++pass)
             for (int v = 0; v < c; ++v) {
-              tot += H[u][v] * H[u][v];
-              if (u != v) off += H[u][v] * H[u][v];
-            }
-          if (!(off > 1e-32 * tot)) break;
-          for (int p = 0; p < c; ++p)
-            for (int q = p + 1; q < c; ++q) {
-              if (H[p][q] == 0.0) continue;
-              const double th = (H[q][q] - H[p][p]) / (2.0 * H[p][q]);
-              const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-              const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
-              for (int k = 0; k < c; ++k) {
-                const double hp = H[p][k], hq = H[q][k];
-                H[p][k] = cs * hp - sn * hq;
-                H[q][k] = sn * hp + cs * hq;
+              double* xv = xc + (size_t)v * ld;
+              for (int u = 0; u < v; ++u) {
+                const double* xu = xc + (size_t)u * ld;
+                double d = 0.0;
+                for (int k = lane; k < N; k += 32) d = fma(xu[k], xv[k], d);
+                d = warp_sum(d);
+                for (int k = lane; k < N; k += 32) xv[k] = fma(-d, xu[k], xv[k]);
+                __syncwarp();
               }
-              for (int k = 0; k < c; ++k) {
-                const double hp = H[k][p], hq = H[k][q];
-                H[k][p] = cs * hp - sn * hq;
-                H[k][q] = sn * hp + cs * hq;
-                const double vp = V[k][p], vq = V[k][q];
-                V[k][p] = cs * vp - sn * vq;
-                V[k][q] = sn * vp + cs * vq;
-              }
+              double n2 = 0.0;
+              for (int k = lane; k < N; k += 32) n2 = fma(xv[k], xv[k], n2);
+              n2 = warp_sum(n2);
+              const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+              for (int k = lane; k < N; k += 32) xv[k] *= inv;
+              __syncwarp();
+              if (!isfinite(n2) && low) ovf = true;
             }
-        }
-        for (int v = 0; v < c; ++v) ord[v] = v;
-        for (int a = 1; a < c; ++a) {
-          const int t = ord[a];
-          int b = a - 1;
-          while (b >= 0 && H[ord[b]][ord[b]] > H[t][t]) {
-            ord[b + 1] = ord[b];
-            --b;
+          if (ovf) {
+            __syncwarp();
+            if (lane == 0) qs[q] = st | kOvf;
           }
-          ord[b + 1] = t;
+          __syncwarp();
         }
-        for (int v = 0; v < c; ++v) theta[v] = H[ord[v]][ord[v]];
       }
-      __syncwarp();
-      for (int k = lane; k < N; k += 32) {
-        double row[kMaxCluster], out[kMaxCluster];
-        for (int v = 0; v < c; ++v) row[v] = xc[(size_t)v * ld + k];
+      for (int q = 0; q < nq; ++q) {
+        const int st = qs[q];
+        if (st & kFin) continue;
+        const int c = qc[q], i = qi[q];
+        double* xc = sl.Xc + (size_t)i * ld;
+        if (st & kOvf) {
+          for (int v = 0; v < c; ++v)
+            for (int k = lane; k < N; k += 32) xc[(size_t)v * ld + k] = hash_unit((unsigned)k, (unsigned)(i + v));
+          __syncwarp();
+          if (lane == 0) qs[q] = (st & ~kOvf) | kF64;
+          __syncwarp();
+          continue;
+        }
+        // Rayleigh-Ritz
+        for (int u = 0; u < c; ++u)
+          for (int v = u; v < c; ++v) {
+            const double h = warp_sum(lane_xTy<S>(sl.Tb, N, xc + (size_t)u * ld, xc + (size_t)v * ld, lane));
+            if (lane == 0) {
+              H[u][v] = h;
+              H[v][u] = h;
+            }
+          }
+        __syncwarp();
+        if (lane == 0) {
+          for (int u = 0; u < c; ++u)
+            for (int v = 0; v < c; ++v) V[u][v] = u == v ? 1.0 : 0.0;
+          for (int sweep = 0; sweep < 30; ++sweep) {
+            double offd = 0.0, tot = 0.0;
+            for (int u = 0; u < c; ++u)
+              for (int v = 0; v < c; ++v) {
+                tot += H[u][v] * H[u][v];
+                if (u != v) offd += H[u][v] * H[u][v];
+              }
+            if (!(offd > 1e-32 * tot)) break;
+            for (int a = 0; a < c; ++a)
+              for (int b = a + 1; b < c; ++b) {
+                if (H[a][b] == 0.0) continue;
+                const double tq = (H[b][b] - H[a][a]) / (2.0 * H[a][b]);
+                const double t = (tq >= 0 ? 1.0 : -1.0) / (fabs(tq) + sqrt(tq * tq + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < c; ++k) {
+                  const double ha = H[a][k], hb = H[b][k];
+                  H[a][k] = cs * ha - sn * hb;
+                  H[b][k] = sn * ha + cs * hb;
+                }
+                for (int k = 0; k < c; ++k) {
+                  const double ha = H[k][a], hb = H[k][b];
+                  H[k][a] = cs * ha - sn * hb;
+                  H[k][b] = sn * ha + cs * hb;
+                  const double va = V[k][a], vb = V[k][b];
+                  V[k][a] = cs * va - sn * vb;
+                  V[k][b] = sn * va + cs * vb;
+                }
+              }
+          }
+          for (int v = 0; v < c; ++v) ord[v] = v;
+          for (int a = 1; a < c; ++a) {
+            const int t = ord[a];
+            int b = a - 1;
+            while (b >= 0 && H[ord[b]][ord[b]] > H[t][t]) {
+              ord[b + 1] = ord[b];
+              --b;
+            }
+            ord[b + 1] = t;
+          }
+          for (int v = 0; v < c; ++v) theta[qo[q] + v] = H[ord[v]][ord[v]];
+        }
+        __syncwarp();
+        for (int k = lane; k < N; k += 32) {
+          double row[kMaxCluster], out[kMaxCluster];
+          for (int v = 0; v < c; ++v) row[v] = xc[(size_t)v * ld + k];
+          for (int v = 0; v < c; ++v) {
+            double t = 0.0;
+            for (int u = 0; u < c; ++u) t = fma(row[u], V[u][ord[v]], t);
+            out[v] = t;
+          }
+          for (int v = 0; v < c; ++v) xc[(size_t)v * ld + k] = out[v];
+        }
+        __syncwarp();
+        if (round < ((st & kF64) ? 0 : kRounds32) || (st & kPolish)) continue;
+        // the group has converged once every member's residual passes
+        bool ok = true;
         for (int v = 0; v < c; ++v) {
-          double t = 0.0;
-          for (int u = 0; u < c; ++u) t = fma(row[u], V[u][ord[v]], t);
-          out[v] = t;
+          const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xc + (size_t)v * ld, theta[qo[q] + v], lane));
+          ok = ok && sqrt(r2) <= kResTol * tnorm;
         }
-        for (int v = 0; v < c; ++v) xc[(size_t)v * ld + k] = out[v];
+        if (ok && lane == 0) qs[q] = st | kDone;
+        __syncwarp();
       }
-      __syncwarp();
-      if (round < rounds32 || polish) continue;
-      // converged once every member's residual passes
-      bool ok = true;
-      for (int v = 0; v < c; ++v) {
-        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xc + (size_t)v * ld, theta[v], lane));
-        ok = ok && sqrt(r2) <= kResTol * tnorm;
-#ifdef LYAP_DEBUG
-        dbg_res[round] = fmax(dbg_res[round], sqrt(r2));
-#endif
-      }
-      done = ok;
     }
     // final Rayleigh quotients and residual test; the first and last S rows go back to X for
     // the a and w rows
-    for (int v = 0; v < c; ++v) {
-      const double* xv = xc + (size_t)v * ld;
-      const double num = warp_sum(lane_xTy<S>(sl.Tb, N, xv, xv, lane));
-      const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xv, num, lane));
-      if (lane < S) {
-        sl.X[(size_t)lane * ld + i + v] = xv[lane];
-        sl.X[(size_t)(N - S + lane) * ld + i + v] = xv[N - S + lane];
-      }
-      if (lane == 0) {
-        sl.lam[i + v] = num;
-        const bool inside = num >= sl.est[i] - 0.5 * sl.etol[i] && num <= sl.est[i + c - 1] + 0.5 * sl.etol[i + c - 1];
-        if (!(sqrt(r2) <= kResTol * tnorm) || !isfinite(num) || !inside) {
-          atomicOr(g.chk_err + m - 1, DERR_EIGEN);
+    for (int q = 0; q < nq; ++q) {
+      const int i = qi[q], c = qc[q];
+      for (int v = 0; v < c; ++v) {
+        const double* xv = sl.Xc + (size_t)(i + v) * ld;
+        const double num = warp_sum(lane_xTy<S>(sl.Tb, N, xv, xv, lane));
+        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xv, num, lane));
+        if (lane < S) {
+          sl.X[(size_t)lane * ld + i + v] = xv[lane];
+          sl.X[(size_t)(N - S + lane) * ld + i + v] = xv[N - S + lane];
+        }
+        if (lane == 0) {
+          sl.lam[i + v] = num;
+          const bool inside =
+              num >= sl.est[i] - 0.5 * sl.etol[i] && num <= sl.est[i + c - 1] + 0.5 * sl.etol[i + c - 1];
+          if (!(sqrt(r2) <= kResTol * tnorm) || !isfinite(num) || !inside) {
+            atomicOr(g.chk_err + m - 1, DERR_EIGEN);
 #ifdef LYAP_DEBUG
-          printf("eig fail m=%d N=%d i=%d c=%d v=%d rq=%.17g res=%.3e tnorm=%.3e est[i-1..i+c]=%.6f %.6f %.6f %.6f etol=%.4g "
-                 "rounds %.3e %.3e %.3e %.3e shifts %.6f %.6f theta %.6f %.6f\n",
-                 m, N, i, c, v, num, sqrt(r2), tnorm, i > 0 ? sl.est[i - 1] : 0.0, sl.est[i], sl.est[i + c - 1],
-                 i + c < N ? sl.est[i + c] : 0.0, sl.etol[i], dbg_res[0], dbg_res[1], dbg_res[2], dbg_res[3],
-                 shift[0], shift[c - 1], theta[0], theta[c - 1]);
+            printf("eig fail m=%d N=%d i=%d c=%d v=%d rq=%.17g res=%.3e tnorm=%.3e est[i]=%.17g est[i+c-1]=%.17g "
+                   "etol=%.4g state=%d\n",
+                   m, N, i, c, v, num, sqrt(r2), tnorm, sl.est[i], sl.est[i + c - 1], sl.etol[i], qs[q]);
 #endif
+          }
         }
       }
+      __syncwarp();
+      if (lane == 0) write_aw<S>(g, sl, m, N, ld, i, c);
+      __syncwarp();
     }
-    __syncwarp();
-    if (lane == 0) write_aw<S>(g, sl, m, N, ld, i, c);
-    __syncwarp();
   }
 }
 
@@ -1120,16 +1205,25 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
     case 4: k_refine64<4><<<gv, 32, 0, st>>>(g); break;
     case 8: k_refine64<8><<<gv, 32, 0, st>>>(g); break;
   }
-  // clusters: 16 blocks of 4 warps per check, each warp takes clusters from the list in turn
+  switch (g.s) {
+    case 1: k_invit<1><<<gv, 32, 0, st>>>(g); break;
+    case 2: k_invit<2><<<gv, 32, 0, st>>>(g); break;
+    case 3: k_invit<3><<<gv, 32, 0, st>>>(g); break;
+    case 4: k_invit<4><<<gv, 32, 0, st>>>(g); break;
+    case 8: k_invit<8><<<gv, 32, 0, st>>>(g); break;
+  }
+  // groups: packed into warps of up to 32 members; 16 blocks of 4 warps per check take the packs
+  // in turn
+  k_pack_clusters<<<g.nchk, 32, 0, st>>>(g);
   dim3 gc(16, g.nchk);
   switch (g.s) {
-    case 1: k_invit<1><<<gv, 32, 0, st>>>(g); k_invit_clusters<1><<<gc, 128, 0, st>>>(g); break;
-    case 2: k_invit<2><<<gv, 32, 0, st>>>(g); k_invit_clusters<2><<<gc, 128, 0, st>>>(g); break;
-    case 3: k_invit<3><<<gv, 32, 0, st>>>(g); k_invit_clusters<3><<<gc, 128, 0, st>>>(g); break;
-    case 4: k_invit<4><<<gv, 32, 0, st>>>(g); k_invit_clusters<4><<<gc, 128, 0, st>>>(g); break;
-    case 8: k_invit<8><<<gv, 32, 0, st>>>(g); k_invit_clusters<8><<<gc, 128, 0, st>>>(g); break;
+    case 1: k_invit_clusters<1><<<gc, 128, 0, st>>>(g); break;
+    case 2: k_invit_clusters<2><<<gc, 128, 0, st>>>(g); break;
+    case 3: k_invit_clusters<3><<<gc, 128, 0, st>>>(g); break;
+    case 4: k_invit_clusters<4><<<gc, 128, 0, st>>>(g); break;
+    case 8: k_invit_clusters<8><<<gc, 128, 0, st>>>(g); break;
   }
-  return 6;
+  return 7;
 }
 
 }  // namespace
