@@ -36,6 +36,8 @@ constexpr int kBandThreads = 512;
 constexpr int kGroup = 8;    // lanes per concurrent Givens rotation
 constexpr int kDelta = 4;    // stage lag between consecutive sweeps (non-overlapping windows for b >= 2)
 constexpr int kMaxCluster = 16;
+constexpr int kClusterBlocks = 16;  // blocks per check of k_invit_clusters
+constexpr int kClusterWarps = 64;   // warps per check of k_invit_clusters (4 per block)
 // Members of a cluster of fp32 estimates larger than this (a spectrum far wider than its
 // smallest gaps, or near-duplicate Ritz values) get fp64 estimates by bisection with Sturm
 // counts on the fp64 band, and are then grouped at the fp64 tolerance.
@@ -751,9 +753,12 @@ __device__ double lane_res2(const double* __restrict__ Tb, int N, const double* 
 // and the end of the list
 __device__ __forceinline__ int* pack_list(const Slot& sl, int nmax) { return sl.clist + nmax + 8; }
 
-// 3a. groups packed greedily, in list order, into packs of at most 32 members (one warp each
-// in k_invit_clusters); one warp per check, the sizes read 32 at a time
-__global__ void k_pack_clusters(CheckArgs g) {
+// 3a. groups packed greedily, in list order, into packs (one warp each in k_invit_clusters) of at
+// most `cap` members, a larger group alone.  When the launch holds more warps than the GPU keeps
+// resident (`dense`), the fp64 pipe is the limit and packs take up to 32 members; otherwise the
+// members are spread evenly over the 64 warps a check gets (latency is the limit there).  One
+// warp per check, the sizes read 32 at a time.
+__global__ void k_pack_clusters(CheckArgs g, int dense) {
   const int c_idx = blockIdx.x;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
@@ -761,13 +766,24 @@ __global__ void k_pack_clusters(CheckArgs g) {
   const int lane = threadIdx.x;
   const int ncl = sl.clist[0];
   int* pk = pack_list(sl, g.nmax);
+  int cap = 32;
+  if (!dense) {
+    int tm = 0;
+    for (int base = 0; base < ncl; base += 32) {
+      int cv = base + lane < ncl ? sl.clist[3 + 2 * (base + lane)] : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cv += __shfl_xor_sync(0xffffffffu, cv, o);
+      tm += cv;
+    }
+    cap = min(32, max(2, (tm + kClusterWarps - 1) / kClusterWarps));
+  }
   int np = 0, tot = 0;
   for (int base = 0; base < ncl; base += 32) {
     const int cv = base + lane < ncl ? sl.clist[3 + 2 * (base + lane)] : 0;
     const int n = min(32, ncl - base);
     for (int t = 0; t < n; ++t) {
       const int c = __shfl_sync(0xffffffffu, cv, t);
-      if (np == 0 || tot + c > 32) {
+      if (np == 0 || tot + c > cap) {
         if (lane == 0) pk[1 + np] = base + t;
         ++np;
         tot = 0;
@@ -793,7 +809,7 @@ __global__ void k_pack_clusters(CheckArgs g) {
 // Xc + i nmax), so the row loops coalesce.
 template <int S>
 __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
-  constexpr int WPB = 4;
+  constexpr int WPB = kClusterWarps / kClusterBlocks;
   constexpr int kPackMax = 16;  // groups per pack (every group has at least two members)
   enum : int { kDone = 1, kPolish = 2, kFin = 4, kOvf = 8, kF64 = 16 };
   __shared__ double Hs[WPB][kMaxCluster][kMaxCluster];
@@ -1213,9 +1229,17 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
     case 8: k_invit<8><<<gv, 32, 0, st>>>(g); break;
   }
   // groups: packed into warps of up to 32 members; 16 blocks of 4 warps per check take the packs
-  // in turn
-  k_pack_clusters<<<g.nchk, 32, 0, st>>>(g);
-  dim3 gc(16, g.nchk);
+  // in turn (the SM count is read once: a process uses one GPU model)
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  // two blocks of k_invit_clusters (254 registers a thread) fit on an SM
+  k_pack_clusters<<<g.nchk, 32, 0, st>>>(g, g.nchk * kClusterWarps >= 8 * sms);
+  dim3 gc(kClusterBlocks, g.nchk);
   switch (g.s) {
     case 1: k_invit_clusters<1><<<gc, 128, 0, st>>>(g); break;
     case 2: k_invit_clusters<2><<<gc, 128, 0, st>>>(g); break;

@@ -114,12 +114,11 @@ __device__ __forceinline__ void store_row(double* __restrict__ X, int64_t ld, in
 // entry order of the row in every case (identical bits in both passes).
 constexpr int kUnroll = 8;
 template <typename T, int S>
-__device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lane, const T* __restrict__ Vc,
-                                         int64_t ldc, T (&w)[S]) {
+__device__ __forceinline__ void sell_row_at(const OpDev& op, int64_t slice_ptr, int width, int lane,
+                                            const T* __restrict__ Vc, int64_t ldc, T (&w)[S]) {
 #pragma unroll
   for (int a = 0; a < S; ++a) w[a] = T(0);
-  const int64_t base = op.slice_ptr[slice] + lane;
-  const int width = op.slice_w[slice];
+  const int64_t base = slice_ptr + lane;
   const T* __restrict__ val = static_cast<const T*>(op.sell_val);
   for (int j0 = 0; j0 < width; j0 += kUnroll) {
     int32_t c[kUnroll];
@@ -139,6 +138,12 @@ __device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lan
 #pragma unroll
       for (int a = 0; a < S; ++a) w[a] = fma(v[u], x[u][a], w[a]);
   }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void sell_row(const OpDev& op, int64_t slice, int lane, const T* __restrict__ Vc,
+                                         int64_t ldc, T (&w)[S]) {
+  sell_row_at<T, S>(op, op.slice_ptr[slice], op.slice_w[slice], lane, Vc, ldc, w);
 }
 
 
@@ -274,25 +279,116 @@ __device__ void load_coefs(Coefs<T, S>& co, const double* __restrict__ rec, int 
   __syncthreads();
 }
 
-// ---- deterministic block reduction + last-CTA finalisation ------------------------
+// ---- deterministic two-stage reductions ----------------------------------------------
+// Stage 1 (every CTA): the threads' accumulators are summed by warp shuffles in a fixed order,
+// then over the warps in order, into the CTA's slot of the partials array.  Stage 2 (one CTA):
+// warp w sums coefficients w, w + kWarps, ...; its lanes stride over the slots and combine in a
+// fixed shuffle order, so the result does not depend on timing.
+//
+// GB300 runs fp64 at a small fraction of its fp32 rate (a warp instruction holds the SM's fp64
+// pipe for about 16 cycles whatever its active lanes), so with fp32 accumulators both stages
+// stay on the fp32 pipe: a partial is an unevaluated pair hi + lo of floats, and pairs are
+// added with Knuth's TwoSum, which yields the exact rounding error of each addition (about 44
+// significant bits, far below the fp32 rounding of the sweep data).  A slot holds the pair in
+// the 8 bytes of a double.  fp64 accumulators keep fp64 throughout.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return FF{hi, e - (hi - s)};
+}
+
+// Slots are stored coefficient-major, P[k * count + slot], so stage 2 reads each coefficient's
+// slots with coalesced loads.
+//
+// stage 1: this CTA's sums of acc -> P[k * count + slot] (a float pair for fp32 accumulators);
+// scratch holds kWarps * NACC doubles (shared memory).  Ends with the sums written by the
+// threads k < NACC (no barrier after the writes).
 template <typename Acc, int NACC>
-__device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials, unsigned int* counter,
-                                double* __restrict__ tot /*smem NACC*/, double* __restrict__ scratch /*smem kWarps*NACC*/,
-                                unsigned int slot, unsigned int count) {
+__device__ void cta_partial(Acc (&acc)[NACC], double* __restrict__ P, unsigned int slot, unsigned int count,
+                            double* __restrict__ scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Acc* sc = reinterpret_cast<Acc*>(scratch);
 #pragma unroll
   for (int k = 0; k < NACC; ++k) {
     Acc v = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) scratch[warp * NACC + k] = (double)v;
+    if (lane == 0) sc[warp * NACC + k] = v;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
-    double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += scratch[w * NACC + k];
-    partials[(size_t)slot * NACC + k] = t;
+    if constexpr (sizeof(Acc) == sizeof(float)) {
+      FF t{0.f, 0.f};
+      for (int w = 0; w < kWarps; ++w) t = ff_add(t, FF{sc[w * NACC + k], 0.f});
+      reinterpret_cast<float2*>(P)[(size_t)k * count + slot] = make_float2(t.hi, t.lo);
+    } else {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += sc[w * NACC + k];
+      P[(size_t)k * count + slot] = t;
+    }
   }
+}
+
+// stage 2: tot[k] = sum over slots b < count of P[k * count + b]; lane l adds the slots
+// l, l + 32, ... in order, loading eight at a time (independent loads in flight together);
+// ends with a barrier
+template <typename Acc, int NACC>
+__device__ void sum_slots(const double* __restrict__ P, unsigned int count, double* __restrict__ tot) {
+  constexpr int kB = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < NACC; k += kWarps) {
+    if constexpr (sizeof(Acc) == sizeof(float)) {
+      const float2* col = reinterpret_cast<const float2*>(P) + (size_t)k * count;
+      FF t{0.f, 0.f};
+      for (unsigned int b0 = 0; b0 < count; b0 += 32 * kB) {
+        float2 v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const unsigned int b = b0 + 32 * u + lane;
+          v[u] = b < count ? __ldcg(col + b) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) t = ff_add(t, FF{v[u].x, v[u].y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const FF u{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+        t = ff_add(t, u);
+      }
+      if (lane == 0) tot[k] = (double)t.hi + (double)t.lo;
+    } else {
+      const double* col = P + (size_t)k * count;
+      double t = 0.0;
+      for (unsigned int b0 = 0; b0 < count; b0 += 32 * kB) {
+        double v[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const unsigned int b = b0 + 32 * u + lane;
+          v[u] = b < count ? __ldcg(col + b) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) t += v[u];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) tot[k] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// stage 1 into this CTA's slot, then stage 2 by the last CTA to arrive (returns true there)
+template <typename Acc, int NACC>
+__device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials, unsigned int* counter,
+                                double* __restrict__ tot /*smem NACC*/, double* __restrict__ scratch /*smem kWarps*NACC*/,
+                                unsigned int slot, unsigned int count) {
+  cta_partial<Acc, NACC>(acc, partials, slot, count, scratch);
   __threadfence();
   __shared__ unsigned int ticket;
   __syncthreads();
@@ -300,16 +396,7 @@ __device__ bool reduce_partials(Acc (&acc)[NACC], double* __restrict__ partials,
   __syncthreads();
   if (ticket != count - 1) return false;
   __threadfence();
-  // warp w sums coefficients k = w, w + kWarps, ...; its lanes stride over the CTAs and
-  // combine in a fixed shuffle order, so the result does not depend on timing
-  for (int k = warp; k < NACC; k += kWarps) {
-    double t = 0.0;
-    for (unsigned int b = lane; b < count; b += 32) t += __ldcg(partials + (size_t)b * NACC + k);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) tot[k] = t;
-  }
-  __syncthreads();
+  sum_slots<Acc, NACC>(partials, count, tot);
   if (threadIdx.x == 0) *counter = 0u;
   return true;
 }
@@ -423,6 +510,20 @@ __device__ void finalize_s3(double* rw, const double* tot, int* flags) {
   if (!all_finite<S>(Tn, SS)) atomicOr(flags, DERR_NONFINITE);
 }
 
+// rows of W, V_j and V_{j-1} (zero without a previous block)
+template <typename T, int S>
+__device__ __forceinline__ void load3(const T* __restrict__ W, const T* __restrict__ Vc, int64_t ldc,
+                                      const T* __restrict__ Vp, int64_t ldp, bool hp, int64_t row, T (&w)[S],
+                                      T (&q)[S], T (&p)[S]) {
+  load_row<S>(W, (int64_t)S, row, w);
+  load_row<S>(Vc, ldc, row, q);
+  if (hp) load_row<S>(Vp, ldp, row, p);
+  else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) p[a] = T(0);
+  }
+}
+
 // ---- sweep kernels -----------------------------------------------------------
 struct SweepArgs {
   OpDev op;
@@ -449,12 +550,26 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_spmm_proj(Swe
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  // the next slice's metadata is loaded one slice ahead, so a slice starts with its column
+  // indices and values instead of a round trip for its offset and width
+  int64_t nptr = 0;
+  int nwid = 0;
+  if (gwarp < g.op.nslices) {
+    nptr = g.op.slice_ptr[gwarp];
+    nwid = g.op.slice_w[gwarp];
+  }
   for (int64_t sl = gwarp; sl < g.op.nslices; sl += nwarps) {
+    const int64_t cptr = nptr;
+    const int cwid = nwid;
+    if (sl + nwarps < g.op.nslices) {
+      nptr = g.op.slice_ptr[sl + nwarps];
+      nwid = g.op.slice_w[sl + nwarps];
+    }
     const int64_t rs = sl * LYAP_SLICE + lane;
     const int64_t row = g.op.perm ? (rs < g.op.n ? (int64_t)g.op.perm[rs] : g.op.n) : rs;
     if (row < g.op.n) {
       T w[S];
-      sell_row<T, S>(g.op, sl, lane, Vc, g.ldc, w);
+      sell_row_at<T, S>(g.op, cptr, cwid, lane, Vc, g.ldc, w);
       store_row<S>(W, (int64_t)S, row, w);
       T q[S], p[S];
       load_row<S>(Vc, g.ldc, row, q);
@@ -543,13 +658,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_gram2(SweepAr
   const bool hp = g.has_prev;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
     T w[S], p[S], q[S];
-    load_row<S>(W, (int64_t)S, row, w);
-    load_row<S>(Vc, g.ldc, row, q);
-    if (hp) load_row<S>(Vp, g.ldp, row, p);
-    else {
-#pragma unroll
-      for (int a = 0; a < S; ++a) p[a] = T(0);
-    }
+    load3<T, S>(W, Vc, g.ldc, Vp, g.ldp, hp, row, w, q, p);
     mgs_row<T, S>(p, q, co.tp, co.td, w, hp);
     trsm_row<T, S>(co.r1, co.r1i, w);
 #pragma unroll
@@ -577,13 +686,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_write_next(Sw
   const bool hp = g.has_prev;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n; row += (int64_t)gridDim.x * blockDim.x) {
     T w[S], p[S], q[S];
-    load_row<S>(W, (int64_t)S, row, w);
-    load_row<S>(Vc, g.ldc, row, q);
-    if (hp) load_row<S>(Vp, g.ldp, row, p);
-    else {
-#pragma unroll
-      for (int a = 0; a < S; ++a) p[a] = T(0);
-    }
+    load3<T, S>(W, Vc, g.ldc, Vp, g.ldp, hp, row, w, q, p);
     next_row<T, S>(co, p, q, w, hp);
     store_row<S>(Vn, g.ldn, row, w);
   }
@@ -988,38 +1091,17 @@ __device__ bool grid_sync(unsigned int* bar, unsigned int nblocks, int* flags) {
   return s_ok != 0;
 }
 
-// this CTA's sums of the per-thread accumulators (fixed order) -> dst[NACC]
+// this CTA's sums of the per-thread accumulators -> its slot of P, exactly as the sweeps' stage 1
 template <typename Acc, int NACC>
-__device__ void cta_reduce_to(Acc (&acc)[NACC], double* __restrict__ dst, double* __restrict__ scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NACC; ++k) {
-    Acc v = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) scratch[warp * NACC + k] = (double)v;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < NACC; k += blockDim.x) {
-    double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += scratch[w * NACC + k];
-    dst[k] = t;
-  }
+__device__ void cta_reduce_to(Acc (&acc)[NACC], double* __restrict__ P, unsigned int G, double* __restrict__ scratch) {
+  cta_partial<Acc, NACC>(acc, P, blockIdx.x, G, scratch);
   __syncthreads();
 }
 
-// tot[k] = sum over CTAs b of P[b][k] in the order of the last-CTA reduction of the sweeps
-template <int NACC>
+// tot[k] = sum over CTAs b of P[b][k], exactly as the sweeps' stage 2
+template <typename Acc, int NACC>
 __device__ void reduce_all(const double* __restrict__ P, unsigned int G, double* __restrict__ tot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k < NACC; k += kWarps) {
-    double t = 0.0;
-    for (unsigned int b = lane; b < G; b += 32) t += __ldcg(P + (size_t)b * NACC + k);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) tot[k] = t;
-  }
-  __syncthreads();
+  sum_slots<Acc, NACC>(P, G, tot);
 }
 
 template <typename T, int S>
@@ -1081,10 +1163,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_fused_steps(F
             }
         }
       }
-      cta_reduce_to<Acc, N1>(acc, P1 + (size_t)blockIdx.x * N1, scratch);
+      cta_reduce_to<Acc, N1>(acc, P1, G, scratch);
     }
     if (!grid_sync(g.bar, G, g.flags)) return;
-    reduce_all<N1>(P1, G, tot);
+    reduce_all<Acc, N1>(P1, G, tot);
     if (threadIdx.x == 0) finalize_s1<S>(rec, tot, hp, fl);
     __syncthreads();
     load_coefs<T, S>(co, rec, 1);
@@ -1117,10 +1199,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_fused_steps(F
 #pragma unroll
           for (int c = a; c < S; ++c, ++e) acc[e] = fma((Acc)w[a], (Acc)w[c], acc[e]);
       }
-      cta_reduce_to<Acc, N2>(acc, P2 + (size_t)blockIdx.x * N2, scratch);
+      cta_reduce_to<Acc, N2>(acc, P2, G, scratch);
     }
     if (!grid_sync(g.bar, G, g.flags)) return;
-    reduce_all<N2>(P2, G, tot);
+    reduce_all<Acc, N2>(P2, G, tot);
     if (threadIdx.x == 0) finalize_s2<S>(rec, tot, hp, fl);
     __syncthreads();
     load_coefs<T, S>(co, rec, 2);
@@ -1146,10 +1228,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_fused_steps(F
 #pragma unroll
           for (int c = 0; c < S; ++c) acc[a * S + c] = fma((Acc)w[a], (Acc)w[c], acc[a * S + c]);
       }
-      cta_reduce_to<Acc, N3>(acc, P3 + (size_t)blockIdx.x * N3, scratch);
+      cta_reduce_to<Acc, N3>(acc, P3, G, scratch);
     }
     if (!grid_sync(g.bar, G, g.flags)) return;
-    reduce_all<N3>(P3, G, tot);
+    reduce_all<Acc, N3>(P3, G, tot);
     if (threadIdx.x == 0) finalize_s3<S>(rec, tot, fl);
     __syncthreads();
     load_coefs<T, S>(co, rec, 3);
