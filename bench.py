@@ -66,6 +66,33 @@ def dist_env():
     return rank, world, local
 
 
+def _dist_active():
+    import torch.distributed as dist
+
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def barrier():
+    """Barrier over all ranks of the default process group (nothing without one)."""
+    if _dist_active():
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest of the ranks' values (the value itself without a process group); the
+    tensor lives on ``device`` (the rank's GPU under NCCL, the CPU under gloo)."""
+    if not _dist_active():
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -528,12 +555,6 @@ def ours(args):
             L.lyap_destroy(h)
         return st, t, m, hist, ph
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
-
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -554,13 +575,7 @@ def ours(args):
         phases.append(last[4])
     clk = clocks.stop()
     barrier()
-    total_ms = float(np.sum(times))
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(float(np.sum(times)), dev)
     st, t, m, hist, ph = last
     if st != L.LYAP_OK:
         raise RuntimeError(f"solve did not converge (status {st})")
