@@ -1,0 +1,131 @@
+"""FP64 oracle of the inner solves with A for the extended Krylov space (Sec. 4).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The paper applies A^{-1} to the second half of each basis block with a direct solver (the
+cost of those solves is reported separately in Sec. 6).  The CUDA path replaces the direct
+solver by preconditioned conjugate gradients on M = -A, which is symmetric positive definite
+since A is symmetric negative definite.  This module restates, from their published
+definitions:
+
+  * conjugate gradients with a preconditioner P ~ M^{-1} (Hestenes and Stiefel, 1952), in its
+    textbook form: one product with M, one application of P and two inner products per
+    iteration, stopped at ||b - M x|| <= tol ||b|| on the recursively updated residual;
+  * Jacobi scaling, P r = r / diag(M);
+  * the zero-fill incomplete Cholesky factorisation IC(0) (Meijerink and van der Vorst, 1977):
+    the lower-triangular L with the sparsity pattern of tril(M) such that (L L^T)_{ik} = M_{ik}
+    for every (i, k) in that pattern, computed row by row:
+        L_ik = (M_ik - sum_{j < k} L_ij L_kj) / L_kk   for k < i in the pattern of row i,
+        L_ii = sqrt(M_ii - sum_{j < i} L_ij^2),
+    with the sums over columns j in the patterns of both rows; P r = (L L^T)^{-1} r by a
+    forward and a backward triangular solve.
+
+Plain Python loops over the rows: for the small grids of the tests only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+class IC0Breakdown(ArithmeticError):
+    """A non-positive pivot: IC(0) does not exist for this matrix."""
+
+
+def ic0(M) -> sp.csr_matrix:
+    """IC(0) factor L of the symmetric positive definite sparse matrix M (CSR, lower triangle
+    with the diagonal; only tril(M) is read)."""
+    Ml = sp.csr_matrix(sp.tril(M))
+    Ml.sort_indices()
+    n = Ml.shape[0]
+    rows: list[dict[int, float]] = []  # row i of L as {column: value}
+    for i in range(n):
+        lo, hi = Ml.indptr[i], Ml.indptr[i + 1]
+        cols, vals = Ml.indices[lo:hi], Ml.data[lo:hi]
+        row: dict[int, float] = {}
+        diag = 0.0
+        for c, v in zip(cols, vals):
+            c = int(c)
+            if c == i:
+                diag = float(v)
+                continue
+            # L_ic = (M_ic - sum_{j < c} L_ij L_cj) / L_cc, columns j already in row i
+            rk = rows[c]
+            acc = float(v)
+            for j, lij in row.items():
+                if j < c:
+                    lkj = rk.get(j)
+                    if lkj is not None:
+                        acc -= lij * lkj
+            row[c] = acc / rk[c]
+        d = diag - sum(x * x for x in row.values())
+        if not d > 0.0:
+            raise IC0Breakdown(f"pivot {d} at row {i}")
+        row[i] = float(np.sqrt(d))
+        rows.append(row)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    indices, data = [], []
+    for i, row in enumerate(rows):
+        for c in sorted(row):
+            indices.append(c)
+            data.append(row[c])
+        indptr[i + 1] = len(indices)
+    return sp.csr_matrix((np.array(data), np.array(indices, dtype=np.int64), indptr), shape=(n, n))
+
+
+def jacobi_prec(M):
+    """P r = r / diag(M)."""
+    d = np.asarray(M.diagonal(), dtype=np.float64)
+    return lambda r: r / d
+
+
+def ic0_prec(L):
+    """P r = (L L^T)^{-1} r: forward solve with L, backward solve with L^T."""
+    L = sp.csr_matrix(L)
+    Lt = sp.csr_matrix(L.T)
+
+    def apply(r):
+        y = spla.spsolve_triangular(L, r, lower=True)
+        return spla.spsolve_triangular(Lt, y, lower=False)
+
+    return apply
+
+
+@dataclass
+class CGResult:
+    x: np.ndarray
+    iterations: int
+    converged: bool
+    residuals: np.ndarray  # ||r_k|| / ||b||, k = 0 .. iterations
+
+
+def pcg(M, b, prec=None, tol: float = 1e-10, maxit: int = 10000) -> CGResult:
+    """Preconditioned conjugate gradients for M x = b from x = 0."""
+    b = np.asarray(b, dtype=np.float64)
+    P = prec if prec is not None else (lambda r: r)
+    x = np.zeros_like(b)
+    r = b.copy()
+    nb = float(np.linalg.norm(b))
+    hist = [1.0 if nb > 0 else 0.0]
+    if nb == 0.0:
+        return CGResult(x, 0, True, np.array(hist))
+    z = P(r)
+    p = z.copy()
+    rz = float(r @ z)
+    for it in range(1, maxit + 1):
+        q = M @ p
+        alpha = rz / float(p @ q)
+        x += alpha * p
+        r -= alpha * q
+        rel = float(np.linalg.norm(r)) / nb
+        hist.append(rel)
+        if rel <= tol:
+            return CGResult(x, it, True, np.array(hist))
+        z = P(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return CGResult(x, maxit, False, np.array(hist))
