@@ -18,7 +18,11 @@ definitions:
         L_ik = (M_ik - sum_{j < k} L_ij L_kj) / L_kk   for k < i in the pattern of row i,
         L_ii = sqrt(M_ii - sum_{j < i} L_ij^2),
     with the sums over columns j in the patterns of both rows; P r = (L L^T)^{-1} r by a
-    forward and a backward triangular solve.
+    forward and a backward triangular solve;
+  * the modified factorisation MIC(0) (Gustafsson, 1978): the same pattern, but each update of
+    the elimination that falls outside the pattern is subtracted from the diagonals of its row
+    and its column instead of being dropped, so that L L^T has the row sums of M,
+    (L L^T) 1 = M 1.
 
 Plain Python loops over the rows: for the small grids of the tests only.
 """
@@ -74,6 +78,47 @@ def ic0(M) -> sp.csr_matrix:
             data.append(row[c])
         indptr[i + 1] = len(indices)
     return sp.csr_matrix((np.array(data), np.array(indices, dtype=np.int64), indptr), shape=(n, n))
+
+
+def mic0(M) -> sp.csr_matrix:
+    """MIC(0) factor L of the symmetric positive definite sparse matrix M: right-looking
+    elimination on the pattern of tril(M); the update l_ik l_jk of an entry (i, j) outside the
+    pattern is subtracted from a_ii and a_jj."""
+    Ml = sp.csc_matrix(sp.tril(M))
+    Ml.sort_indices()
+    n = Ml.shape[0]
+    # working lower triangle by columns: col[k] = {row: value}, rows >= k
+    col = []
+    for k in range(n):
+        lo, hi = Ml.indptr[k], Ml.indptr[k + 1]
+        col.append({int(r): float(v) for r, v in zip(Ml.indices[lo:hi], Ml.data[lo:hi])})
+    diag = np.array([col[k].get(k, 0.0) for k in range(n)])
+    L_cols = []
+    for k in range(n):
+        d = diag[k]
+        if not d > 0.0:
+            raise IC0Breakdown(f"pivot {d} at row {k}")
+        lkk = float(np.sqrt(d))
+        below = sorted(r for r in col[k] if r > k)
+        lk = {r: col[k][r] / lkk for r in below}
+        L_cols.append((lkk, lk))
+        # Schur complement on the pattern; updates outside it go to both diagonals
+        for a, i in enumerate(below):
+            li = lk[i]
+            diag[i] -= li * li
+            for j in below[:a]:
+                u = li * lk[j]  # entry (i, j), i > j > k
+                if i in col[j]:
+                    col[j][i] -= u
+                else:
+                    diag[i] -= u
+                    diag[j] -= u
+    rows_i, cols_i, vals = [], [], []
+    for k, (lkk, lk) in enumerate(L_cols):
+        rows_i.append(k); cols_i.append(k); vals.append(lkk)
+        for r, v in lk.items():
+            rows_i.append(r); cols_i.append(k); vals.append(v)
+    return sp.csr_matrix((vals, (rows_i, cols_i)), shape=(n, n))
 
 
 def jacobi_prec(M):

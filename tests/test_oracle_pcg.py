@@ -12,6 +12,10 @@ preconditioning for M = -A, checked against facts that do not depend on the code
     eigenvalues: a diagonal matrix with three distinct values is solved in three.
   * On the variable-coefficient diffusion operator both preconditioned solves reach the
     tolerance, agree with a direct solve, and IC(0) needs fewer iterations than Jacobi.
+  * MIC(0) keeps the row sums, (L L^T) 1 = M 1, and agrees with M off the diagonal on the
+    pattern.  On the 5-point stencil its pivots obey d = 4 - 2/d_west - 2/d_south, so every
+    pivot is at least 2 and the interior ones approach the double root d = 2 of d = 4 - 4/d.
+    It needs fewer iterations than IC(0) on the variable-coefficient operator.
 """
 import numpy as np
 import pytest
@@ -106,3 +110,40 @@ def test_ic0_beats_jacobi_on_variable_coefficients(k):
         assert np.linalg.norm(M @ r.x - b) <= 1e-9 * np.linalg.norm(b)
         assert np.linalg.norm(r.x - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
     assert ri.iterations < 0.7 * rj.iterations
+
+
+def test_mic0_keeps_row_sums_and_pattern():
+    k = 24
+    kappa = np.exp(1.5 * wl.gaussian_field(k, 2, seed=5, corr_len=4.0))
+    M = -wl.var_coeff_diffusion(kappa)
+    L = pcg.mic0(M)
+    one = np.ones(k * k)
+    rs = M @ one
+    assert np.max(np.abs(L @ (L.T @ one) - rs)) <= 1e-13 * np.max(np.abs(M.diagonal()))
+    Md = M.toarray()
+    LLt = (L @ L.T).toarray()
+    off = (Md != 0.0) & ~np.eye(k * k, dtype=bool)
+    assert np.max(np.abs((LLt - Md)[off])) <= 1e-13 * np.max(np.abs(Md))
+    # the diagonal is where it differs from IC(0): the dropped fill lands there
+    assert np.max(np.abs(np.diag(LLt) - np.diag(Md))) > 1e-3 * np.max(np.abs(Md))
+
+
+def test_mic0_pivots_on_the_laplacian():
+    k = 48
+    M = -wl.laplacian_2d(k) / float(k + 1) ** 2
+    d = pcg.mic0(M).diagonal() ** 2
+    assert d.min() >= 2.0 - 1e-12
+    assert abs(d[0] - 4.0) < 1e-14
+    deep = d.reshape(k, k)[k - 8:k - 1, k // 2 - 4:k // 2 + 4]
+    assert np.max(deep) < 2.1  # IC(0) pivots there are near 2 + sqrt(2)
+
+
+def test_mic0_beats_ic0_on_variable_coefficients():
+    k = 64
+    kappa = np.exp(1.5 * wl.gaussian_field(k, 2, seed=1000, corr_len=2.0))
+    M = -wl.var_coeff_diffusion(kappa)
+    b = wl.rhs(k * k, 1, seed=7)[:, 0]
+    ri = pcg.pcg(M, b, prec=pcg.ic0_prec(pcg.ic0(M)), tol=1e-8, maxit=5000)
+    rm = pcg.pcg(M, b, prec=pcg.ic0_prec(pcg.mic0(M)), tol=1e-8, maxit=5000)
+    assert ri.converged and rm.converged
+    assert rm.iterations < 0.8 * ri.iterations
