@@ -94,3 +94,66 @@ def test_invalid_arguments_rejected(lib):
     A2.val_dtype, A2.mem = _lib.LYAP_F64, _lib.LYAP_MEM_HOST
     with pytest.raises(_lib.LyapError):
         _lib.lyap_workspace_size(A2, None, 1, o)
+
+
+def test_batch_planning_pools(lib):
+    """Batched planning on the host: every instance adds its own storage, and each of the
+    first twelve instances adds a pool (a check area of at least 2 GiB plus factor scratch)."""
+    from paper_1602_05033_gb300 import _lib
+
+    keep = []
+    A = _host_csr(wl.laplacian_2d(16), keep)
+    o = _lib.lyap_default_options()
+    o.maxit = 50
+
+    def size(c):
+        return _lib.lyap_batch_workspace_size([A] * c, [2] * c, o)
+
+    gib = 1 << 30
+    s1, s2, s12, s13 = size(1), size(2), size(12), size(13)
+    assert s2 - s1 >= 2 * gib  # the second instance brings a second pool
+    assert s12 - size(11) >= 2 * gib
+    assert 0 < s13 - s12 < 2 * gib  # no pool beyond twelve
+    with pytest.raises(_lib.LyapError) as e:
+        _lib.lyap_batch_workspace_size([A, A], [2, 5], o)
+    assert e.value.status == _lib.LYAP_ERR_ARG
+    o.sell_sigma = 4  # batched sweeps take the natural row order only
+    with pytest.raises(_lib.LyapError) as e:
+        _lib.lyap_batch_workspace_size([A], [2], o)
+    assert e.value.status == _lib.LYAP_ERR_ARG
+
+
+def test_ek_planning_rejects_bad_arguments(lib):
+    from paper_1602_05033_gb300 import _lib
+
+    keep = []
+    A = _host_csr(wl.laplacian_2d(16), keep)
+    assert _lib.lyap_ek_workspace_size(A, 2, 20, 16, 16) > _lib.lyap_ek_workspace_size(A, 2, 10, 16, 16) > 0
+    for s, maxit, nx, ny in [(3, 20, 16, 16), (2, 0, 16, 16), (2, 20, 16, 15)]:
+        with pytest.raises(_lib.LyapError) as e:
+            _lib.lyap_ek_workspace_size(A, s, maxit, nx, ny)
+        assert e.value.status == _lib.LYAP_ERR_ARG
+    A.val_dtype = _lib.LYAP_F32  # the extended Krylov path is fp64
+    with pytest.raises(_lib.LyapError) as e:
+        _lib.lyap_ek_workspace_size(A, 2, 20, 16, 16)
+    assert e.value.status == _lib.LYAP_ERR_ARG
+
+
+def test_create_rejects_bad_arguments_before_any_device_work(lib):
+    from paper_1602_05033_gb300 import _lib
+
+    keep = []
+    A = _host_csr(wl.laplacian_2d(8), keep)
+    C = np.ones((64, 2))
+    keep.append(C)
+    o = _lib.lyap_default_options()
+    cases = [
+        dict(s=5, tol=1e-8, c_mem=_lib.LYAP_MEM_HOST, B=None),   # unsupported block size
+        dict(s=2, tol=-1.0, c_mem=_lib.LYAP_MEM_HOST, B=None),   # negative tolerance
+        dict(s=2, tol=1e-8, c_mem=7, B=None),                     # unknown memory kind
+        dict(s=2, tol=1e-8, c_mem=_lib.LYAP_MEM_HOST, B=A),      # B without C2
+    ]
+    for c in cases:
+        with pytest.raises(_lib.LyapError) as e:
+            _lib.lyap_create(A, c["B"], C.ctypes.data, None, c["c_mem"], c["s"], c["tol"], o, 0, 0, 0)
+        assert e.value.status == _lib.LYAP_ERR_ARG, c
