@@ -13,6 +13,7 @@ lyap       block Lanczos (Alg. 2), cheap residual (Prop. 3.1 / Alg. 3),
            truncated factor (eq. 2.5, Sec. 3.2) and the two-pass device (Sec. 3.3)
 sylvester  two-sided variant for A X + X B + C1 C2^T = 0 (Sec. 5.1, Alg. 4)
 sylvester_small  A large and B small: only A projected, B diagonalised once (Sec. 5.2, Alg. 5)
+lyap_general     A X E + E X A + C C^T = 0 with E symmetric positive definite, by Cholesky of E
 explicit   explicit residual norms used as pins (dense and exact low-rank form)
 ek         extended Krylov space K_m(A, C) + K_m(A^{-1}, A^{-1} C) with exact inner solves (Sec. 4)
 cnn        convolutional preconditioner of the inner solves: forward, gradients, losses

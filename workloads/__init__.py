@@ -28,6 +28,7 @@ __all__ = [
     "paper_rand_rhs",
     "rhs",
     "random_snd_dense",
+    "fe_mass_stiffness_2d",
     "batched_instances",
     "config_c1",
     "config_c2",
@@ -219,6 +220,41 @@ def random_snd_dense(n: int, seed: int, lam_min: float = 1.0, lam_max: float = 1
     lam = -np.exp(rng.uniform(np.log(lam_min), np.log(lam_max), n))
     A = (Qm * lam) @ Qm.T
     return 0.5 * (A + A.T)
+
+
+def fe_mass_stiffness_2d(k: int, kappa=None):
+    """Bilinear (Q1) finite elements on the unit square with k x k interior nodes and zero
+    Dirichlet values: the mass matrix E (symmetric positive definite) and A = -K, K the
+    stiffness matrix of -div(kappa grad u) (symmetric positive definite), so that A is
+    symmetric negative definite.  ``kappa`` (k+1 x k+1 element values, default 1) gives
+    variable coefficients.  The generalised Lyapunov equation A X E + E X A + C C^T = 0 of the
+    paper's example with a mass matrix uses this pair as a synthetic stand-in."""
+    h = 1.0 / (k + 1)
+    ne = k + 1
+    kap = np.ones((ne, ne)) if kappa is None else np.asarray(kappa, dtype=np.float64)
+    # element matrices on a square of side h, local nodes (0,0), (1,0), (0,1), (1,1)
+    m1 = h / 6.0 * np.array([[2.0, 1.0], [1.0, 2.0]])
+    k1 = 1.0 / h * np.array([[1.0, -1.0], [-1.0, 1.0]])
+    Me = np.kron(m1, m1)
+    Ke = np.kron(k1, m1) + np.kron(m1, k1)
+    rows, cols, mv, kv = [], [], [], []
+    for ey in range(ne):
+        for ex in range(ne):
+            loc = []
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    gx, gy = ex + dx - 1, ey + dy - 1  # interior node indices, -1 / k on the boundary
+                    loc.append(gy * k + gx if 0 <= gx < k and 0 <= gy < k else -1)
+            # np.kron(a, b) puts the index of a first: local order (dy, dx) matches (y-major, x-minor)
+            for a in range(4):
+                for b in range(4):
+                    if loc[a] >= 0 and loc[b] >= 0:
+                        rows.append(loc[a]); cols.append(loc[b])
+                        mv.append(Me[a, b]); kv.append(kap[ey, ex] * Ke[a, b])
+    n = k * k
+    E = sp.csr_matrix((mv, (rows, cols)), shape=(n, n))
+    K = sp.csr_matrix((kv, (rows, cols)), shape=(n, n))
+    return _csr(-K), _csr(E)
 
 
 def batched_instances(count: int = 256, seed: int = 0, kmin: int = 64, kmax: int = 512):
