@@ -22,8 +22,10 @@
  *  - Pointers flagged LYAP_MEM_HOST are host memory (pinned or pageable); the
  *    library copies them to or from the workspace inside the call.
  *  - Streams are passed as void* holding a cudaStream_t (NULL = legacy stream).
- *    All work is ordered on the caller's stream; lyap_solve returns once the
- *    convergence decision is known on the host.
+ *    All work is ordered on the caller's stream, except that lyap_solve runs the
+ *    convergence checks of a finished chunk of steps on the handle's second stream
+ *    while the next chunk runs on the caller's; it synchronises both before it
+ *    returns, once the convergence decision is known on the host.
  *  - Calling order: create -> solve -> (residual_norm)* -> factor -> destroy.
  *    factor may be called once per solve.
  */
@@ -120,6 +122,8 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1,
 /* Pass 1 (Alg. 1 steps 3-7): block Lanczos with block MGS done twice and CholQR2
  * normalisation (Alg. 2), the cheap residual norm of Prop. 3.1 / Alg. 3
  * (Alg. 4 for Sylvester) at every check_every-th step, until tol or maxit.
+ * Steps run in chunks ahead of their checks; the steps of a chunk beyond the
+ * converged m are discarded, and a sweep error among them does not fail the solve.
  * Returns LYAP_OK, LYAP_NOT_CONVERGED or an error. */
 int lyap_solve(lyap_handle* h, void* stream);
 
