@@ -122,8 +122,9 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1,
 /* Pass 1 (Alg. 1 steps 3-7): block Lanczos with block MGS done twice and CholQR2
  * normalisation (Alg. 2), the cheap residual norm of Prop. 3.1 / Alg. 3
  * (Alg. 4 for Sylvester) at every check_every-th step, until tol or maxit.
- * Steps run in chunks ahead of their checks; the steps of a chunk beyond the
- * converged m are discarded, and a sweep error among them does not fail the solve.
+ * Steps run in chunks ahead of their checks: the chunk after the one whose checks
+ * find convergence has already been launched, and is discarded, including any sweep
+ * error it reports.
  * Returns LYAP_OK, LYAP_NOT_CONVERGED or an error. */
 int lyap_solve(lyap_handle* h, void* stream);
 
