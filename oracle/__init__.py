@@ -17,6 +17,7 @@ lyap_general     A X E + E X A + C C^T = 0 with E symmetric positive definite, b
 explicit   explicit residual norms used as pins (dense and exact low-rank form)
 ek         extended Krylov space K_m(A, C) + K_m(A^{-1}, A^{-1} C) with exact inner solves (Sec. 4)
 cnn        convolutional preconditioner of the inner solves: forward, gradients, losses
-pcg        inner solves with A by conjugate gradients: Jacobi and IC(0) preconditioning
+pcg        inner solves with A by conjugate gradients: Jacobi, IC(0) and MIC(0) preconditioning
+learned_factor   a network predicting the IC(0)-pattern factor values: loss, gradients
 """
 from . import lyap, sylvester, explicit  # noqa: F401
