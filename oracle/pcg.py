@@ -22,7 +22,10 @@ definitions:
   * the modified factorisation MIC(0) (Gustafsson, 1978): the same pattern, but each update of
     the elimination that falls outside the pattern is subtracted from the diagonals of its row
     and its column instead of being dropped, so that L L^T has the row sums of M,
-    (L L^T) 1 = M 1.
+    (L L^T) 1 = M 1;
+  * the factorised sparse approximate inverse FSAI (Kolotilina and Yeremin, 1993): G lower
+    triangular on a chosen pattern, row i from the local system M[J_i, J_i] g = e_i on its
+    pattern J_i, scaled so that (G M G^T)_ii = 1; P r = G^T (G r), products only.
 
 Plain Python loops over the rows: for the small grids of the tests only.
 """
@@ -119,6 +122,48 @@ def mic0(M) -> sp.csr_matrix:
         for r, v in lk.items():
             rows_i.append(r); cols_i.append(k); vals.append(v)
     return sp.csr_matrix((vals, (rows_i, cols_i)), shape=(n, n))
+
+
+def fsai(M, patterns) -> sp.csr_matrix:
+    """FSAI factor G of the SPD matrix M; ``patterns[i]`` lists the columns j <= i of row i
+    (it must contain i)."""
+    M = sp.csr_matrix(M)
+    n = M.shape[0]
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        J = sorted(set(int(j) for j in patterns[i]))
+        if i not in J or J[-1] != i:
+            raise ValueError(f"row {i}: the pattern must end at the diagonal")
+        MJ = M[J][:, J].toarray()
+        e = np.zeros(len(J))
+        e[-1] = 1.0
+        g = np.linalg.solve(MJ, e)
+        if not g[-1] > 0.0:
+            raise ArithmeticError(f"row {i}: non-positive FSAI pivot")
+        g /= np.sqrt(g[-1])
+        rows += [i] * len(J)
+        cols += J
+        vals += list(g)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def grid_lower_patterns(k: int, reach: int):
+    """For a k x k grid (x fastest): row i's pattern is every node j <= i within `reach` cells
+    of i in both directions (reach 1: the lower half of the 3 x 3 neighbourhood)."""
+    pats = []
+    for i in range(k * k):
+        xi, yi = i % k, i // k
+        J = [y * k + x for y in range(max(0, yi - reach), yi + 1)
+             for x in range(max(0, xi - reach), min(k, xi + reach + 1)) if y * k + x <= i]
+        pats.append(J)
+    return pats
+
+
+def fsai_prec(G):
+    """P r = G^T (G r)."""
+    G = sp.csr_matrix(G)
+    Gt = sp.csr_matrix(G.T)
+    return lambda r: Gt @ (G @ r)
 
 
 def jacobi_prec(M):

@@ -147,3 +147,29 @@ def test_mic0_beats_ic0_on_variable_coefficients():
     rm = pcg.pcg(M, b, prec=pcg.ic0_prec(pcg.mic0(M)), tol=1e-8, maxit=5000)
     assert ri.converged and rm.converged
     assert rm.iterations < 0.8 * ri.iterations
+
+
+def test_fsai_on_the_full_lower_pattern_is_the_inverse_factor():
+    rng = np.random.default_rng(8)
+    n = 12
+    B = rng.standard_normal((n, n))
+    M = sp.csr_matrix(B @ B.T + n * np.eye(n))
+    G = pcg.fsai(M, [list(range(i + 1)) for i in range(n)])
+    # G^T G = M^{-1}: G is the inverse of the Cholesky factor of M
+    assert np.allclose((G.T @ G).toarray(), np.linalg.inv(M.toarray()), rtol=0, atol=1e-12)
+
+
+def test_fsai_scaling_and_pattern_growth():
+    k = 24
+    kappa = np.exp(1.5 * wl.gaussian_field(k, 2, seed=5, corr_len=4.0))
+    M = -wl.var_coeff_diffusion(kappa)
+    b = wl.rhs(k * k, 1, seed=7)[:, 0]
+    its = []
+    for reach in (1, 2):
+        G = pcg.fsai(M, pcg.grid_lower_patterns(k, reach))
+        d = (G @ M @ G.T).diagonal()
+        assert np.max(np.abs(d - 1.0)) <= 1e-12
+        assert np.all(G.diagonal() > 0)
+        its.append(pcg.pcg(M, b, prec=pcg.fsai_prec(G), tol=1e-8).iterations)
+    jac = pcg.pcg(M, b, prec=pcg.jacobi_prec(M), tol=1e-8).iterations
+    assert its[1] < its[0] < jac
