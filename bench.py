@@ -686,6 +686,7 @@ def e2e_arm(args, P, rp, cl, vl32, s, opt, dev):
     times, t, m = [], 0, 0
     for it in range(1 + min(args.steps, 3)):
         torch.cuda.synchronize()
+        barrier()
         a = time.perf_counter()
         h = L.lyap_create(csr, None, h_C.data_ptr(), None, L.LYAP_MEM_HOST, s, 1e-8, o, ws.data_ptr(), ws_bytes, stream)
         try:
@@ -700,7 +701,8 @@ def e2e_arm(args, P, rp, cl, vl32, s, opt, dev):
             times.append(b - a)
     h2d = rp.nbytes + cl.nbytes + vl32.nbytes + P.C1.nbytes
     d2h = n * t * 4 + m * 8
-    return {"value": float(np.median(times)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    # the slowest rank's median (each rank solves its own replica)
+    return {"value": max_over_ranks(float(np.median(times)), dev), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": len(times)}
 
 
