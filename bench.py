@@ -1,18 +1,23 @@
 """Benchmark: time to relative residual 1e-8 on the n = 1e6 Lyapunov workload.
 
 Workload: A = -(3D 7-point Laplacian on a 100^3 grid, h = 1/101), n = 1e6,
-C = rhs(n, 4, seed = rank) iid N(0,1), s = 4, tol 1e-8, maxit 400, mixed
-precision (fp32 basis and SpMM, fp64 reductions, CholQR2 factors, reduced
-eigenproblem and residual), two-pass factor.  One step = lyap_create (SELL-C-sigma
-build from the device-resident CSR) + lyap_solve + lyap_factor into a device Z;
-the metric is that step's time in seconds.
+C = rhs(n, 4, seed = rank) iid N(0,1), s = 4, tol 1e-8, maxit 400, two-pass
+factor.  One step = lyap_create (SELL-C-sigma build from the device-resident
+CSR) + lyap_solve + lyap_factor into a device Z; the metric is that step's time
+in seconds.
+
+Several precision paths are timed (--paths).  The convergence test of every path
+is the cheap residual of Prop. 3.1, a function of T_m alone; after the timing, the
+explicit residual ||A Z Z^T + Z Z^T A + C C^T||_F / ||C||_F^2 of each returned
+factor is computed in fp64 on the host, and the headline is the fastest path
+whose factor truly reaches the tolerance.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun every rank solves its own replica (seed = rank, weak scaling;
 the method has no cross-rank exchange on one GPU per problem).  Rank 0 prints
-one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded
-sample of the same workload on the host cores.
+one JSON line.  ``--impl reference`` times one full solve of the same workload
+by the FP64 CPU oracle on the host cores.
 """
 from __future__ import annotations
 
@@ -31,7 +36,7 @@ import numpy as np  # noqa: E402
 METRIC = "time to rel. residual 1e-8 (s)"
 UNIT = "s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_c2_lap3d100_s4.json")
-WORKLOAD = "Lyapunov, A = -(3D 7-point Laplacian on 100^3), n = 1e6, s = 4, C iid N(0,1), tol 1e-8, maxit 400, mixed precision, two-pass"
+WORKLOAD_BASE = "Lyapunov, A = -(3D 7-point Laplacian on 100^3), n = 1e6, s = 4, C iid N(0,1), tol 1e-8, maxit 400, two-pass"
 
 
 def parse():
@@ -51,7 +56,9 @@ def parse():
     ap.add_argument("--ek-precond", choices=["jacobi", "cnn", "both"], default="both")
     ap.add_argument("--count", type=int, default=32,
                     help="instances of the batch workload (256 is the full workload; its per-instance checks take minutes)")
-    ap.add_argument("--no-f64-path", action="store_true", help="skip the plain fp64 comparison solve")
+    ap.add_argument("--paths", default="mixed,f64",
+                    help="precision paths timed on the n = 1e6 workload; the headline is the fastest one whose "
+                         "returned factor has an explicit relative residual <= tol")
     ap.add_argument("--profile-case", choices=["lanczos", "check", "sylv-check"], default=None,
                     help="run a short solve of the workload for a profiler and exit: 'lanczos' runs 6 block "
                          "Lanczos steps, 'check' 64 steps with their convergence checks (tol 0), 'sylv-check' "
@@ -94,56 +101,34 @@ def max_over_ranks(value: float, device=None) -> float:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# CPU oracle leg (cpu_baseline, the reference arm, and the explicit residual of the GPU results)
 # ---------------------------------------------------------------------------
-def oracle_sample(k: int, m_star: int, sample_its: int = 40):
-    """Times the FP64 oracle (as it stands) on a bounded sample of the workload and
-    extrapolates to the full solve of m_star iterations.
-
-    Sample: the first ``sample_its`` block Lanczos steps with every convergence check,
-    5 second-pass steps and the truncated factor at m = sample_its.  Model (the step
-    costs are constant in m, the check of T_m grows like m^2 at these sizes, the
-    factor's small dense eigenproblems like m^2 as well):
-        T = m_star (t_lanczos + t_pass2) + c sum_{m <= m_star} m^2 + t_factor (m_star / sample_its)^2
-    with c the mean of t_check(m) / m^2 over the second half of the sample."""
+def oracle_full(k: int):
+    """Times one full solve of the workload by the FP64 CPU oracle, as it stands: block Lanczos with
+    a convergence check at every m until rel. residual <= tol, then the truncated factor by the
+    two-pass device.  Returns (seconds, m, description)."""
     import workloads as wl
     from oracle import lyap
 
     P = wl.config_c2(0, k=k)
-    A, C = P.A, P.C1
     t0 = time.perf_counter()
-    V1, log = lyap.start(C)
-    Vp, Vc = None, V1
-    tl, tc = [], []
-    for j in range(1, sample_its + 1):
-        a = time.perf_counter()
-        Vn, tp, td, tn = lyap.lanczos_step(A, Vp, Vc)
-        log.tau_prev.append(tp)
-        log.tau_diag.append(td)
-        log.tau_next.append(tn)
-        Vp, Vc = Vc, Vn
-        b = time.perf_counter()
-        lyap.residual_at(log, j)
-        c = time.perf_counter()
-        tl.append(b - a)
-        tc.append(c - b)
-    a = time.perf_counter()
-    for _ in zip(range(5), lyap.regenerate_basis(A, C, log, sample_its)):
-        pass
-    t_p2 = (time.perf_counter() - a) / 5
-    a = time.perf_counter()
-    lyap.truncated_factor(log, sample_its)
-    t_fac = time.perf_counter() - a
-    sample_secs = time.perf_counter() - t0
-    ms = np.arange(1, sample_its + 1)
-    sel = ms >= sample_its // 2
-    cfit = float(np.mean(np.array(tc)[sel] / ms[sel] ** 2))
-    checks = cfit * float(np.sum(np.arange(1, m_star + 1, dtype=float) ** 2))
-    total = m_star * (float(np.mean(tl)) + t_p2) + checks + t_fac * (m_star / sample_its) ** 2
-    desc = (f"FP64 oracle, first {sample_its} of {m_star} block Lanczos steps of the n={k**3} workload with every "
-            f"check, 5 second-pass steps and the truncated factor at m={sample_its} ({sample_secs:.1f} s of CPU "
-            f"time); extrapolated to m={m_star}: steps x {m_star}, checks as c*m^2")
-    return total, sample_secs, desc
+    res = lyap.solve(P.A, P.C1, tol=P.tol, maxit=P.maxit)
+    t1 = time.perf_counter()
+    Z, _ = lyap.factor(P.A, P.C1, res)
+    t2 = time.perf_counter()
+    desc = (f"one full FP64 oracle run of the n={k**3} workload: {res.m} block Lanczos steps with a check at "
+            f"every m ({t1 - t0:.1f} s), then the truncated factor by the two-pass device ({t2 - t1:.1f} s, "
+            f"t={Z.shape[1]}); NumPy/SciPy, BLAS threads = {cores_used()}")
+    return t2 - t0, int(res.m), desc
+
+
+def explicit_rel_residual(A, Z, C):
+    """||A Z Z^T + Z Z^T A + C C^T||_F / ||C||_F^2 in fp64 on the host (the oracle's exact low-rank
+    form), for a factor the GPU returned."""
+    from oracle import explicit
+
+    Z = np.asarray(Z, dtype=np.float64)
+    return explicit.lyap_lowrank(A, Z, C) / float(np.linalg.norm(C)) ** 2
 
 
 def cores_used():
@@ -154,34 +139,28 @@ def cores_used():
 
 
 def reference_arm(args):
+    """The FP64 CPU oracle on the same workload, timed once per invocation (a full solve takes about
+    a minute on the host cores, so the requested steps and warm-up are not repeated)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    golden = json.load(open(GOLDEN))
-    m_star = golden["m"] if args.k == 100 else 400
-    vals, secs = [], 0.0
-    desc = ""
-    for it in range(args.warmup + args.steps):
-        v, s, desc = oracle_sample(args.k, m_star, sample_its=30)
-        secs += s
-        if it >= args.warmup:
-            vals.append(v)
-    value = float(np.median(vals))
+    value, m, desc = oracle_full(args.k)
     line = {
         "impl": "reference",
         "metric": METRIC,
         "value": value,
         "unit": UNIT,
         "n_gpus": args.gpus,
-        "steps": args.steps,
-        "warmup": args.warmup,
+        "steps": 1,
+        "warmup": 0,
+        "requested": {"steps": args.steps, "warmup": args.warmup},
         "ms_per_step": 1000.0 * value,
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("mixed precision", "fp64 oracle")},
+        "config": {"workload": WORKLOAD_BASE + ", fp64 CPU oracle", "m": m},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -322,7 +301,7 @@ def make_step(P, dev, precision, tcap, maxit):
             L.lyap_destroy(h)
         return st, t, m, hist, ph
 
-    return step, opt, (csrA, csrB)
+    return step, opt, (csrA, csrB), (Z1, Z2)
 
 
 def timed(step, steps, warmup, flush, barrier=lambda: None):
@@ -363,7 +342,7 @@ def sylv_line(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     P = wl.config_c3(0)
-    step, opt, (ca, cb) = make_step(P, dev, L.LYAP_PREC_MIXED, 512, P.maxit)
+    step, opt, (ca, cb), _ = make_step(P, dev, L.LYAP_PREC_MIXED, 512, P.maxit)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     clocks = ClockSampler(0)
     clocks.start()
@@ -502,20 +481,25 @@ def batch_line(args):
     return 0
 
 
+PRECISIONS = {
+    # name: (option value, dtype label, bytes per value of A in the SELL copy, bytes per basis value)
+    "mixed": ("LYAP_PREC_MIXED", "f32 bulk (basis, SpMM, factor) / f64 CholQR2 factors, eigenproblem, residual", 8, 4),
+    "f64": ("LYAP_PREC_F64", "f64", 12, 8),
+}
+
+
 def ours(args):
     import torch
 
     import workloads as wl
     from paper_1602_05033_gb300 import _lib as L
-    from paper_1602_05033_gb300 import csr_arrays
 
     rank, world, local = dist_env()
     golden = json.load(open(GOLDEN)) if args.k == 100 else None
     # the CPU baseline runs first, before any CUDA work in this process
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        m_star = golden["m"] if golden else 400
-        v, s, desc = oracle_sample(args.k, m_star)
+        v, _, desc = oracle_full(args.k)
         cpu = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": desc}
 
     torch.cuda.set_device(local)
@@ -525,132 +509,85 @@ def ours(args):
 
         dist.init_process_group("nccl", device_id=dev)
     P = wl.config_c2(rank, k=args.k)
-    rp, cl, vl = csr_arrays(P.A)
-    vl32 = vl.astype(np.float32)
-    assert np.array_equal(vl32.astype(np.float64), vl), "Laplacian values must be exact in fp32"
-    n, s = P.A.shape[0], P.s
-    d_rp, d_cl, d_vl = (torch.from_numpy(x).to(dev) for x in (rp, cl, vl32))
-    d_C = torch.from_numpy(P.C1).to(dev)
-    csr = L.lyap_csr()
-    csr.n, csr.nnz = n, cl.shape[0]
-    csr.rowptr, csr.col, csr.val = d_rp.data_ptr(), d_cl.data_ptr(), d_vl.data_ptr()
-    csr.val_dtype, csr.mem = L.LYAP_F32, L.LYAP_MEM_DEVICE
-    opt = L.lyap_default_options()
-    opt.maxit = 400
-    opt.precision = L.LYAP_PREC_MIXED
+    n, s, nnz = P.A.shape[0], P.s, P.A.nnz
     tcap = 256
-    ws_bytes = L.lyap_workspace_size(csr, None, s, opt)
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    Z = torch.empty((n, tcap), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev).cuda_stream
-
-    def step():
-        h = L.lyap_create(csr, None, d_C.data_ptr(), None, L.LYAP_MEM_DEVICE, s, 1e-8, opt, ws.data_ptr(), ws_bytes,
-                          stream)
-        try:
-            st = L.lyap_solve(h, stream)
-            t = L.lyap_factor(h, Z.data_ptr(), tcap, None, 0, L.LYAP_F32, L.LYAP_MEM_DEVICE, tcap, stream)
-            hist, m, _ = L.lyap_residual_norm(h, opt.maxit)
-            ph = L.lyap_phase_times(h)
-        finally:
-            L.lyap_destroy(h)
-        return st, t, m, hist, ph
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
+    names = [p for p in args.paths.split(",") if p in PRECISIONS]
+    peak, peak_src = measured_peaks()
     clocks = ClockSampler(local)
     clocks.start()
-    times, phases, last = [], [], None
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush (512 MB write) outside the timed interval
-        torch.cuda.synchronize()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        last = step()
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        phases.append(last[4])
+    runs, zs = {}, {}
+    for name in names:
+        prec = getattr(L, PRECISIONS[name][0])
+        step, opt, _, (Z1, _) = make_step(P, dev, prec, tcap, 400)
+        times, phases, last = timed(step, args.steps, args.warmup, flush, barrier)
+        st, t, m, hist, ph = last
+        total_ms = max_over_ranks(float(np.sum(times)), dev)
+        vb, bb = PRECISIONS[name][2], PRECISIONS[name][3]
+        alg = nnz * vb + 5 * n * s * bb
+        ach = lanczos_rate(phases, alg)
+        r = {"value": total_ms / args.steps / 1000.0, "status": int(st), "m": int(m), "t": int(t),
+             "cheap_rel_residual": float(hist[m - 1]),
+             "phases_ms": {k: round(float(np.mean([p[i] for p in phases])), 3) for i, k in
+                           enumerate(["create_ms", "solve_ms", "factor_ms", "lanczos_steps", "check_ms", "lanczos_ms"])},
+             "lanczos_GBps": round(ach, 1), "lanczos_frac": round(ach / peak, 4), "bytes_per_step": alg,
+             "gpu_launches": int(np.mean([p[6] for p in phases]))}
+        if golden is not None:
+            g = np.array(golden["history"])
+            k_ = min(len(g), len(hist))
+            r["vs_oracle"] = {"m_oracle": golden["m"], "t_oracle": golden["t"],
+                              "max_rel_dhist": float(np.max(np.abs(hist[:k_] - g[:k_]) / g[:k_]))}
+        runs[name] = r
+        zs[name] = Z1[:, :t].double().cpu().numpy() if rank == 0 else None
+        del step, Z1
+        torch.cuda.empty_cache()
     clk = clocks.stop()
     barrier()
-    total_ms = max_over_ranks(float(np.sum(times)), dev)
-    st, t, m, hist, ph = last
-    if st != L.LYAP_OK:
-        raise RuntimeError(f"solve did not converge (status {st})")
-    ms_per_step = total_ms / args.steps
-
-    # roofline of the block Lanczos step (SpMM + two MGS sweeps + CholQR2): algorithmic
-    # bytes = A (fp32 value + int32 column per nonzero) + 5 blocks of n x s fp32
-    # (read V_j, V_{j-1}; W written and read once; V_{j+1} written)
-    nnz = cl.shape[0]
-    alg_bytes = nnz * 8 + 5 * n * s * 4
-    lanczos_ms = float(np.mean([p[5] for p in phases]))
-    steps_run = float(np.mean([p[3] for p in phases]))
-    achieved = alg_bytes * steps_run / (lanczos_ms * 1e-3) / 1e9
-    peak, peak_src = measured_peaks()
-    phase = {k: round(float(np.mean([p[i] for p in phases])), 3) for i, k in
-             enumerate(["create_ms", "solve_ms", "factor_ms", "lanczos_steps", "check_ms", "lanczos_ms"])}
-    launches = int(np.mean([p[6] for p in phases]))
+    # CPU leg: the explicit residual of every returned factor, in fp64 on the host (outside the timing)
+    if rank == 0:
+        for name in names:
+            runs[name]["true_rel_residual"] = explicit_rel_residual(P.A, zs[name], P.C1)
+            runs[name]["reaches_tol"] = bool(runs[name]["status"] == 0 and runs[name]["true_rel_residual"] <= P.tol)
+    zs.clear()
+    ok = [nm for nm in names if runs[nm].get("reaches_tol")]
+    head = min(ok, key=lambda nm: runs[nm]["value"]) if ok else ("f64" if "f64" in names else names[0])
+    hr = runs[head]
+    for nm in names:
+        if nm != head and runs[nm].get("reaches_tol") and hr.get("reaches_tol"):
+            runs[nm]["time_vs_headline"] = round(runs[nm]["value"] / hr["value"], 3)
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_arm(args, P, rp, cl, vl32, s, opt, dev)
-    f64 = None
-    if not args.no_f64_path:
-        # the same workload on the plain fp64 path (fp64 basis, SpMM and factor): the reference
-        # point of the mixed-precision form
-        del ws, Z
-        torch.cuda.empty_cache()
-        step64, opt64, _ = make_step(P, dev, L.LYAP_PREC_F64, tcap, 400)
-        t64, ph64, last64 = timed(step64, 2, 1, flush, barrier)
-        alg64 = nnz * 12 + 5 * n * s * 8
-        a64 = lanczos_rate(ph64, alg64)
-        f64 = {"value": float(np.mean(t64)) / 1000.0, "unit": UNIT, "m": int(last64[2]), "t": int(last64[1]),
-               "lanczos_GBps": round(a64, 1), "lanczos_frac": round(a64 / measured_peaks()[0], 4),
-               "lanczos_ms": round(float(np.mean([p[5] for p in ph64])), 3),
-               "check_ms": round(float(np.mean([p[4] for p in ph64])), 3),
-               "factor_ms": round(float(np.mean([p[2] for p in ph64])), 3),
-               "speedup_of_mixed": round(float(np.mean(t64)) / ms_per_step, 3)}
-    parity = None
-    if golden is not None:
-        g = np.array(golden["history"])
-        k_ = min(len(g), len(hist))
-        parity = {"m_oracle": golden["m"], "m_gpu": int(m), "t_oracle": golden["t"], "t_gpu": int(t),
-                  "max_abs_dhist": float(np.max(np.abs(hist[:k_] - g[:k_])))}
+        e2e = e2e_arm(args, P, getattr(L, PRECISIONS[head][0]), dev)
     line = {
         "metric": METRIC,
-        "value": ms_per_step / 1000.0,
+        "value": hr["value"],
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_per_step,
+        "ms_per_step": 1000.0 * hr["value"],
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 bulk / f64 reductions and reduced problem",
+        "dtype": PRECISIONS[head][1],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "s": s, "nnz": nnz, "tol": 1e-8, "maxit": 400,
-                   "parallelism": f"{world} independent replicas", "l2": "flushed before each step (512 MB write)"},
-        "roofline": {"kernel": "block Lanczos step: SELL SpMM + 2 block MGS sweeps + CholQR2 (4 launches)",
-                     "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": sweep_traffic(),
-                     "bytes_per_unit": alg_bytes, "peak_source": peak_src},
-        "phases_ms": phase,
-        "gpu_launches": launches,
+        "config": {"workload": WORKLOAD_BASE + f", {head} path", "n": n, "s": s, "nnz": nnz, "tol": P.tol,
+                   "maxit": 400, "parallelism": f"{world} independent replicas",
+                   "l2": "flushed before each step (512 MB write)"},
+        "headline_path": head,
+        "headline_reaches_tol": bool(hr.get("reaches_tol")),
+        "roofline": {"kernel": "block Lanczos step (SpMM, block MGS twice, CholQR2), " + head,
+                     "bound": "hbm", "achieved": hr["lanczos_GBps"], "peak": peak, "unit": "GB/s",
+                     "frac": hr["lanczos_frac"], "traffic": sweep_traffic() if head == "mixed" else None,
+                     "bytes_per_unit": hr["bytes_per_step"], "peak_source": peak_src},
+        "gpu_launches": hr["gpu_launches"],
         "clocks": clk,
-        "result": {"m": int(m), "t": int(t), "rel_residual": float(hist[m - 1])},
-        "parity_vs_oracle": parity,
+        "paths": runs,
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if e2e is not None:
         line["e2e"] = e2e
-    if f64 is not None:
-        line["plain_f64_path"] = f64
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -660,47 +597,52 @@ def ours(args):
     return 0
 
 
-def e2e_arm(args, P, rp, cl, vl32, s, opt, dev):
+def e2e_arm(args, P, precision, dev):
     """Same metric through the C ABI with host buffers: pinned CSR and C in, pinned Z out."""
     import torch
 
     from paper_1602_05033_gb300 import _lib as L
+    from paper_1602_05033_gb300 import csr_arrays
 
-    n = P.A.shape[0]
+    n, s = P.A.shape[0], P.s
+    rp, cl, vl = csr_arrays(P.A)
+    vl32 = vl.astype(np.float32)
+    assert np.array_equal(vl32.astype(np.float64), vl), "operator values must be exact in fp32"
     tcap = 128
+    f32z = precision == L.LYAP_PREC_MIXED
     pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
     h_rp, h_cl, h_vl, h_C = pin(rp), pin(cl), pin(vl32), pin(np.ascontiguousarray(P.C1))
-    h_Z = torch.empty((n, tcap), dtype=torch.float32).pin_memory()
+    h_Z = torch.empty((n, tcap), dtype=torch.float32 if f32z else torch.float64).pin_memory()
     csr = L.lyap_csr()
     csr.n, csr.nnz = n, cl.shape[0]
     csr.rowptr, csr.col, csr.val = h_rp.data_ptr(), h_cl.data_ptr(), h_vl.data_ptr()
     csr.val_dtype, csr.mem = L.LYAP_F32, L.LYAP_MEM_HOST
-    o = L.lyap_options()
-    for f, _ in L.lyap_options._fields_:
-        setattr(o, f, getattr(opt, f))
+    o = L.lyap_default_options()
+    o.maxit = 400
+    o.precision = precision
     o.zcap = tcap
     ws_bytes = L.lyap_workspace_size(csr, None, s, o)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    hist_buf = np.empty(o.maxit)
     times, t, m = [], 0, 0
+    zdt = L.LYAP_F32 if f32z else L.LYAP_F64
     for it in range(1 + min(args.steps, 3)):
         torch.cuda.synchronize()
         barrier()
         a = time.perf_counter()
-        h = L.lyap_create(csr, None, h_C.data_ptr(), None, L.LYAP_MEM_HOST, s, 1e-8, o, ws.data_ptr(), ws_bytes, stream)
+        h = L.lyap_create(csr, None, h_C.data_ptr(), None, L.LYAP_MEM_HOST, s, P.tol, o, ws.data_ptr(), ws_bytes,
+                          stream)
         try:
             L.lyap_solve(h, stream)
-            t = L.lyap_factor(h, h_Z.data_ptr(), tcap, None, 0, L.LYAP_F32, L.LYAP_MEM_HOST, tcap, stream)
+            t = L.lyap_factor(h, h_Z.data_ptr(), tcap, None, 0, zdt, L.LYAP_MEM_HOST, tcap, stream)
             hist, m, _ = L.lyap_residual_norm(h, o.maxit)
-            hist_buf[:m] = hist
         finally:
             L.lyap_destroy(h)
         b = time.perf_counter()
         if it > 0:
             times.append(b - a)
     h2d = rp.nbytes + cl.nbytes + vl32.nbytes + P.C1.nbytes
-    d2h = n * t * 4 + m * 8
+    d2h = n * t * (4 if f32z else 8) + m * 8
     # the slowest rank's median (each rank solves its own replica)
     return {"value": max_over_ranks(float(np.median(times)), dev), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": len(times)}

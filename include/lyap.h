@@ -167,14 +167,16 @@ int lyap_phase_times(lyap_handle* h, double* out, int cap);
  * frees the workspace afterwards. */
 int lyap_destroy(lyap_handle* h);
 
-/* Allocation-free evaluation of the relative residual ||R_m||_F / beta^2 of Prop. 3.1
- * for a projected matrix the caller supplies.  It is an addition of this library: the
- * paper has no counterpart.  It runs the kernels of lyap_solve's convergence check, but
- * every byte of their scratch sits in one fixed device array compiled into the library,
- * so the call makes no cudaMalloc, cudaFree or other allocating call.  It is meant for
- * callers that cannot allocate device memory at the point where they need a residual:
- * code running inside another framework whose caching allocator already holds the free
- * device memory (a raw cudaMalloc there fails or fragments that pool), and real-time or
+/* Allocation-free evaluation of the relative residual ||R_m||_F / beta^2 for a projected
+ * matrix the caller supplies: the residual norm of the Lyapunov equation computed from the
+ * eigenvalues and the first and last s rows of the eigenvectors of the block tridiagonal T_m,
+ * exactly as the convergence check of lyap_solve does.  The paper has no counterpart: this
+ * entry point is an addition of this library.  It runs the kernels of lyap_solve's
+ * convergence check, but every byte of their scratch sits in one fixed device array compiled
+ * into the library, so the call makes no cudaMalloc, cudaFree or other allocating call.  It
+ * is meant for callers that cannot allocate device memory at the point where they need a
+ * residual: code running inside another framework whose caching allocator already holds the
+ * free device memory (a raw cudaMalloc there fails or fragments that pool), and real-time or
  * embedded loops whose memory is fixed at set-up and may not change afterwards.
  *  ab        : device memory, lower band of T_m, ab[d + i*ldab] = T_m[i+d][i] for
  *              d = 0..s and i < s*m (the layout lyap_projected_matrix returns); ldab >= s+1
@@ -184,12 +186,16 @@ int lyap_destroy(lyap_handle* h);
  *  rel_out   : device memory, receives the relative residual (a double)
  *  status_out: device memory, receives LYAP_OK or the error status of the evaluation (an int)
  *  stream    : cudaStream_t the work is ordered on; the call returns after enqueueing
- * Limits: 1 <= s <= 4 and s*m <= 256; anything larger returns LYAP_ERR_ARG.  The array
- * (about 6 MiB) is held by every GPU that loads the library until the process exits.
- * The first call on a device looks the array's address up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share
- * the one array and each call clears what must start at zero, so calls whose work
- * overlaps on the GPU (concurrent streams or threads) race and must be serialised. */
+ * Limits: 1 <= s <= 4 and s*m <= 256; anything larger returns LYAP_ERR_ARG.
+ * Set-up: with lazy module loading (the CUDA default), a device gets the library's device
+ * code and this array (about 6 MiB) only when the library first runs a kernel there, and
+ * that load allocates device memory.  So make the first call on each device at set-up, while
+ * memory can still be allocated and before any stream capture; that first call also looks
+ * the array's address up (cudaGetSymbolAddress) with the device current.  From then on the
+ * array stays held on that device until the process exits, and calls allocate nothing.
+ * All calls share the one array and each call clears what must start at zero, so calls
+ * whose work overlaps on the GPU (concurrent streams or threads) race and must be
+ * serialised. */
 int lyap_residual_noalloc(int s, int m, const double* ab, int ldab, const double* gamma,
                           const double* tau_next, double beta, double* rel_out,
                           int* status_out, void* stream);

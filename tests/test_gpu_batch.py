@@ -62,13 +62,22 @@ def test_batch_matches_single_solves_and_oracle(pkg, precision):
             assert abs(ms[i] - one.m) <= 1
             k = min(len(h_b), len(h_1))
             assert np.all(np.abs(h_b[:k] - h_1[:k]) <= 1e-9 + 1e-5 * np.abs(h_1[:k])), (i, np.max(np.abs(h_b[:k] - h_1[:k])))
+        ref = olyap.solve(P.A, P.C1, tol=1e-8, maxit=400)
+        Z = bt.factor(i).double().cpu().numpy()
+        Zo, _ = olyap.factor(P.A, P.C1, ref)
         if precision == "f64":
-            ref = olyap.solve(P.A, P.C1, tol=1e-8, maxit=400)
             assert ms[i] == ref.m
-            assert np.all(np.abs(h_b - ref.history) <= 1e-10 + 1e-10 * np.abs(ref.history))
-            Z = bt.factor(i).cpu().numpy()
-            Zo, _ = olyap.factor(P.A, P.C1, ref)
+            assert np.all(np.abs(h_b - ref.history) <= 1e-14 + 1e-10 * np.abs(ref.history))
             assert _xprobe(Z, Zo) <= 1e-8
+        else:
+            # the fp32 basis against the fp64 oracle: the relative history deviation and the
+            # factor within the mixed tolerances of tests/test_gpu_precision.py
+            assert abs(ms[i] - ref.m) <= 1
+            k = min(len(h_b), len(ref.history))
+            dev = np.abs(h_b[:k] - ref.history[:k]) / ref.history[:k]
+            print(f"instance {i}: n={P.A.shape[0]} s={P.C1.shape[1]} max rel deviation from the oracle {dev.max():.3e}")
+            assert dev.max() <= 1e-2
+            assert _xprobe(Z, Zo) <= 1e-4
         one.close()
     bt.close()
 

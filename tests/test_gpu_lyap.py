@@ -5,7 +5,7 @@ Three levels, each with its own tolerance:
     with the oracle's Prop. 3.1 evaluated on the GPU's own T_m, gamma and
     tau_{m+1,m} (exported by lyap_projected_matrix), at every m.  Both evaluate
     the same function of the same fp64 data, so
-        |rel_gpu(m) - rel_oracle(T_gpu)(m)| <= 1e-10 * max(rel, 1e-2) + 1e-13.
+        |rel_gpu(m) - rel_oracle(T_gpu)(m)| <= 1e-10 rel + HIST_ATOL.
   * the block Lanczos recurrence: T_m from the GPU (fused MGS + CholQR2) against
     T_m from the oracle (textbook MGS + Householder QR) while local
     orthogonality keeps them close: |dT| <= 1e-11 ||T||.
@@ -24,8 +24,11 @@ from oracle import lyap as olyap
 
 pytestmark = pytest.mark.gpu
 
-HIST_ATOL = 1e-10
+# relative 1e-10 per entry, plus an absolute floor (in units of beta^2) for entries whose
+# rounding is absolute: the last rows of eigenvectors of converged Ritz values are computed to
+# absolute, not relative, accuracy, so late entries carry an absolute error of a few eps
 HIST_RTOL = 1e-10
+HIST_ATOL = 1e-14
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +76,7 @@ def _check_on_gpu_T(sol, C, ms):
         ab, gam, tau = sol.projected(m)
         lam, Q = sla.eig_banded(ab, lower=True)
         rel = olyap.cheap_residual(lam, Q, gam, tau, s) / beta2
-        bound = 1e-10 * max(rel, 1e-2) + 1e-13
+        bound = HIST_RTOL * rel + HIST_ATOL
         worst = max(worst, abs(hist[m - 1] - rel) / bound)
     return worst
 

@@ -1,4 +1,4 @@
-"""The allocation-free residual entry point (lyap_residual_noalloc) against lyap_solve.
+"""The allocation-free residual entry point (lyap_residual_noalloc) against lyap_solve and the oracle.
 
 lyap_residual_noalloc serves callers that cannot allocate device memory when they need a
 residual norm, for instance code running inside another framework whose caching allocator
@@ -6,14 +6,19 @@ already holds the free memory.  It evaluates the same residual as the convergenc
 lyap_solve, with its scratch in a fixed array inside the library.  This test feeds it the
 projected matrices of a solve (exported by lyap_projected_matrix), calls it twice in a row
 (the second call must not see anything the first left in the shared array) and compares the
-results with the history lyap_solve recorded, within the tolerance of the check tests.
+results with the history lyap_solve recorded and with the FP64 oracle's residual formula on
+the same T_m, within the tolerance of the check tests.  After a first call (which, with lazy
+module loading, loads the library's device code and its array), further calls must leave the
+device's free memory and the caching allocator's reservation unchanged.
 
 The file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
+import scipy.linalg as sla
 
 import workloads as wl
+from oracle import lyap as olyap
 
 pytestmark = pytest.mark.gpu
 
@@ -61,8 +66,52 @@ def test_noalloc_residual_matches_solve_history(env):
             assert int(status.item()) == L.LYAP_OK
             got = float(rel.item())
             ref = float(hist[m - 1])
-            assert abs(got - ref) <= 1e-10 * max(ref, 1e-2) + 1e-13, (m, got, ref)
+            assert abs(got - ref) <= 1e-10 * ref + 1e-15, (m, got, ref)
+            lam, Q = sla.eig_banded(ab, lower=True)
+            ora = olyap.cheap_residual(lam, Q, gam, tau, s) / beta**2
+            assert abs(got - ora) <= 1e-10 * ora + 1e-15, (m, got, ora)
     sol.close()
+
+
+def test_noalloc_calls_allocate_nothing(env):
+    torch, L = env
+    from paper_1602_05033_gb300 import Solver
+
+    A = wl.laplacian_2d(12)
+    s = 3
+    C = wl.rhs(A.shape[0], s, 5)
+    sol = Solver(A, C, tol=1e-9, maxit=60)
+    sol.solve()
+    m = min(sol.m, 256 // s)
+    ab, gam, tau = sol.projected(m)
+    beta = float(np.linalg.norm(C))
+    sol.close()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ab_d = torch.from_numpy(np.ascontiguousarray(ab.T)).to(dev)
+    gam_d = torch.from_numpy(np.ascontiguousarray(gam)).to(dev)
+    tau_d = torch.from_numpy(np.ascontiguousarray(tau)).to(dev)
+    rel = torch.zeros(1, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def call():
+        L.lyap_residual_noalloc(s, m, ab_d.data_ptr(), s + 1, gam_d.data_ptr(), tau_d.data_ptr(), beta,
+                                rel.data_ptr(), status.data_ptr(), stream)
+
+    call()  # set-up call: loads the device code and the array on this device
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    res0 = torch.cuda.memory_reserved(dev)
+    vals = []
+    for _ in range(3):
+        call()
+        torch.cuda.synchronize()
+        vals.append(float(rel.item()))
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert torch.cuda.memory_reserved(dev) == res0
+    assert free1 == free0, (free0, free1)
+    assert int(status.item()) == L.LYAP_OK
+    assert vals[0] == vals[1] == vals[2]
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(env):
