@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--ek-precond", choices=["jacobi", "cnn", "both"], default="both")
     ap.add_argument("--count", type=int, default=32,
                     help="instances of the batch workload (256 is the full workload; its per-instance checks take minutes)")
-    ap.add_argument("--paths", default="mixed,f64",
+    ap.add_argument("--paths", default="f32x2,mixed,f64",
                     help="precision paths timed on the n = 1e6 workload; the headline is the fastest one whose "
                          "returned factor has an explicit relative residual <= tol")
     ap.add_argument("--profile-case", choices=["lanczos", "check", "sylv-check"], default=None,
@@ -485,6 +485,8 @@ PRECISIONS = {
     # name: (option value, dtype label, bytes per value of A in the SELL copy, bytes per basis value)
     "mixed": ("LYAP_PREC_MIXED", "f32 bulk (basis, SpMM, factor) / f64 CholQR2 factors, eigenproblem, residual", 8, 4),
     "f64": ("LYAP_PREC_F64", "f64", 12, 8),
+    "f32x2": ("LYAP_PREC_F32X2", "f32x2 bulk (basis, SpMM, sums, factor as float pairs on the fp32 pipe) / f64 "
+              "Cholesky factors, eigenproblem, residual", 8, 8),
 }
 
 
@@ -576,7 +578,8 @@ def ours(args):
                    "l2": "flushed before each step (512 MB write)"},
         "headline_path": head,
         "headline_reaches_tol": bool(hr.get("reaches_tol")),
-        "roofline": {"kernel": "block Lanczos step (SpMM, block MGS twice, CholQR2), " + head,
+        "roofline": {"kernel": "block Lanczos step (SpMM with the projection and Gram sums; then the row "
+                               "update to V_(j+1)), " + head,
                      "bound": "hbm", "achieved": hr["lanczos_GBps"], "peak": peak, "unit": "GB/s",
                      "frac": hr["lanczos_frac"], "traffic": sweep_traffic() if head == "mixed" else None,
                      "bytes_per_unit": hr["bytes_per_step"], "peak_source": peak_src},

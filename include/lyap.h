@@ -56,7 +56,8 @@ typedef enum {
 
 enum { LYAP_F64 = 0, LYAP_F32 = 1 };            /* element types              */
 enum { LYAP_MEM_DEVICE = 0, LYAP_MEM_HOST = 1 }; /* where a pointer lives       */
-enum { LYAP_PREC_F64 = 0, LYAP_PREC_MIXED = 1 }; /* bulk precision of the basis */
+/* bulk number type of the basis, the SpMM and the row arithmetic of a solve */
+enum { LYAP_PREC_F64 = 0, LYAP_PREC_MIXED = 1, LYAP_PREC_F32X2 = 2 };
 
 /* Sparse matrix in CSR form, read only during lyap_workspace_size and lyap_create.
  * Column indices of each row need not be sorted; the matrix must be symmetric
@@ -75,22 +76,27 @@ typedef struct {
   int maxit;             /* iteration cap (default 1000)                                    */
   int check_every;       /* d: test the residual at every d-th space dimension (Sec. 6);
                             default 1                                                      */
-  double trunc_eps;      /* truncation threshold of the reduced solution, relative to
-                            ||C1||_F ||C2||_F (eq. 2.5 with eps = 1e-12 in the paper);
-                            default 1e-12                                                  */
-  int precision;         /* LYAP_PREC_F64: basis and SpMM in fp64.  LYAP_PREC_MIXED: basis,
-                            SpMM and the factor in fp32, reductions, CholQR2 factors, the
-                            reduced eigenproblem and the residual in fp64 (default F64)     */
+  double trunc_eps;      /* truncation threshold eps of the reduced solution (eq. 2.5), relative
+                            to ||C1||_F ||C2||_F: the discarded eigenvalues (singular values for
+                            Sylvester) have a tail of Frobenius norm <= eps ||C1|| ||C2||.
+                            0 (default): eps = min(1e-12, tol / (10 (||T_m|| + ||J_m||))), so that
+                            the truncation changes the residual by at most tol / 10 (it moves
+                            A X + X B by at most (||A|| + ||B||) eps ||C1|| ||C2||; with ||C|| = 1
+                            the paper uses 1e-12)                                                */
+  int precision;         /* LYAP_PREC_F64: basis, SpMM and factor in fp64.
+                            LYAP_PREC_MIXED: basis, SpMM and factor in fp32; per-thread sums in
+                            fp32, combined across the GPU as float pairs.
+                            LYAP_PREC_F32X2: basis, SpMM, sums and factor in float pairs
+                            (hi + lo, about 48 bits) computed on the fp32 pipe; operator values
+                            as fp32 when given as LYAP_F32, else as float pairs; block sizes 1-4.
+                            In every mode the Cholesky factors, the reduced eigenproblem and the
+                            residual are fp64 (default F64)                                    */
   int sell_sigma;        /* SELL-C-sigma sorting window in rows (1 = no sorting; default 1) */
   int pass2_blocks;      /* k: basis blocks buffered per Z update in the second pass
                             (default 16)                                                   */
   int check_batch;       /* most convergence checks evaluated per batch (default 32)        */
   int zcap;              /* columns of Z the workspace can stage for LYAP_MEM_HOST output of
                             lyap_factor (default 0: device output only)                    */
-  int fused_steps;       /* 1: run each chunk of block Lanczos iterations as one cooperative
-                            launch (grid barriers between the four sweeps, W kept in shared
-                            memory; s <= 4, sell_sigma 1); 0: four launches per iteration
-                            (default 0)                                                     */
 } lyap_options;
 
 typedef struct lyap_handle lyap_handle;
@@ -119,8 +125,8 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1,
                 const lyap_options* opt, void* workspace, size_t ws_bytes,
                 void* stream, lyap_handle** out);
 
-/* Pass 1 (Alg. 1 steps 3-7): block Lanczos with block MGS done twice and CholQR2
- * normalisation (Alg. 2), the cheap residual norm of Prop. 3.1 / Alg. 3
+/* Pass 1 (Alg. 1 steps 3-7): block Lanczos (Alg. 2: the block MGS projections and a Cholesky
+ * QR normalisation, formed from one reduction per step), the cheap residual norm of Prop. 3.1 / Alg. 3
  * (Alg. 4 for Sylvester) at every check_every-th step, until tol or maxit.
  * Steps run in chunks ahead of their checks: the chunk after the one whose checks
  * find convergence has already been launched, and is discarded, including any sweep

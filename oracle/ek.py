@@ -115,6 +115,7 @@ class EKResult:
     history: np.ndarray
     m: int
     converged: bool
+    tol: float = 1e-8
 
 
 def solve(A, C, tol=1e-8, maxit=200, inner=None) -> EKResult:
@@ -135,14 +136,17 @@ def solve(A, C, tol=1e-8, maxit=200, inner=None) -> EKResult:
         if rel <= tol:
             converged = True
             break
-    return EKResult(log, np.array(hist), m, converged)
+    return EKResult(log, np.array(hist), m, converged, tol)
 
 
-def factor(res: EKResult, trunc_eps: float = 1e-12):
-    """Z = V_m (Q Ycheck) with the truncation of eq. 2.5 (eps = trunc_eps beta^2), stored basis."""
+def factor(res: EKResult, trunc_eps: float | None = None):
+    """Z = V_m (Q Ycheck) with the truncation of eq. 2.5 (eps = trunc_eps beta^2; None: the
+    tolerance-consistent lyap.auto_trunc_eps), stored basis."""
     log, m = res.log, res.m
     S = 2 * log.s
     lam, Q = sla.eig_banded(band_T(log, m), lower=True)
+    if trunc_eps is None:
+        trunc_eps = lyap.auto_trunc_eps(res.tol, float(np.max(np.abs(lam))))
     a = Q[:S, :].T @ log.gamma1
     Yt = -(a @ a.T) / (lam[:, None] + lam[None, :])
     sig, Wv = np.linalg.eigh(Yt)

@@ -158,6 +158,24 @@ class SolveResult:
     history: np.ndarray     # relative residual at m = 1..m_final (NaN where not checked)
     m: int
     converged: bool
+    tol: float = 1e-8
+
+
+def auto_trunc_eps(tol, norm_T, norm_J=None):
+    """Truncation threshold of eq. 2.5 tied to the residual target (relative to ||C1|| ||C2||).
+
+    The paper uses eps = 1e-12 with ||C||_F = 1 and tol = 1e-6.  Truncating the reduced solution
+    by a tail of Frobenius norm eps moves A X + X B by at most (||A||_2 + ||B||_2) eps, so on
+    operators with ||A|| ~ 1e5 a fixed 1e-12 alone would leave a residual ~1e-7.  The reading
+    used here keeps the truncation's share at tol / 10:
+        eps = min(1e-12, tol / (10 (||T_m||_2 + ||J_m||_2)))   (J_m = T_m for Lyapunov),
+    with ||T_m||_2 (<= ||A||_2, close to it once the extreme Ritz values have converged) the
+    largest |eigenvalue| of T_m.
+    """
+    nj = norm_T if norm_J is None else norm_J
+    if not (norm_T + nj > 0) or not np.isfinite(norm_T + nj):
+        return 1e-12
+    return min(1e-12, tol / (10.0 * (norm_T + nj)))
 
 
 def solve(A, C, tol=1e-8, maxit=1000, check_every=1, keep_basis=False) -> SolveResult:
@@ -189,20 +207,23 @@ def solve(A, C, tol=1e-8, maxit=1000, check_every=1, keep_basis=False) -> SolveR
                 break
         else:
             hist.append(np.nan)
-    return SolveResult(log=log, history=np.array(hist), m=m, converged=converged)
+    return SolveResult(log=log, history=np.array(hist), m=m, converged=converged, tol=tol)
 
 
-def truncated_factor(log: LanczosLog, m: int, trunc_eps: float = 1e-12):
+def truncated_factor(log: LanczosLog, m: int, trunc_eps: float | None = None, tol: float | None = None):
     """Low-rank factor of the reduced solution, truncated in the eigenbasis of T_m.
 
     Y~ = -(e_i^T S e_j / (lambda_i + lambda_j))_{ij} (eq. 3.2); its eigenvalues
     sigma (non-increasing) are truncated so that the discarded tail has
     Frobenius norm <= eps (eq. 2.5, applied to Y~ as in Sec. 3.2), with
-    eps = trunc_eps * beta^2; negative sigma (rounding) are never kept.
+    eps = trunc_eps * beta^2 (trunc_eps None: auto_trunc_eps(tol, ||T_m||));
+    negative sigma (rounding) are never kept.
     Returns M = Q_m Ycheck (s*m x t) such that Y_m ~= M M^T, and the kept sigma.
     """
     s = log.s
     lam, Q = eig_T(log, m)
+    if trunc_eps is None:
+        trunc_eps = auto_trunc_eps(tol, float(np.max(np.abs(lam))))
     a = Q[:s, :].T @ log.gamma
     Yt = -(a @ a.T) / (lam[:, None] + lam[None, :])
     sig, Wv = np.linalg.eigh(Yt)
@@ -238,10 +259,11 @@ def regenerate_basis(A, C, log: LanczosLog, m: int):
         Vprev, Vcur = Vcur, Vnext
 
 
-def factor(A, C, res: SolveResult, trunc_eps: float = 1e-12, two_pass: bool = True):
-    """Alg. 1 steps 8-9: Z_m = V_m (Q_m Ycheck), by the two-pass device or the stored basis."""
+def factor(A, C, res: SolveResult, trunc_eps: float | None = None, two_pass: bool = True):
+    """Alg. 1 steps 8-9: Z_m = V_m (Q_m Ycheck), by the two-pass device or the stored basis.
+    trunc_eps None: the tolerance-consistent threshold of auto_trunc_eps with the solve's tol."""
     s, m = res.log.s, res.m
-    M, sig = truncated_factor(res.log, m, trunc_eps)
+    M, sig = truncated_factor(res.log, m, trunc_eps, res.tol)
     n = C.shape[0]
     Z = np.zeros((n, M.shape[1]))
     if two_pass:

@@ -27,6 +27,7 @@ class SylvResult:
     history: np.ndarray
     m: int
     converged: bool
+    tol: float = 1e-8
 
 
 def cheap_residual(lam, Q, ups, P, g1, g2, tau, iota, s):
@@ -85,18 +86,20 @@ def solve(A, B, C1, C2, tol=1e-8, maxit=1000, check_every=1, keep_basis=False) -
                 break
         else:
             hist.append(np.nan)
-    return SylvResult(logA, logB, np.array(hist), m, converged)
+    return SylvResult(logA, logB, np.array(hist), m, converged, tol)
 
 
-def truncated_factors(logA, logB, m, trunc_eps=1e-12):
+def truncated_factors(logA, logB, m, trunc_eps=None, tol=None):
     """Truncated SVD of Y~ (Sec. 5.1): Y~ ~= Y1 Y2^T with ||tail||_F <= eps.
 
     Returns M1 = Q Y1 and M2 = P Y2 (each s*m x t) and the kept singular values;
-    eps = trunc_eps * ||C1||_F ||C2||_F.
+    eps = trunc_eps * ||C1||_F ||C2||_F (trunc_eps None: lyap.auto_trunc_eps(tol, ||T_m||, ||J_m||)).
     """
     s = logA.s
     lam, Q = lyap.eig_T(logA, m)
     ups, P = lyap.eig_T(logB, m)
+    if trunc_eps is None:
+        trunc_eps = lyap.auto_trunc_eps(tol, float(np.max(np.abs(lam))), float(np.max(np.abs(ups))))
     a = Q[:s, :].T @ logA.gamma
     b = P[:s, :].T @ logB.gamma
     Yt = -(a @ b.T) / (lam[:, None] + ups[None, :])
@@ -108,10 +111,10 @@ def truncated_factors(logA, logB, m, trunc_eps=1e-12):
     return Q @ (U[:, :t] * r), P @ (Vt[:t, :].T * r), sig[:t]
 
 
-def factor(A, B, C1, C2, res: SylvResult, trunc_eps=1e-12):
+def factor(A, B, C1, C2, res: SylvResult, trunc_eps=None):
     """Z1 = V_m (Q Y1), Z2 = U_m (P Y2), both by the two-pass device (6s stored vectors)."""
     s, m = res.logA.s, res.m
-    M1, M2, sig = truncated_factors(res.logA, res.logB, m, trunc_eps)
+    M1, M2, sig = truncated_factors(res.logA, res.logB, m, trunc_eps, res.tol)
     Z1 = np.zeros((C1.shape[0], M1.shape[1]))
     Z2 = np.zeros((C2.shape[0], M2.shape[1]))
     for j, Vj in enumerate(lyap.regenerate_basis(A, C1, res.logA, m)):

@@ -26,7 +26,7 @@ LYAP_ERR_EIGEN = 10
 
 LYAP_F64, LYAP_F32 = 0, 1
 LYAP_MEM_DEVICE, LYAP_MEM_HOST = 0, 1
-LYAP_PREC_F64, LYAP_PREC_MIXED = 0, 1
+LYAP_PREC_F64, LYAP_PREC_MIXED, LYAP_PREC_F32X2 = 0, 1, 2
 
 # every symbol include/lyap.h declares
 EXPORTED = (
@@ -84,7 +84,6 @@ class lyap_options(ct.Structure):
         ("pass2_blocks", ct.c_int),
         ("check_batch", ct.c_int),
         ("zcap", ct.c_int),
-        ("fused_steps", ct.c_int),
     ]
 
 

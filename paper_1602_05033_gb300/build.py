@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblyap.so")
-SOURCES = ["api.cu", "sell.cu", "lanczos.cu", "check.cu", "factor.cu", "batch.cu", "ek.cu"]
+SOURCES = ["api.cu", "sell.cu", "step.cu", "lanczos.cu", "check.cu", "factor.cu", "batch.cu", "ek.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE]
 
@@ -38,7 +38,7 @@ def _newer(target: str, deps: list[str]) -> bool:
 
 def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "lyap.h")]
+    headers = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "ff.cuh"), os.path.join(INCLUDE, "lyap.h")]
     extra = extra or []
     cc = nvcc()
 

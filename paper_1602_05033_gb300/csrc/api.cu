@@ -12,25 +12,31 @@
 #include <vector>
 
 size_t factor_ws_bytes(int s, int nmax, int sylv);
-size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32);
+size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk);
 int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col, const void* d_val, int sigma,
-               int bulk_f32, OpDev& op, int* d_flags, cudaStream_t st);
+               int bulk, OpDev& op, int* d_flags, cudaStream_t st);
 
 namespace {
 
 
-// one wave of the row sweeps on this device (at least 256 rows per CTA); the reduction
-// order depends on the grid, so results are reproducible run to run on a given GPU model
-int sweep_grid_for(int64_t n, int s, int bulk_f32) {
+// CTAs of the two sweeps of a block Lanczos step: as many as fit on the device at once (one
+// wave), at most one per 256 rows.  The reduction order depends on the grid, so results are
+// reproducible run to run on a given GPU model.
+void sweep_grids_for(int64_t n, int s, int bulk, int pair, int* grid_a, int* grid_b) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
-  int64_t g = (int64_t)sms * sweep_blocks_per_sm(s, bulk_f32);
+  int pa = 1, pb = 1;
+  step_blocks_per_sm(s, bulk, pair, &pa, &pb);
   const int64_t byrows = (n + 255) / 256;
-  if (g > byrows) g = byrows;
-  if (g < 1) g = 1;
-  if (g > kMaxSweepGrid) g = kMaxSweepGrid;
-  return (int)g;
+  auto clamp = [&](int64_t g) {
+    if (g > byrows) g = byrows;
+    if (g < 1) g = 1;
+    if (g > kMaxSweepGrid) g = kMaxSweepGrid;
+    return (int)g;
+  };
+  *grid_a = clamp((int64_t)sms * pa);
+  *grid_b = clamp((int64_t)sms * pb);
 }
 
 int valid_s(int s) { return s == 1 || s == 2 || s == 3 || s == 4 || s == 8; }
@@ -49,13 +55,12 @@ lyap_options resolve(const lyap_options* opt) {
   if (opt) {
     if (opt->maxit > 0) o.maxit = opt->maxit;
     if (opt->check_every > 0) o.check_every = opt->check_every;
-    if (opt->trunc_eps > 0) o.trunc_eps = opt->trunc_eps;
+    o.trunc_eps = opt->trunc_eps > 0 ? opt->trunc_eps : 0.0;
     o.precision = opt->precision;
     if (opt->sell_sigma > 0) o.sell_sigma = opt->sell_sigma;
     if (opt->pass2_blocks >= 2) o.pass2_blocks = opt->pass2_blocks;
     if (opt->check_batch > 0) o.check_batch = opt->check_batch;
     if (opt->zcap > 0) o.zcap = opt->zcap;
-    o.fused_steps = opt->fused_steps == 1 ? 1 : 0;
   }
   if (o.check_batch > 256) o.check_batch = 256;
   return o;
@@ -78,14 +83,14 @@ int validate_csr(const lyap_csr* A) { return check_csr(A); }
 int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external) {
   p.s = s;
   p.sylv = B != nullptr;
-  p.bulk_f32 = o.precision == LYAP_PREC_MIXED;
+  p.bulk = o.precision;
   p.maxit = o.maxit;
   p.check_batch = o.check_batch;
   p.check_batch_req = o.check_batch;
   p.nmax = s * o.maxit;
   p.pass2_blocks = o.pass2_blocks;
   p.zcap = o.zcap;
-  const size_t w = p.bulk_f32 ? 4 : 8;
+  const size_t w = p.bulk == LYAP_PREC_MIXED ? 4 : 8;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t r = off;
@@ -99,19 +104,21 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
     int rc = sell_plan_host(M, o.sell_sigma, &nsl, &snnz);
     if (rc != LYAP_OK) return rc;
     Plan::OpOff& q = p.op[k];
+    q.val_pair = p.bulk == LYAP_PREC_F32X2 && M->val_dtype == LYAP_F64;
+    const size_t wv = p.bulk == LYAP_PREC_F64 ? 8 : (q.val_pair ? 8 : 4);
     q.n = M->n;
     q.nslices = nsl;
     q.sell_nnz = snnz;
     q.slice_ptr = take(sizeof(int64_t) * (nsl + 1));
     q.slice_w = take(sizeof(int32_t) * nsl);
     q.sell_col = take(sizeof(int32_t) * (size_t)snnz);
-    q.sell_val = take(w * (size_t)snnz);
+    q.sell_val = take(wv * (size_t)snnz);
     q.perm = take(o.sell_sigma > 1 ? sizeof(int32_t) * (size_t)M->n : 0);
     for (int r = 0; r < 3; ++r) q.V[r] = take(w * (size_t)M->n * s);
     q.W = take(w * (size_t)M->n * s);
     q.C = take(sizeof(double) * (size_t)M->n * s);
     q.log = take(sizeof(double) * (size_t)(o.maxit + 1) * LOG_NREC * s * s);
-    q.partials = take(sizeof(double) * (size_t)kMaxSweepGrid * 7 * s * s);  // the fused steps use three stages
+    q.partials = take(sizeof(double) * (size_t)kMaxSweepGrid * max_nacc(s));
     q.counter = take(256);
     nmaxop = std::max<int64_t>(nmaxop, M->n);
   }
@@ -138,7 +145,7 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
   p.check = take(p.check_bytes);
   p.factor_bytes = factor_ws_bytes(s, p.nmax, p.sylv);
   size_t p2 = 0;
-  for (int k = 0; k < 1 + p.sylv; ++k) p2 += pass2_ws_bytes(p.op[k].n, s, o.pass2_blocks, p.bulk_f32);
+  for (int k = 0; k < 1 + p.sylv; ++k) p2 += pass2_ws_bytes(p.op[k].n, s, o.pass2_blocks, p.bulk);
   p.factor = take(p.factor_bytes + p2);
   p.zstage = take(o.zcap > 0 ? sizeof(double) * (size_t)o.zcap * (A->n + (B ? B->n : 0)) : 0);
   p.staging_bytes = staging_bytes(A) + staging_bytes(B);
@@ -186,13 +193,12 @@ void lyap_default_options(lyap_options* opt) {
   if (!opt) return;
   opt->maxit = 1000;
   opt->check_every = 1;
-  opt->trunc_eps = 1e-12;
+  opt->trunc_eps = 0.0;
   opt->precision = LYAP_PREC_F64;
   opt->sell_sigma = 1;
   opt->pass2_blocks = 16;
   opt->check_batch = 32;
   opt->zcap = 0;
-  opt->fused_steps = 0;
 }
 
 const char* lyap_status_string(int status) {
@@ -218,7 +224,9 @@ int lyap_workspace_size(const lyap_csr* A, const lyap_csr* B, int s, const lyap_
   if (rc != LYAP_OK) return rc;
   if (B && (rc = check_csr(B)) != LYAP_OK) return rc;
   lyap_options o = resolve(opt);
-  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
+  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED && o.precision != LYAP_PREC_F32X2)
+    return LYAP_ERR_ARG;
+  if (!step_supported(o.precision, s)) return LYAP_ERR_ARG;
   Plan p;
   rc = make_plan(A, B, s, o, p, 0);
   if (rc != LYAP_OK) return rc;
@@ -239,7 +247,9 @@ int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const 
   if (rc != LYAP_OK) return rc;
   if (B && (rc = check_csr(B)) != LYAP_OK) return rc;
   lyap_options o = resolve(opt);
-  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
+  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED && o.precision != LYAP_PREC_F32X2)
+    return LYAP_ERR_ARG;
+  if (!step_supported(o.precision, s)) return LYAP_ERR_ARG;
   Plan p;
   rc = make_plan(A, B, s, o, p, external);
   if (rc != LYAP_OK) return rc;
@@ -247,7 +257,8 @@ int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const 
   *out = nullptr;
   lyap_handle* h = new (std::nothrow) lyap_handle();
   if (!h) return LYAP_ERR_ARG;
-  p.sweep_grid = sweep_grid_for(std::max(A->n, B ? B->n : (int64_t)0), s, p.bulk_f32);
+  sweep_grids_for(std::max(A->n, B ? B->n : (int64_t)0), s, p.bulk, p.op[0].val_pair || (p.sylv && p.op[1].val_pair),
+                  &p.sweep_grid, &p.sweep_grid_b);
   h->plan = p;
   h->ws = static_cast<char*>(workspace);
   h->s = s;
@@ -285,6 +296,7 @@ int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const 
     op.sell_col = at<int32_t>(h->ws, q.sell_col);
     op.sell_val = h->ws + q.sell_val;
     op.perm = o.sell_sigma > 1 ? at<int32_t>(h->ws, q.perm) : nullptr;
+    op.val_pair = q.val_pair;
     for (int r = 0; r < 3; ++r) op.V[r] = h->ws + q.V[r];
     op.W = h->ws + q.W;
     op.C = at<double>(h->ws, q.C);
@@ -311,7 +323,7 @@ int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const 
       cl = dcl;
       vl = dvl;
     }
-    rc = sell_build(M, rp, cl, vl, o.sell_sigma, p.bulk_f32, op, h->flags, st);
+    rc = sell_build(M, rp, cl, vl, o.sell_sigma, p.bulk, op, h->flags, st);
     if (rc != LYAP_OK) return fail(rc);
     h->launches += 1;
     const cudaMemcpyKind kind = c_mem == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -341,7 +353,7 @@ void solve_begin(lyap_handle* h, cudaStream_t st) {
   k_init_flags<<<(p.maxit + 255) / 256, 256, 0, st>>>(h->flags, h->hist, h->chk_err, p.maxit);
   h->launches += 1;
   for (int k = 0; k < 1 + p.sylv; ++k)
-    h->launches += launch_init_block(h->op[k], h->s, p.bulk_f32, p.sweep_grid, h->flags, st);
+    h->launches += launch_init_block(h->op[k], h->s, p.bulk, p.sweep_grid, h->flags, st);
 }
 
 // records the outcome of a solve (m, convergence, iterations run), copies the history to
@@ -405,15 +417,9 @@ int lyap_solve(lyap_handle* h, void* stream) {
   auto launch_chunk = [&](int from, int upto, int c) {
     int* fw = cw + (c & 1);
     cudaEventRecord(c_beg[c & 1], st);
-    for (int k = 0; k < 1 + p.sylv; ++k) {
-      if (h->opt.fused_steps == 1 && upto > from &&
-          launch_fused_steps(h->op[k], s, p.bulk_f32, from + 1, upto - from, fw, st)) {
-        h->launches += 1;
-        continue;
-      }
+    for (int k = 0; k < 1 + p.sylv; ++k)
       for (int j = from + 1; j <= upto; ++j)
-        h->launches += launch_lanczos_step(h->op[k], s, p.bulk_f32, p.sweep_grid, j, fw, st);
-    }
+        h->launches += launch_lanczos_step(h->op[k], s, p.bulk, p.sweep_grid, p.sweep_grid_b, j, fw, st);
     cudaEventRecord(c_end[c & 1], st);
   };
   int chunk = std::min(4, p.check_batch_req);
@@ -525,7 +531,7 @@ int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, 
   if (!h || !h->solved || h->factored || !Z1 || !t_out || tcap < 0) return LYAP_ERR_ARG;
   if ((h->plan.sylv != 0) != (Z2 != nullptr)) return LYAP_ERR_ARG;
   if (z_dtype != LYAP_F64 && z_dtype != LYAP_F32) return LYAP_ERR_ARG;
-  if (z_dtype == LYAP_F32 && !h->plan.bulk_f32) return LYAP_ERR_ARG;
+  if (z_dtype == LYAP_F32 && h->plan.bulk != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
   if (ldz1 < tcap || (Z2 && ldz2 < tcap)) return LYAP_ERR_ARG;
   if (z_mem != LYAP_MEM_DEVICE && z_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
   if (z_mem == LYAP_MEM_HOST && tcap > h->plan.zcap) return LYAP_ERR_ARG;

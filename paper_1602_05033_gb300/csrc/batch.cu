@@ -50,6 +50,8 @@ int plan_batch(int count, const lyap_csr* A, const int* s, const lyap_options& o
   bp.inst_off.resize(count);
   bp.inst_bytes.resize(count);
   size_t slot_full = 0, fac = 0;
+  // the batched sweeps run the fp64 and fp32 bulk types
+  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
   for (int b = 0; b < count; ++b) {
     if (!valid_block(s[b])) return LYAP_ERR_ARG;
     int rc = validate_csr(&A[b]);
@@ -62,7 +64,7 @@ int plan_batch(int count, const lyap_csr* A, const int* s, const lyap_options& o
     const int nmax = s[b] * o.maxit;
     slot_full = std::max(slot_full, check_slot_bytes(s[b], nmax));
     fac = std::max(fac, factor_ws_bytes(s[b], nmax, 0) +
-                            pass2_ws_bytes(A[b].n, s[b], o.pass2_blocks, o.precision == LYAP_PREC_MIXED));
+                            pass2_ws_bytes(A[b].n, s[b], o.pass2_blocks, o.precision));
     bp.tile_cap += (size_t)((A[b].n + kRowChoices[0] - 1) / kRowChoices[0]) + 1;
   }
   bp.pool_check = lyap_align256((int64_t)std::max(slot_full, kPoolCheckMin));

@@ -32,6 +32,7 @@ enum {
   REC_TDIAG,      // tau_{jj}   = alpha_j + beta_j (raw)
   REC_TPREV,      // tau_{j-1,j} = alpha_{j-1} + beta_{j-1} (raw)
   REC_CROSS,      // V_j^T V_{j-1} (rounding-level, used by the fused MGS algebra)
+  REC_GCC,        // V_j^T V_j as measured in step j (the fp32 basis uses it in step j + 1)
   LOG_NREC
 };
 
@@ -55,6 +56,7 @@ struct OpDev {
   int32_t* sell_col = nullptr;   // sell_nnz
   void* sell_val = nullptr;      // sell_nnz, fp64 or fp32
   int32_t* perm = nullptr;       // n (SELL row -> original row), nullptr when sigma == 1
+  int val_pair = 0;              // SELL values stored as float pairs (float-pair bulk, values not exact in fp32)
   void* V[3] = {nullptr, nullptr, nullptr};
   void* W = nullptr;
   double* C = nullptr;           // fp64 copy of the right-hand side (n x s)
@@ -67,9 +69,10 @@ struct OpDev {
 struct Plan {
   int s = 1;
   int sylv = 0;
-  int bulk_f32 = 0;
+  int bulk = LYAP_PREC_F64;  // bulk number type of the basis: LYAP_PREC_F64, _MIXED (fp32), _F32X2 (pairs)
   int maxit = 1000;
-  int sweep_grid = 0;     // CTAs of every row sweep
+  int sweep_grid = 0;     // CTAs of the reducing sweep of a block Lanczos step (and of the init sweeps)
+  int sweep_grid_b = 0;   // CTAs of the sweep writing V_{j+1}
   int check_batch = 32;   // full-size (nmax) slots that fit in the check area (the factor uses one)
   int check_batch_req = 32;  // checks per batch asked for; a batch's slots are sized by its largest m
   int nmax = 0;           // largest reduced dimension s * maxit
@@ -80,6 +83,7 @@ struct Plan {
   struct OpOff {
     size_t slice_ptr, slice_w, sell_col, sell_val, perm, V[3], W, C, log, partials, counter;
     int64_t n, nslices, sell_nnz;
+    int val_pair;
   } op[2];
   size_t hist = 0, flags = 0, chk_err = 0, check = 0, check_bytes = 0, factor = 0, factor_bytes = 0, zstage = 0,
          staging = 0, staging_bytes = 0;
@@ -147,12 +151,17 @@ struct BTile {
 // sell.cu
 int sell_plan_host(const lyap_csr* A, int sigma, int64_t* nslices, int64_t* sell_nnz);
 
-// lanczos.cu
+// step.cu: one block Lanczos step of one operator (two sweeps), its initial block, the second pass
 int max_nacc(int s);
-int sweep_blocks_per_sm(int s, int bulk_f32);
-int launch_init_block(OpDev& op, int s, int bulk_f32, int grid, int* d_flags, cudaStream_t st);
-int launch_lanczos_step(OpDev& op, int s, int bulk_f32, int grid, int j, int* d_flags, cudaStream_t st);
-int launch_fused_steps(OpDev& op, int s, int bulk_f32, int j0, int nsteps, int* d_flags, cudaStream_t st);
+int step_supported(int bulk, int s);
+void step_blocks_per_sm(int s, int bulk, int pair, int* per_sm_a, int* per_sm_b);
+int launch_init_block(OpDev& op, int s, int bulk, int grid, int* d_flags, cudaStream_t st);
+int launch_lanczos_step(OpDev& op, int s, int bulk, int grid_a, int grid_b, int j, int* d_flags, cudaStream_t st);
+void launch_pass2(OpDev& op, int s, int bulk, int grid, int j, const void* vp, int64_t ldp, const void* vc,
+                  int64_t ldc, void* vn, int64_t ldn, cudaStream_t st);
+void launch_pass2_v1(OpDev& op, int s, int bulk, int grid, void* vn, int64_t ldn, cudaStream_t st);
+
+// lanczos.cu: the batched sweeps (many instances per launch)
 int launch_batch_step(int s, int bulk_f32, const BInst* d_inst, const BTile* d_tiles, int ntiles, int grid,
                       cudaStream_t st);
 int batch_blocks_per_sm(int s, int bulk_f32);
@@ -175,7 +184,7 @@ int round_status(lyap_handle* h);
 
 // factor.cu
 size_t factor_ws_bytes(int s, int nmax, int sylv);
-size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32);
+size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk);
 int run_factor_basis(lyap_handle* h, const double* basis, int64_t n, double* Z, int64_t ldz, int tcap, int* t_out,
                      cudaStream_t st);
 int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,

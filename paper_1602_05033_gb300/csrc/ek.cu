@@ -1040,7 +1040,7 @@ int lyap_ek_create(const lyap_csr* A, const double* C, int c_mem, int s, double 
   lyap_handle& hk = e->hk;
   hk.plan.s = S;
   hk.plan.sylv = 0;
-  hk.plan.bulk_f32 = 0;
+  hk.plan.bulk = LYAP_PREC_F64;
   hk.plan.maxit = maxit;
   hk.plan.nmax = S * maxit;
   hk.plan.check_batch = 1;

@@ -15,15 +15,13 @@
 // M = Q Ycheck is then accumulated into Z = sum_j V_j E_j^T M while the basis is
 // regenerated from the logged coefficients (k blocks buffered per GEMM update).
 #include "common.cuh"
+#include "ff.cuh"
 
 #include <float.h>
 #include <math.h>
 #include <vector>
 #include <algorithm>
 
-void launch_pass2(OpDev& op, int s, int bulk_f32, int grid, int j, const void* vp, int64_t ldp, const void* vc,
-                  int64_t ldc, void* vn, int64_t ldn, cudaStream_t st);
-void launch_pass2_v1(OpDev& op, int s, int bulk_f32, int grid, void* vn, int64_t ldn, cudaStream_t st);
 void check_slot0(lyap_handle* h, int opi, double** lam, double** a, double** w);
 
 namespace {
@@ -535,6 +533,81 @@ __global__ void __launch_bounds__(256) k_gemm_accum(int64_t n, int K, int t, con
   }
 }
 
+// Z += Vbuf M with float pairs: V holds rows of S pairs per block (the S high parts, then the S
+// low parts), Z holds pairs in the 8 bytes of each of its doubles until k_pairs_to_double
+template <int S>
+__global__ void __launch_bounds__(256) k_gemm_accum_ff(int64_t n, int K, int t, const float* __restrict__ Vb,
+                                                       int64_t ldv, const double* __restrict__ Mg, int64_t ldm,
+                                                       float2* __restrict__ Z, int64_t ldz) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ ff As[BK][BM + 1];
+  __shared__ ff Bs[BK][BN];
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int col0 = blockIdx.y * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  ff acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = ff_make(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+      const int r = idx / BK, kk = idx % BK;
+      const int64_t gr = row0 + r;
+      const int k = k0 + kk;
+      ff v = ff_make(0.f, 0.f);
+      if (gr < n && k < K) {
+        // value k of row gr: block k / S, column k % S
+        const float* p = Vb + 2 * (gr * ldv + (int64_t)(k / S) * S);
+        v = ff_make(p[k % S], p[S + k % S]);
+      }
+      As[kk][r] = v;
+    }
+    for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
+      const int kk = idx / BN, c = idx % BN;
+      Bs[kk][c] = (k0 + kk < K && col0 + c < t) ? ff_from_double(Mg[(int64_t)(k0 + kk) * ldm + col0 + c])
+                                                 : ff_make(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      ff av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ff_acc(acc[i][j], av[i], bv[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gr = row0 + ty * 4 + i;
+    if (gr >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gc = col0 + tx * 4 + j;
+      if (gc < t) {
+        const float2 z = Z[gr * ldz + gc];
+        const ff r = ff_add(ff_make(z.x, z.y), ff_norm(acc[i][j]));
+        Z[gr * ldz + gc] = make_float2(r.hi, r.lo);
+      }
+    }
+  }
+}
+
+// the pairs accumulated in Z's doubles -> their fp64 values
+__global__ void k_pairs_to_double(double* Z, int64_t n, int64_t ldz, int t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * t) return;
+  double* z = Z + (i / t) * ldz + (i % t);
+  const float2 p = *reinterpret_cast<const float2*>(z);
+  *z = (double)p.x + (double)p.y;
+}
+
 template <typename TZ>
 __global__ void k_zero_cols(TZ* Z, int64_t n, int64_t ldz, int t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -542,16 +615,25 @@ __global__ void k_zero_cols(TZ* Z, int64_t n, int64_t ldz, int t) {
   Z[(i / t) * ldz + (i % t)] = TZ(0);
 }
 
-void gemm_accum(int bulk_f32, int z_f32, int64_t n, int K, int t, const void* Vb, int64_t ldv, const double* Mg,
+void gemm_accum(int bulk, int s, int z_f32, int64_t n, int K, int t, const void* Vb, int64_t ldv, const double* Mg,
                 int64_t ldm, void* Z, int64_t ldz, cudaStream_t st) {
   if (t <= 0 || K <= 0) return;
   dim3 grid((unsigned)((n + 63) / 64), (unsigned)((t + 63) / 64));
-  if (bulk_f32 && z_f32)
+  if (bulk == LYAP_PREC_F32X2) {
+    const int64_t ldvv = ldv;  // values per row of the buffer
+    switch (s) {
+      case 1: k_gemm_accum_ff<1><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
+      case 2: k_gemm_accum_ff<2><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
+      case 3: k_gemm_accum_ff<3><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
+      case 4: k_gemm_accum_ff<4><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
+    }
+  } else if (bulk == LYAP_PREC_MIXED && z_f32) {
     k_gemm_accum<float, float><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float*)Z, ldz);
-  else if (bulk_f32)
+  } else if (bulk == LYAP_PREC_MIXED) {
     k_gemm_accum<float, double><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (double*)Z, ldz);
-  else
+  } else {
     k_gemm_accum<double, double><<<grid, 256, 0, st>>>(n, K, t, (const double*)Vb, ldv, Mg, ldm, (double*)Z, ldz);
+  }
 }
 
 FactorWs carve(char* base, int s, int nmax2, int tmax, int nmax) {
@@ -575,8 +657,8 @@ int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void*
                 cudaStream_t st) {
   OpDev& op = h->op[opi];
   const int s = h->s, m = h->m, kb = h->plan.pass2_blocks;
-  const int bulk = h->plan.bulk_f32;
-  const size_t w = bulk ? 4 : 8;
+  const int bulk = h->plan.bulk;
+  const size_t w = bulk == LYAP_PREC_MIXED ? 4 : 8;
   const int64_t n = op.n;
   const int64_t ldb = (int64_t)kb * s;
   char* buf[2] = {reinterpret_cast<char*>(op.V[0]) + 0, nullptr};
@@ -607,9 +689,14 @@ int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void*
       const int g = (j - 1) / kb;
       const int j0 = g * kb + 1;
       const int nblk = j - j0 + 1;
-      gemm_accum(bulk, z_f32, n, nblk * s, tk, buf[g & 1], ldb, M + (size_t)(j0 - 1) * s * ldm, ldm, Z, ldz, st);
+      gemm_accum(bulk, s, z_f32, n, nblk * s, tk, buf[g & 1], ldb, M + (size_t)(j0 - 1) * s * ldm, ldm, Z, ldz, st);
       h->launches += 1;
     }
+  }
+  if (bulk == LYAP_PREC_F32X2 && tk > 0) {
+    const int64_t tot = n * tk;
+    k_pairs_to_double<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((double*)Z, n, ldz, tk);
+    h->launches += 1;
   }
   return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
 }
@@ -642,9 +729,33 @@ size_t factor_ws_bytes(int s, int nmax, int sylv) {
   return b;
 }
 
-size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk_f32) {
-  const size_t w = bulk_f32 ? 4 : 8;
+size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk) {
+  const size_t w = bulk == LYAP_PREC_MIXED ? 4 : 8;
   return 2 * (size_t)lyap_align256((int64_t)(n * (int64_t)kb * s * w));
+}
+
+// eps of eq. 2.5: the option, or, when it is 0, min(1e-12, tol / (10 (||T_m|| + ||J_m||))), so that
+// the truncation moves the residual by at most tol / 10 (J_m = T_m for Lyapunov).  ||T_m|| is the
+// largest |eigenvalue|, the first or last of the ascending list.
+int trunc_eps_of(lyap_handle* h, const double* lam_a, const double* lam_b, int N, double* eps, cudaStream_t st) {
+  if (h->opt.trunc_eps > 0.0) {
+    *eps = h->opt.trunc_eps;
+    return LYAP_OK;
+  }
+  double ends[4] = {0.0, 0.0, 0.0, 0.0};
+  LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[0], lam_a, sizeof(double), cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[1], lam_a + N - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (lam_b) {
+    LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[2], lam_b, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[3], lam_b + N - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  const double na = fmax(fabs(ends[0]), fabs(ends[1]));
+  const double nb = lam_b ? fmax(fabs(ends[2]), fabs(ends[3])) : na;
+  double e = 1e-12;
+  if (na + nb > 0.0 && isfinite(na + nb)) e = fmin(e, h->tol / (10.0 * (na + nb)));
+  *eps = e;
+  return LYAP_OK;
 }
 
 // Sylvester factors (Sec. 5.1): Y~_ij = -(a_i . b_j)/(lambda_i + upsilon_j) is the off-diagonal
@@ -691,7 +802,10 @@ int run_factor_sylv(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ld
   check_slot0(h, 1, &lb, &ab, &wb);
   k_stack<<<(N2 + 127) / 128, 128, 0, st>>>(la, aa, lb, ab, N, s, mu, cst);
   // 2. pivoted Cholesky of the stacked kernel
-  const double eps_abs = h->opt.trunc_eps * h->op[0].beta * h->op[1].beta;
+  double teps = 0.0;
+  int rc_e = trunc_eps_of(h, la, lb, N, &teps, st);
+  if (rc_e != LYAP_OK) return rc_e;
+  const double eps_abs = teps * h->op[0].beta * h->op[1].beta;
   k_pivoted_cholesky<<<1, kPcThreads, 0, st>>>(mu, cst, N2, s, tmax, 1e-2 * eps_abs, f, dg);
   h->launches += 2;
   LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -770,7 +884,10 @@ int factor_core(lyap_handle* h, int tcap, int* t_out, double** M_out, int* ldm_o
   check_slot0(h, 0, &lam, &a, &w);
   // 2. pivoted Cholesky of Y~ = -(a_i . a_j)/(lambda_i + lambda_j)
   const double beta2 = h->op[0].beta * h->op[0].beta;
-  const double eps_abs = h->opt.trunc_eps * beta2;
+  double teps = 0.0;
+  int rc_e = trunc_eps_of(h, lam, nullptr, N, &teps, st);
+  if (rc_e != LYAP_OK) return rc_e;
+  const double eps_abs = teps * beta2;
   k_pivoted_cholesky<<<1, kPcThreads, 0, st>>>(lam, a, N, s, tmax, 1e-2 * eps_abs, f, dg);
   h->launches += 1;
   LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -844,7 +961,7 @@ int run_factor_basis(lyap_handle* h, const double* basis, int64_t n, double* Z, 
     const int64_t tot = n * tk;
     k_zero_cols<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Z, n, ldz, tk);
     for (int j = 0; j < h->m; ++j)
-      gemm_accum(0, 0, n, s, tk, basis + (size_t)j * n * s, s, M + (size_t)j * s * ldm, ldm, Z, ldz, st);
+      gemm_accum(LYAP_PREC_F64, s, 0, n, s, tk, basis + (size_t)j * n * s, s, M + (size_t)j * s * ldm, ldm, Z, ldz, st);
     h->launches += 1 + h->m;
   }
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));

@@ -64,6 +64,15 @@ int plan(const lyap_csr* A, int sigma, SellPlanHost& p) {
   return LYAP_OK;
 }
 
+// an operator value in the stored type: fp64, fp32, or a float pair (hi = fl32(v), lo = fl32(v - hi))
+template <typename Tout>
+__device__ __forceinline__ Tout sell_value(double v) { return Tout(v); }
+template <>
+__device__ __forceinline__ float2 sell_value<float2>(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 template <typename Tin, typename Tout>
 __global__ void k_sell_fill(int64_t n, int64_t nsl, const int64_t* __restrict__ rowptr,
                             const int32_t* __restrict__ col, const Tin* __restrict__ val,
@@ -90,16 +99,16 @@ __global__ void k_sell_fill(int64_t n, int64_t nsl, const int64_t* __restrict__ 
       if (c < 0 || c >= n) {
         atomicOr(flags, DERR_BOUNDS);
         scol[e] = pad_col;
-        sval[e] = Tout(0);
+        sval[e] = sell_value<Tout>(0.0);
       } else {
         scol[e] = c;
         const Tin v = val[b + j];
         if (!isfinite((double)v)) atomicOr(flags, DERR_NONFINITE);
-        sval[e] = Tout(v);
+        sval[e] = sell_value<Tout>((double)v);
       }
     } else {
       scol[e] = pad_col;
-      sval[e] = Tout(0);
+      sval[e] = sell_value<Tout>(0.0);
     }
   }
 }
@@ -117,7 +126,7 @@ int sell_plan_host(const lyap_csr* A, int sigma, int64_t* nslices, int64_t* sell
 
 // d_rowptr/d_col/d_val: the CSR arrays in device memory (the caller's, or staged copies)
 int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col, const void* d_val, int sigma,
-               int bulk_f32, OpDev& op, int* d_flags, cudaStream_t st) {
+               int bulk, OpDev& op, int* d_flags, cudaStream_t st) {
   SellPlanHost p;
   int rc = plan(A, sigma, p);
   if (rc != LYAP_OK) return rc;
@@ -135,25 +144,19 @@ int sell_build(const lyap_csr* A, const int64_t* d_rowptr, const int32_t* d_col,
   const int64_t threads = op.nslices * LYAP_SLICE;
   const int bs = 256;
   const int64_t grid = (threads + bs - 1) / bs;
+#define LYAP_FILL(TIN, TOUT)                                                                                     \
+  k_sell_fill<TIN, TOUT><<<(unsigned)grid, bs, 0, st>>>(A->n, op.nslices, d_rowptr, d_col, (const TIN*)d_val, op.perm, \
+                                                     op.slice_ptr, op.slice_w, op.sell_col, (TOUT*)op.sell_val, d_flags)
+  // stored type: fp64 (fp64 bulk), fp32 (fp32 bulk, and float-pair bulk with fp32 input values), pairs
   if (A->val_dtype == LYAP_F64) {
-    if (bulk_f32)
-      k_sell_fill<double, float><<<(unsigned)grid, bs, 0, st>>>(A->n, op.nslices, d_rowptr, d_col, (const double*)d_val,
-                                                                op.perm, op.slice_ptr, op.slice_w, op.sell_col,
-                                                                (float*)op.sell_val, d_flags);
-    else
-      k_sell_fill<double, double><<<(unsigned)grid, bs, 0, st>>>(A->n, op.nslices, d_rowptr, d_col, (const double*)d_val,
-                                                                 op.perm, op.slice_ptr, op.slice_w, op.sell_col,
-                                                                 (double*)op.sell_val, d_flags);
+    if (bulk == LYAP_PREC_MIXED) LYAP_FILL(double, float);
+    else if (bulk == LYAP_PREC_F32X2) LYAP_FILL(double, float2);
+    else LYAP_FILL(double, double);
   } else {
-    if (bulk_f32)
-      k_sell_fill<float, float><<<(unsigned)grid, bs, 0, st>>>(A->n, op.nslices, d_rowptr, d_col, (const float*)d_val,
-                                                               op.perm, op.slice_ptr, op.slice_w, op.sell_col,
-                                                               (float*)op.sell_val, d_flags);
-    else
-      k_sell_fill<float, double><<<(unsigned)grid, bs, 0, st>>>(A->n, op.nslices, d_rowptr, d_col, (const float*)d_val,
-                                                                op.perm, op.slice_ptr, op.slice_w, op.sell_col,
-                                                                (double*)op.sell_val, d_flags);
+    if (bulk == LYAP_PREC_F64) LYAP_FILL(float, double);
+    else LYAP_FILL(float, float);
   }
+#undef LYAP_FILL
   LYAP_CUDA_TRY(cudaGetLastError());
   // the host vectors must outlive the async copies
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));

@@ -13,6 +13,10 @@ def csr_arrays(A):
             np.ascontiguousarray(A.data, dtype=np.float64))
 
 
+# bulk number type of a solve: fp64, fp32 ("mixed": fp32 basis, float-pair sums), float pairs
+PRECISIONS = {"f64": L.LYAP_PREC_F64, "mixed": L.LYAP_PREC_MIXED, "f32x2": L.LYAP_PREC_F32X2}
+
+
 class Solver:
     """One Lyapunov (B is None) or Sylvester solve through lyap_create/solve/factor.
 
@@ -20,9 +24,9 @@ class Solver:
     ``inputs="host"`` hands host pointers to lyap_create, which copies them.
     """
 
-    def __init__(self, A, C1, B=None, C2=None, *, tol=1e-8, maxit=1000, check_every=1, trunc_eps=1e-12,
+    def __init__(self, A, C1, B=None, C2=None, *, tol=1e-8, maxit=1000, check_every=1, trunc_eps=0.0,
                  precision="f64", sell_sigma=1, pass2_blocks=16, check_batch=32, zcap=0, inputs="device",
-                 device="cuda:0", val_dtype="f64", fused_steps=0):
+                 device="cuda:0", val_dtype="f64"):
         import torch
 
         self.torch = torch
@@ -31,7 +35,7 @@ class Solver:
         self.s = int(C1.shape[1])
         self.n1 = int(A.shape[0])
         self.n2 = int(B.shape[0]) if self.sylv else self.n1
-        self.precision = L.LYAP_PREC_MIXED if precision == "mixed" else L.LYAP_PREC_F64
+        self.precision = PRECISIONS[precision]
         self.maxit = int(maxit)
         opt = L.lyap_default_options()
         opt.maxit = int(maxit)
@@ -41,7 +45,6 @@ class Solver:
         opt.sell_sigma = int(sell_sigma)
         opt.pass2_blocks = int(pass2_blocks)
         opt.check_batch = int(check_batch)
-        opt.fused_steps = int(fused_steps)
         # host output of the factor is staged in the workspace; by default size it for any rank
         opt.zcap = int(zcap) if zcap else (self.s * int(maxit) if inputs == "host" else 0)
         self.opt = opt
@@ -161,7 +164,7 @@ class Batch:
         self.device = torch.device(device)
         self.count = len(problems)
         self.maxit = int(maxit)
-        self.precision = L.LYAP_PREC_MIXED if precision == "mixed" else L.LYAP_PREC_F64
+        self.precision = PRECISIONS[precision]
         opt = L.lyap_default_options()
         opt.maxit = self.maxit
         opt.precision = self.precision

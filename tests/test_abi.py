@@ -41,7 +41,8 @@ def test_status_strings_and_defaults(lib):
     assert _lib.status_string(0) == "ok"
     assert "breakdown" in _lib.status_string(_lib.LYAP_ERR_BREAKDOWN).lower()
     o = _lib.lyap_default_options()
-    assert o.maxit == 1000 and o.check_every == 1 and o.trunc_eps == 1e-12 and o.pass2_blocks == 16
+    assert o.maxit == 1000 and o.check_every == 1 and o.trunc_eps == 0.0 and o.pass2_blocks == 16
+    assert o.precision == _lib.LYAP_PREC_F64 and _lib.LYAP_PREC_F32X2 == 2
 
 
 def _host_csr(A, keep):

@@ -6,7 +6,7 @@ Three levels, each with its own tolerance:
     tau_{m+1,m} (exported by lyap_projected_matrix), at every m.  Both evaluate
     the same function of the same fp64 data, so
         |rel_gpu(m) - rel_oracle(T_gpu)(m)| <= 1e-10 rel + HIST_ATOL.
-  * the block Lanczos recurrence: T_m from the GPU (fused MGS + CholQR2) against
+  * the block Lanczos recurrence: T_m from the GPU (projections and Cholesky QR from one reduction) against
     T_m from the oracle (textbook MGS + Householder QR) while local
     orthogonality keeps them close: |dT| <= 1e-11 ||T||.
   * the whole run: the residual histories and iteration counts of the two

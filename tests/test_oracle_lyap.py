@@ -313,3 +313,26 @@ def test_planted_mistake_in_recurrence_is_caught(small_problem, monkeypatch):
     monkeypatch.setattr(lyap, "lanczos_step", orig)
     Vm = np.hstack(bad.log.basis[:8])
     assert np.linalg.norm(Vm.T @ A @ Vm - lyap.dense_T(bad.log, 8)) > 1e-6 * np.linalg.norm(A, 2)
+
+
+def test_truncation_threshold_tied_to_tol():
+    """Reading of eq. 2.5 (eps tied to the residual target): with eps = 1e-12 (the paper's value
+    at ||C|| = 1, tol 1e-6) the truncation alone leaves an explicit residual far above a tol of
+    1e-10 on these Laplacians (||A|| ~ 1e4); with eps = min(1e-12, tol / (20 ||T_m||)) the
+    explicit residual of the factor equals the cheap residual to 1%, which the residual bound
+    2 ||A|| eps <= tol / 10 predicts."""
+    for k, s in ((40, 2), (30, 1), (24, 3)):
+        A = wl.laplacian_2d(k)
+        C = wl.rhs(A.shape[0], s, 3)
+        res = lyap.solve(A, C, tol=1e-10, maxit=400)
+        b2 = np.linalg.norm(C) ** 2
+        Z12, _ = lyap.factor(A, C, res, trunc_eps=1e-12)
+        Za, _ = lyap.factor(A, C, res)
+        r12 = explicit.lyap_lowrank(A, Z12, C) / b2
+        ra = explicit.lyap_lowrank(A, Za, C) / b2
+        assert r12 > 10 * res.history[-1]
+        assert abs(ra - res.history[-1]) <= 1e-2 * res.history[-1]
+        assert Za.shape[1] > Z12.shape[1]
+        lam, _ = lyap.eig_T(res.log, res.m)
+        assert lyap.auto_trunc_eps(1e-10, np.max(np.abs(lam))) == 1e-10 / (20 * np.max(np.abs(lam)))
+    assert lyap.auto_trunc_eps(1e-6, 1.0) == 1e-12  # the paper's eps where it is already small enough
