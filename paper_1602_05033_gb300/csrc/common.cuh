@@ -32,7 +32,6 @@ enum {
   REC_TDIAG,      // tau_{jj}   = alpha_j + beta_j (raw)
   REC_TPREV,      // tau_{j-1,j} = alpha_{j-1} + beta_{j-1} (raw)
   REC_CROSS,      // V_j^T V_{j-1} (rounding-level, used by the fused MGS algebra)
-  REC_GCC,        // V_j^T V_j as measured in step j (the fp32 basis uses it in step j + 1)
   LOG_NREC
 };
 

@@ -1,28 +1,23 @@
-// Block Lanczos step of one operator in two row sweeps with a single reduction (Alg. 2 with a
-// Cholesky QR normalisation; the recurrence of eq. 2.6), and the second pass of Sec. 3.3.
+// Block Lanczos step of one operator (Alg. 2: block MGS done twice, then a Cholesky QR done
+// twice), and the second pass of Sec. 3.3.  One step is four row sweeps, each followed by a
+// fixed-order reduction of per-CTA s x s sums done by the last CTA to finish:
 //
-//   A  W = A V_j (SELL-C-sigma SpMM); per-CTA sums of P = V_{j-1}^T W, Q = V_j^T W and W^T W
-//      (plus V_j^T V_{j-1} and V_j^T V_j for the fp32 basis); the last CTA to finish reduces the
-//      slots in a fixed order and forms
-//        alpha_{j-1} = P,  alpha_j = Q - (V_j^T V_{j-1}) alpha_{j-1}     (block MGS order, Alg. 2)
-//        G = (W - V_{j-1} alpha_{j-1} - V_j alpha_j)^T (...)  from the sums alone,
-//        tau_{j+1,j} = chol(G)  (upper triangular, positive diagonal),
-//      which it logs as tau_{j-1,j}, tau_jj and tau_{j+1,j}.
-//   B  V_{j+1} = (W - V_{j-1} tau_{j-1,j} - V_j tau_jj) tau_{j+1,j}^{-1}.
+//   S1  W = A V_j (SELL-C-sigma SpMM)         sums V_{j-1}^T W, V_j^T W, V_j^T V_{j-1}
+//       -> alpha_{j-1}, alpha_j (the first MGS sweep in fused form)
+//   S2  w1 = W - V_{j-1} alpha_{j-1} - V_j alpha_j   sums V_{j-1}^T w1, V_j^T w1, w1^T w1
+//       -> beta_{j-1}, beta_j (the second MGS sweep), R1 = chol(w2^T w2), w2 = w1 - V beta
+//   S3  x = w2 R1^{-1}                         sum x^T x -> R2 = chol(x^T x), tau_{j+1,j} = R2 R1
+//   S4  V_{j+1} = (W - V_{j-1} tau_{j-1,j} - V_j tau_jj) tau_{j+1,j}^{-1}
 //
-// In exact arithmetic this is Alg. 2: the two block MGS sweeps leave the same coefficients as
-// one projection on an orthonormal basis, and Cholesky QR with the Gram matrix of the projected
-// block gives the same tau_{j+1,j} as the QR factorisation.  The projected rows are formed once,
-// in sweep B, so a step reads the operator once and five blocks plus the re-read of W, V_j and
-// V_{j-1} in sweep B.  For the fp32 basis, whose vectors are orthonormal only to about eps32,
-// the coefficients use the measured Gram matrices of V_{j-1} and V_j (one Neumann step of their
-// inverses) and G accounts for them, which restores orthogonality to second order as the second
-// MGS sweep of Alg. 2 does.
+// Every Gram matrix is measured on the rows actually formed, so the step keeps CholQR2's
+// orthogonality even when the new block is ill-conditioned (block Lanczos near a converged
+// Ritz vector), which a Gram matrix formed from W^T W by cancellation does not.  The rows w1,
+// w2, x are recomputed from W, V_{j-1}, V_j in every sweep instead of being stored.
 //
 // Three bulk number types share the code: fp64; fp32 (per-thread fp32 sums, cross-CTA sums as
 // float pairs); and float pairs throughout (values, sums and row arithmetic on the fp32 pipe,
-// about 48 bits, see ff.cuh).  The second pass runs the same SpMM and row recipe from the logged
-// coefficients and therefore regenerates V_{j+1} bit for bit.
+// about 48 bits, see ff.cuh).  The second pass runs the same SpMM and the row recipe of S4 from
+// the logged coefficients and therefore regenerates V_{j+1} bit for bit.
 #include "common.cuh"
 #include "ff.cuh"
 
@@ -37,21 +32,19 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
 // ---- bulk number types ------------------------------------------------------------------
-// V: stored element; R: a value in registers; Acc: per-thread sum; kOblique: use the measured
-// Gram matrices of V_{j-1}, V_j; kUnroll: SELL entries gathered at once; kMinBlocks: CTAs per SM
+// V: stored element; R: a value in registers; Acc: per-thread sum; kUnroll: SELL entries
+// gathered at once; kMinBlocks: CTAs per SM
 struct NumD {
   using V = double;
   using R = double;
   using Acc = double;
-  static constexpr bool kOblique = false;
   static constexpr int kUnroll = 8;
-  static constexpr int kMinBlocks = 2;
+  static constexpr int kMinBlocks = 1;
 };
 struct NumF {
   using V = float;
   using R = float;
   using Acc = float;
-  static constexpr bool kOblique = true;
   static constexpr int kUnroll = 8;
   static constexpr int kMinBlocks = 2;
 };
@@ -59,7 +52,6 @@ struct NumFF {
   using V = float;  // a row of S pairs is 2S floats: the S high parts, then the S low parts
   using R = ff;
   using Acc = ff;
-  static constexpr bool kOblique = false;
   static constexpr int kUnroll = 4;
   static constexpr int kMinBlocks = 1;
 };
@@ -411,113 +403,6 @@ __device__ bool chol_up(const double* G, double* R) {
   return true;
 }
 
-// ---- the step's coefficients from the reduced sums (all threads of the last CTA) -----------
-// tot: P (S*S), Q (S*S), W^T W (upper triangle, row by row), and for the oblique form
-// X = V_j^T V_{j-1} (S*S) and V_j^T V_j (upper triangle)
-template <int S, bool OBL>
-__device__ void finalize(double* __restrict__ rec, const double* __restrict__ prev, const double* __restrict__ tot,
-                         bool hp, int* flags) {
-  constexpr int SS = S * S;
-  constexpr int NSYM = S * (S + 1) / 2;
-  __shared__ double sh[11][SS];
-  double *Gpp = sh[0], *Gcc = sh[1], *Xs = sh[2], *WW = sh[3], *ap = sh[4], *g = sh[5], *ac = sh[6], *Up = sh[7],
-         *Uc = sh[8], *Y = sh[9], *G = sh[10];
-  const double* P = tot;
-  const double* Q = tot + SS;
-  const double* WWp = tot + 2 * SS;
-  const double* Xp = tot + 2 * SS + NSYM;
-  const double* CCp = Xp + SS;
-  auto up = [](int a, int b) { return a * S - a * (a - 1) / 2 + (b - a); };  // packed upper index, a <= b
-  const int k = threadIdx.x;
-  const int a = k / S, b = k % S;
-  const bool act = k < SS;
-  if (act) {
-    const double id = a == b ? 1.0 : 0.0;
-    Gpp[k] = (OBL && hp) ? prev[REC_GCC * SS + k] : id;
-    Gcc[k] = OBL ? CCp[a <= b ? up(a, b) : up(b, a)] : id;
-    Xs[k] = (OBL && hp) ? Xp[k] : 0.0;
-    WW[k] = WWp[a <= b ? up(a, b) : up(b, a)];
-  }
-  __syncthreads();
-  if (act) {  // alpha_{j-1} = (2I - Gpp) P  (one Neumann step of Gpp^{-1})
-    double t = 0.0;
-    if (hp) {
-      if (OBL) {
-        for (int u = 0; u < S; ++u) t += ((a == u ? 2.0 : 0.0) - Gpp[a * S + u]) * P[u * S + b];
-      } else {
-        t = P[k];
-      }
-    }
-    ap[k] = t;
-  }
-  __syncthreads();
-  if (act) {  // g = Q - X alpha_{j-1}
-    double t = Q[k];
-    if (OBL)
-      for (int u = 0; u < S; ++u) t -= Xs[a * S + u] * ap[u * S + b];
-    g[k] = t;
-  }
-  __syncthreads();
-  if (act) {  // alpha_j = (2I - Gcc) g
-    double t = g[k];
-    if (OBL) {
-      t = 0.0;
-      for (int u = 0; u < S; ++u) t += ((a == u ? 2.0 : 0.0) - Gcc[a * S + u]) * g[u * S + b];
-    }
-    ac[k] = t;
-  }
-  __syncthreads();
-  if (act) {  // Gpp alpha_{j-1}, Gcc alpha_j, X^T alpha_j
-    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int u = 0; u < S; ++u) {
-      s1 += Gpp[a * S + u] * ap[u * S + b];
-      s2 += Gcc[a * S + u] * ac[u * S + b];
-      s3 += Xs[u * S + a] * ac[u * S + b];
-    }
-    Up[k] = s1;
-    Uc[k] = s2;
-    Y[k] = s3;
-  }
-  __syncthreads();
-  if (act) {
-    // G = w^T w for w = W - V_{j-1} ap - V_j ac, expanded in the reduced sums:
-    // W^T W - 2 sym(ap^T P) - 2 sym(ac^T Q) + ap^T Gpp ap + ac^T Gcc ac + 2 sym(ap^T X^T ac)
-    double t = WW[k];
-    for (int u = 0; u < S; ++u) {
-      t -= ap[u * S + a] * P[u * S + b] + ap[u * S + b] * P[u * S + a];
-      t -= ac[u * S + a] * Q[u * S + b] + ac[u * S + b] * Q[u * S + a];
-      t += ap[u * S + a] * Up[u * S + b] + ac[u * S + a] * Uc[u * S + b];
-      t += ap[u * S + a] * Y[u * S + b] + ap[u * S + b] * Y[u * S + a];
-    }
-    G[k] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double R[SS];
-    bool finite = true;
-    for (int e = 0; e < SS; ++e) finite = finite && isfinite(ap[e]) && isfinite(ac[e]) && isfinite(G[e]);
-    if (!finite) atomicOr(flags, DERR_NONFINITE);
-    if (!chol_up<S>(G, R)) {
-      if (finite) atomicOr(flags, DERR_BREAKDOWN);
-      for (int e = 0; e < SS; ++e) R[e] = (e % (S + 1) == 0) ? 1.0 : 0.0;
-    }
-    for (int e = 0; e < SS; ++e) {
-      const double id = e % (S + 1) == 0 ? 1.0 : 0.0;
-      rec[REC_APREV * SS + e] = ap[e];
-      rec[REC_ADIAG * SS + e] = ac[e];
-      rec[REC_BPREV * SS + e] = 0.0;
-      rec[REC_BDIAG * SS + e] = 0.0;
-      rec[REC_R1 * SS + e] = R[e];
-      rec[REC_R2 * SS + e] = id;
-      rec[REC_TNEXT * SS + e] = R[e];
-      rec[REC_TDIAG * SS + e] = ac[e];
-      rec[REC_TPREV * SS + e] = ap[e];
-      rec[REC_CROSS * SS + e] = Xs[e];
-      rec[REC_GCC * SS + e] = Gcc[e];
-    }
-  }
-}
-
 // ---- kernels -------------------------------------------------------------------------------
 struct StepArgs {
   OpDev op;
@@ -525,26 +410,87 @@ struct StepArgs {
   int has_prev;    // j > 1
   const void* Vp;  // V_{j-1}
   const void* Vc;  // V_j
-  void* Vn;        // V_{j+1} (sweep B, pass 2) or W (sweep A)
+  void* Vn;        // V_{j+1} (S4, pass 2) or W (S1)
   int64_t ldp, ldc, ldn;  // leading dimensions in values
   int* flags;
 };
 
-template <class Num, int S>
-constexpr int nacc() {
-  return Num::kOblique ? 3 * S * S + S * (S + 1) : 2 * S * S + S * (S + 1) / 2;
+// coefficients of the sweeps S2 and S3, converted to the row arithmetic's type
+template <typename R, int S>
+struct CoMid {
+  R ap[S][S], ac[S][S];  // S2: the first MGS sweep
+  R tp[S][S], td[S][S];  // S3: both MGS sweeps combined
+  R r1[S][S], r1i[S];    // S3: the first Cholesky QR factor and its reciprocal diagonal
+};
+
+template <typename R, int S>
+__device__ void load_mid(CoMid<R, S>& co, const double* __restrict__ rec, int stage) {
+  constexpr int SS = S * S;
+  for (int k = threadIdx.x; k < SS; k += blockDim.x) {
+    const int a = k / S, b = k % S;
+    if (stage == 2) {
+      co.ap[a][b] = coef<R>(rec[REC_APREV * SS + k]);
+      co.ac[a][b] = coef<R>(rec[REC_ADIAG * SS + k]);
+    } else {
+      co.tp[a][b] = coef<R>(rec[REC_TPREV * SS + k]);
+      co.td[a][b] = coef<R>(rec[REC_TDIAG * SS + k]);
+      co.r1[a][b] = coef<R>(rec[REC_R1 * SS + k]);
+    }
+  }
+  if (stage == 3)
+    for (int b = threadIdx.x; b < S; b += blockDim.x) co.r1i[b] = coef<R>(1.0 / rec[REC_R1 * SS + b * S + b]);
+  __syncthreads();
 }
 
-// sweep A: SpMM and the step's sums; CTA b owns a contiguous range of slices, so the rows its
-// warps gather from the same plane of the operator are often still in its L1
+// w -= p M1 + q M2 (rows times s x s blocks), M1 skipped without a previous block
+template <typename R, int S>
+__device__ __forceinline__ void project(const R (&p)[S], const R (&q)[S], const R (&M1)[S][S], const R (&M2)[S][S],
+                                        R (&w)[S], bool hp) {
+#pragma unroll
+  for (int b = 0; b < S; ++b) {
+    R t = w[b];
+    if (hp) {
+#pragma unroll
+      for (int a = 0; a < S; ++a) msub(t, p[a], M1[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < S; ++a) msub(t, q[a], M2[a][b]);
+    settle(t);
+    w[b] = t;
+  }
+}
+
+// one sweep's rows: W, V_j and V_{j-1} (zero without a previous block)
+template <class Num, int S>
+__device__ __forceinline__ void load3(const StepArgs& g, int64_t row, typename Num::R (&w)[S],
+                                      typename Num::R (&q)[S], typename Num::R (&p)[S]) {
+  using V = typename Num::V;
+  ld_row<S>(static_cast<const V*>(g.op.W), (int64_t)S, row, w);
+  ld_row<S>(static_cast<const V*>(g.Vc), g.ldc, row, q);
+  if (g.has_prev) ld_row<S>(static_cast<const V*>(g.Vp), g.ldp, row, p);
+  else {
+#pragma unroll
+    for (int a = 0; a < S; ++a) zero(p[a]);
+  }
+}
+
+__device__ __forceinline__ bool all_fin(const double* x, int n) {
+  bool f = true;
+  for (int i = 0; i < n; ++i) f = f && isfinite(x[i]);
+  return f;
+}
+
+// S1: W = A V_j (SELL SpMM) and the first block MGS projections of Alg. 2 in fused form:
+//   alpha_{j-1} = V_{j-1}^T W,  alpha_j = V_j^T W - (V_j^T V_{j-1}) alpha_{j-1}
+// (the same as projecting V_j out of W - V_{j-1} alpha_{j-1}).  CTA b owns a contiguous range of
+// slices, so rows its warps gather from the same plane of the operator are often still in its L1.
 template <class Num, typename AV, int S>
-__global__ void __launch_bounds__(kThreads, Num::kMinBlocks) k_step_a(StepArgs g) {
+__global__ void __launch_bounds__(kThreads, Num::kMinBlocks) k_s1(StepArgs g) {
   using V = typename Num::V;
   using R = typename Num::R;
   using Acc = typename Num::Acc;
   constexpr int SS = S * S;
-  constexpr int NSYM = S * (S + 1) / 2;
-  constexpr int NACC = nacc<Num, S>();
+  constexpr int NACC = 3 * SS;
   Acc acc[NACC];
 #pragma unroll
   for (int k = 0; k < NACC; ++k) zero(acc[k]);
@@ -574,54 +520,174 @@ __global__ void __launch_bounds__(kThreads, Num::kMinBlocks) k_step_a(StepArgs g
       for (int b = 0; b < S; ++b) {
         gram(acc[a * S + b], p[a], w[b]);
         gram(acc[SS + a * S + b], q[a], w[b]);
+        gram(acc[2 * SS + a * S + b], q[a], p[b]);
+      }
+  }
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  if (!reduce_step<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  const int k = threadIdx.x;
+  if (k < SS) {
+    const int a = k / S, b = k % S;
+    double ap = hp ? tot[k] : 0.0, t = tot[SS + k];
+    if (hp)
+      for (int u = 0; u < S; ++u) t -= tot[2 * SS + a * S + u] * tot[u * S + b];
+    rec[REC_APREV * SS + k] = ap;
+    rec[REC_ADIAG * SS + k] = t;
+    rec[REC_CROSS * SS + k] = hp ? tot[2 * SS + k] : 0.0;
+    if (!isfinite(ap) || !isfinite(t)) atomicOr(g.flags, DERR_NONFINITE);
+  }
+}
+
+// S2: w1 = W - V_{j-1} alpha_{j-1} - V_j alpha_j; the second MGS projections and G1 = w1^T w1 ->
+//   beta_{j-1} = V_{j-1}^T w1, beta_j = V_j^T w1 - (V_j^T V_{j-1}) beta_{j-1},
+//   tau_{j-1,j} = alpha_{j-1} + beta_{j-1}, tau_jj = alpha_j + beta_j,
+//   R1 = chol(G1 - beta^T beta)  (the Gram matrix of w2 = w1 - V beta)
+template <class Num, int S>
+__global__ void __launch_bounds__(kThreads, Num::kMinBlocks) k_s2(StepArgs g) {
+  using R = typename Num::R;
+  using Acc = typename Num::Acc;
+  constexpr int SS = S * S;
+  constexpr int NSYM = S * (S + 1) / 2;
+  constexpr int NACC = 2 * SS + NSYM;
+  __shared__ CoMid<R, S> co;
+  double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  load_mid<R, S>(co, rec, 2);
+  Acc acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) zero(acc[k]);
+  const bool hp = g.has_prev;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    R w[S], q[S], p[S];
+    load3<Num, S>(g, row, w, q, p);
+    project<R, S>(p, q, co.ap, co.ac, w, hp);
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int b = 0; b < S; ++b) {
+        gram(acc[a * S + b], p[a], w[b]);
+        gram(acc[SS + a * S + b], q[a], w[b]);
       }
     int e = 2 * SS;
 #pragma unroll
     for (int a = 0; a < S; ++a)
 #pragma unroll
       for (int b = a; b < S; ++b, ++e) gram(acc[e], w[a], w[b]);
-    if constexpr (Num::kOblique) {
-#pragma unroll
-      for (int a = 0; a < S; ++a)
-#pragma unroll
-        for (int b = 0; b < S; ++b) gram(acc[2 * SS + NSYM + a * S + b], q[a], p[b]);
-      int f = 3 * SS + NSYM;
-#pragma unroll
-      for (int a = 0; a < S; ++a)
-#pragma unroll
-        for (int b = a; b < S; ++b, ++f) gram(acc[f], q[a], q[b]);
-    }
   }
   __shared__ double tot[NACC];
   __shared__ double scratch[kWarps * NACC];
   if (!reduce_step<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
-  double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
-  finalize<S, Num::kOblique>(rec, rec - LOG_NREC * SS, tot, hp, g.flags);
+  __shared__ double bp[SS], bd[SS], G[SS];
+  const int k = threadIdx.x;
+  const int a = k / S, b = k % S;
+  if (k < SS) {
+    bp[k] = hp ? tot[k] : 0.0;
+    double t = tot[SS + k];
+    if (hp)
+      for (int u = 0; u < S; ++u) t -= rec[REC_CROSS * SS + a * S + u] * tot[u * S + b];
+    bd[k] = t;
+  }
+  __syncthreads();
+  if (k < SS) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    double v = tot[2 * SS + lo * S - lo * (lo - 1) / 2 + (hi - lo)];
+    for (int u = 0; u < S; ++u) v -= bp[u * S + a] * bp[u * S + b] + bd[u * S + a] * bd[u * S + b];
+    G[k] = v;
+    rec[REC_BPREV * SS + k] = bp[k];
+    rec[REC_BDIAG * SS + k] = bd[k];
+    rec[REC_TPREV * SS + k] = rec[REC_APREV * SS + k] + bp[k];
+    rec[REC_TDIAG * SS + k] = rec[REC_ADIAG * SS + k] + bd[k];
+  }
+  __syncthreads();
+  if (k == 0) {
+    double R1[SS];
+    const bool finite = all_fin(G, SS) && all_fin(bp, SS) && all_fin(bd, SS);
+    if (!finite) atomicOr(g.flags, DERR_NONFINITE);
+    if (!chol_up<S>(G, R1)) {
+      if (finite) atomicOr(g.flags, DERR_BREAKDOWN);
+      for (int e = 0; e < SS; ++e) R1[e] = (e % (S + 1) == 0) ? 1.0 : 0.0;
+    }
+    for (int e = 0; e < SS; ++e) rec[REC_R1 * SS + e] = R1[e];
+  }
 }
 
-// sweep B: V_{j+1}
+// S3: x = (W - V_{j-1} tau_{j-1,j} - V_j tau_jj) R1^{-1}; R2 = chol(x^T x), tau_{j+1,j} = R2 R1
+// (the second pass of Cholesky QR measures the Gram matrix of the rows actually formed)
 template <class Num, int S>
-__global__ void __launch_bounds__(kThreads) k_step_b(StepArgs g) {
+__global__ void __launch_bounds__(kThreads, Num::kMinBlocks) k_s3(StepArgs g) {
+  using R = typename Num::R;
+  using Acc = typename Num::Acc;
+  constexpr int SS = S * S;
+  constexpr int NSYM = S * (S + 1) / 2;
+  constexpr int NACC = NSYM;
+  __shared__ CoMid<R, S> co;
+  double* rec = g.op.log + (size_t)g.j * LOG_NREC * SS;
+  load_mid<R, S>(co, rec, 3);
+  Acc acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) zero(acc[k]);
+  const bool hp = g.has_prev;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    R w[S], q[S], p[S];
+    load3<Num, S>(g, row, w, q, p);
+    project<R, S>(p, q, co.tp, co.td, w, hp);
+#pragma unroll
+    for (int b = 0; b < S; ++b) {
+      R t = w[b];
+#pragma unroll
+      for (int a = 0; a < b; ++a) msub(t, w[a], co.r1[a][b]);
+      w[b] = mulc(t, co.r1i[b]);
+    }
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int b = a; b < S; ++b, ++e) gram(acc[e], w[a], w[b]);
+  }
+  __shared__ double tot[NACC];
+  __shared__ double scratch[kWarps * NACC];
+  if (!reduce_step<Acc, NACC>(acc, g.op.partials, g.op.counter, tot, scratch)) return;
+  if (threadIdx.x == 0) {
+    double G[SS], R2[SS], Tn[SS];
+    int e = 0;
+    for (int a = 0; a < S; ++a)
+      for (int b = a; b < S; ++b, ++e) G[a * S + b] = G[b * S + a] = tot[e];
+    if (!chol_up<S>(G, R2)) {
+      atomicOr(g.flags, all_fin(G, SS) ? DERR_BREAKDOWN : DERR_NONFINITE);
+      for (int f = 0; f < SS; ++f) R2[f] = (f % (S + 1) == 0) ? 1.0 : 0.0;
+    }
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b) {
+        double t = 0.0;
+        for (int u = 0; u < S; ++u) t += R2[a * S + u] * rec[REC_R1 * SS + u * S + b];
+        Tn[a * S + b] = t;
+      }
+    for (int f = 0; f < SS; ++f) {
+      rec[REC_R2 * SS + f] = R2[f];
+      rec[REC_TNEXT * SS + f] = Tn[f];
+    }
+    if (!all_fin(Tn, SS)) atomicOr(g.flags, DERR_NONFINITE);
+  }
+}
+
+// S4: V_{j+1} = (W - V_{j-1} tau_{j-1,j} - V_j tau_jj) tau_{j+1,j}^{-1}, the row recipe of the
+// second pass (both MGS sweeps and both Cholesky QR factors applied at once: eq. 2.6)
+template <class Num, int S>
+__global__ void __launch_bounds__(kThreads) k_s4(StepArgs g) {
   using V = typename Num::V;
   using R = typename Num::R;
   constexpr int SS = S * S;
   __shared__ Co<R, S> co;
   load_co<R, S>(co, g.op.log + (size_t)g.j * LOG_NREC * SS);
-  const V* Vp = static_cast<const V*>(g.Vp);
-  const V* Vc = static_cast<const V*>(g.Vc);
-  const V* W = static_cast<const V*>(g.op.W);
   V* Vn = static_cast<V*>(g.Vn);
   const bool hp = g.has_prev;
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < g.op.n;
        row += (int64_t)gridDim.x * blockDim.x) {
     R w[S], q[S], p[S];
-    ld_row<S>(W, (int64_t)S, row, w);
-    ld_row<S>(Vc, g.ldc, row, q);
-    if (hp) ld_row<S>(Vp, g.ldp, row, p);
-    else {
-#pragma unroll
-      for (int a = 0; a < S; ++a) zero(p[a]);
-    }
+    load3<Num, S>(g, row, w, q, p);
     recipe<R, S>(co, p, q, w, hp);
     st_row<S>(Vn, g.ldn, row, w);
   }
@@ -812,9 +878,11 @@ struct RunStep {
     g.flags = flags;
     g.Vn = op.W;
     g.ldn = S;
-    k_step_a<Num, AV, S><<<grid_a, kThreads, 0, st>>>(g);
+    k_s1<Num, AV, S><<<grid_a, kThreads, 0, st>>>(g);
+    k_s2<Num, S><<<grid_b, kThreads, 0, st>>>(g);
+    k_s3<Num, S><<<grid_b, kThreads, 0, st>>>(g);
     g.Vn = op.V[j % 3];  // V_{j+1}
-    k_step_b<Num, S><<<grid_b, kThreads, 0, st>>>(g);
+    k_s4<Num, S><<<grid_b, kThreads, 0, st>>>(g);
   }
 };
 
@@ -858,14 +926,17 @@ struct RunPass2 {
 template <class Num, typename AV, int S>
 struct Occ {
   static void run(int* a, int* b) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(a, k_step_a<Num, AV, S>, kThreads, 0) != cudaSuccess) *a = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k_step_b<Num, S>, kThreads, 0) != cudaSuccess) *b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(a, k_s1<Num, AV, S>, kThreads, 0) != cudaSuccess) *a = 1;
+    int b2 = 1, b3 = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_s2<Num, S>, kThreads, 0) != cudaSuccess) b2 = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, k_s3<Num, S>, kThreads, 0) != cudaSuccess) b3 = 1;
+    *b = b2 < b3 ? b2 : b3;
   }
 };
 
 }  // namespace
 
-int max_nacc(int s) { return 3 * s * s + s * (s + 1); }
+int max_nacc(int s) { return 3 * s * s; }
 
 int step_supported(int bulk, int s) {
   if (bulk == LYAP_PREC_F32X2) return s >= 1 && s <= 4;
@@ -887,7 +958,7 @@ int launch_init_block(OpDev& op, int s, int bulk, int grid, int* d_flags, cudaSt
 
 int launch_lanczos_step(OpDev& op, int s, int bulk, int grid_a, int grid_b, int j, int* d_flags, cudaStream_t st) {
   dispatch<RunStep>(bulk, op.val_pair, s, op, grid_a, grid_b, j, d_flags, st);
-  return 2;
+  return 4;
 }
 
 // Second pass, step j: writes V_{j+1} from V_{j-1} (vp), V_j (vc).
