@@ -6,17 +6,20 @@
 // at 1/64 of the fp32 rate, and a band reduction is a long chain of dependent
 // rotations that cannot use more than one SM; so for a batch of consecutive m
 // (one slot each) the kernels
-//   1. reduce a scaled copy of T_m to tridiagonal form in fp32 (pipelined Givens
-//      bulge chasing, one CTA per m) -- estimates only;
-//   2. bisect every eigenvalue of that tridiagonal in fp32 (Sturm counts), giving
-//      estimates accurate to a small multiple of eps32 ||T||;
+//   1. copy the band of T_m (fp64, and fp32 scaled by its largest entry) and find
+//      its Gershgorin interval;
+//   2. bisect every eigenvalue on the fp32 band itself (Sturm counts from an
+//      unpivoted LDL^T of T_m - x I, O(N s^2) each), giving estimates accurate to
+//      a few eps32 ||T||;
 //   3. refine every eigenpair in fp64 on the block-tridiagonal T_m itself:
-//      inverse iteration from the estimate, then Rayleigh-quotient shifts, with
-//      the banded LU (partial pivoting) of T_m - sigma I; estimates closer than
-//      the fp32 error bound form a cluster, iterated as a subspace and split by
-//      Rayleigh-Ritz so that its vectors stay orthonormal.  The full eigenvector
-//      is available, so its first and last s rows give a_i = (Q^T E_1 gamma)_i
-//      and w_i = (Q^T E_m tau^T)_i (Alg. 3 steps 3-5);
+//      estimates closer than the fp32 tolerance are first bisected again in fp64;
+//      then inverse iteration from the estimate (fp32 solves, then one fp64 step
+//      at the settled Rayleigh quotient, more only if the residual test asks),
+//      with the banded LU (partial pivoting) of T_m - sigma I; estimates still
+//      closer than the fp64 tolerance form a cluster, iterated as a subspace and
+//      split by Rayleigh-Ritz so that its vectors stay orthonormal.  The full
+//      eigenvector is available, so its first and last s rows give
+//      a_i = (Q^T E_1 gamma)_i and w_i = (Q^T E_m tau^T)_i (Alg. 3 steps 3-5);
 //   4. accumulate ||e_i^T S D_i^{-1} W||^2 per i (Alg. 3 steps 7-10);
 //   5. sum, take sqrt(2 sum)/beta^2 and record the history and the first converged m.
 // Every fp64 step runs one thread per eigenpair across the whole GPU.  Reductions
@@ -32,19 +35,14 @@
 
 namespace {
 
-constexpr int kBandThreads = 512;
-constexpr int kGroup = 8;    // lanes per concurrent Givens rotation
-constexpr int kDelta = 4;    // stage lag between consecutive sweeps (non-overlapping windows for b >= 2)
 constexpr int kMaxCluster = 16;
 constexpr int kClusterBlocks = 16;  // blocks per check of k_invit_clusters
 constexpr int kClusterWarps = 64;   // warps per check of k_invit_clusters (4 per block)
-// Members of a cluster of fp32 estimates larger than this (a spectrum far wider than its
-// smallest gaps, or near-duplicate Ritz values) get fp64 estimates by bisection with Sturm
-// counts on the fp64 band, and are then grouped at the fp64 tolerance.
-#ifndef LYAP_REFINE_AT
-#define LYAP_REFINE_AT 8
-#endif
-constexpr int kRefineAt = LYAP_REFINE_AT;
+// Members of every group of fp32 estimates closer than the fp32 tolerance get fp64 estimates
+// by bisection with Sturm counts on the fp64 band, and are then grouped at the fp64 tolerance:
+// any other estimate is farther from its neighbours than twice its error, so its nearest
+// eigenvalue is its own and the singleton iteration cannot produce a duplicate.
+constexpr int kRefineAt = 1;
 constexpr int kIters32 = 3;   // fp32 inverse iterations at the estimate before the fp64 ones
 constexpr int kRounds32 = 2;  // fp32 rounds of a cluster before its fp64 rounds
 constexpr int kMaxIters = 12; // fp64 inverse iterations (Rayleigh-quotient shifts) until converged
@@ -55,8 +53,7 @@ constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||
 struct Slot {
   double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] fp32 cluster
                  // tolerance, [6] fp64 cluster tolerance
-  float* d32;    // nmax
-  float* e32;    // nmax
+  float* Tb32;   // (s+1) x N   fp32 copy of the band of T_m / scale, Tb32[d*N + c] = T_m[c+d][c] / scale
   double* est;   // nmax   fp32 eigenvalue estimates (unscaled)
   double* lam;   // nmax   fp64 eigenvalues
   double* part;  // nmax
@@ -70,8 +67,8 @@ struct Slot {
   double* Xc;    // nmax x nmax, [i][k]: eigenvector i of a cluster member, contiguous
 };
 
-__host__ __device__ inline size_t slot_doubles(int s, int nmax) {
-  return 8 + (size_t)nmax /* d32+e32 */ + 3 * (size_t)nmax + (size_t)(s + 1) * nmax + 2 * (size_t)s * nmax +
+__host__ __device__ constexpr size_t slot_doubles(int s, int nmax) {
+  return 8 + ((size_t)(s + 1) * nmax + 1) / 2 /* Tb32 */ + 3 * (size_t)nmax + (size_t)(s + 1) * nmax + 2 * (size_t)s * nmax +
          ((size_t)nmax + 16) /* cluster list */ + (size_t)nmax * nmax + (size_t)(2 * s + 1) * nmax * nmax +
          (size_t)nmax /* etol */ + (size_t)nmax * nmax /* Xc */;
 }
@@ -80,9 +77,8 @@ __device__ inline Slot get_slot(double* base, int s, int nmax, int idx) {
   Slot sl;
   double* p = base + (size_t)idx * slot_doubles(s, nmax);
   sl.hdr = p; p += 8;
-  sl.d32 = reinterpret_cast<float*>(p);
-  sl.e32 = reinterpret_cast<float*>(p) + nmax;  // second half of the block of nmax doubles
-  p += nmax;
+  sl.Tb32 = reinterpret_cast<float*>(p);
+  p += ((size_t)(s + 1) * nmax + 1) / 2;
   sl.est = p; p += nmax;
   sl.lam = p; p += nmax;
   sl.part = p; p += nmax;
@@ -134,195 +130,131 @@ __device__ __forceinline__ double tband(const double* __restrict__ Tb, int N, in
   return d <= S ? __ldg(Tb + (size_t)d * N + (r < c ? r : c)) : 0.0;
 }
 
-// lower band (with one extra diagonal for the bulge) in shared memory
-template <typename R>
-__device__ inline R& TB(R* tb, int N, int i, int c) { return tb[(size_t)(i - c) * N + c]; }
-
-// Pipelined Givens reduction of the symmetric band (half-bandwidth b, lower band plus one bulge
-// diagonal in shared memory) to tridiagonal form: sweep k annihilates one sub-diagonal entry and
-// chases the bulge down in steps of b rows; consecutive sweeps run kDelta stages apart so their
-// windows never overlap, and kGroup lanes apply each rotation.
-template <typename R>
-__device__ void band_sweeps(R* tb, int N, int b) {
-  if (b >= 2 && N >= 3) {
-    const int lane = threadIdx.x & 31;
-    const int glane = lane & (kGroup - 1);
-    const int group = threadIdx.x / kGroup;
-    const int ngroups = blockDim.x / kGroup;
-    const int nsweeps = (N - 2) * (b - 1);
-    const int maxlen = (N + b - 1) / b + 1;
-    const long nstages = (long)kDelta * (nsweeps - 1) + maxlen + 1;
-    for (long st = 0; st < nstages; ++st) {
-      long lo = (st - maxlen) / kDelta;
-      if (lo < 0) lo = 0;
-      long hi = st / kDelta;
-      if (hi > nsweeps - 1) hi = nsweeps - 1;
-      for (long base = lo; base <= hi; base += ngroups) {
-        const long idx = base + group;
-        bool valid = idx <= hi;
-        int p = 0, kc = 0;
-        if (valid) {
-          const int k = (int)(idx / (b - 1));
-          const int d = b - (int)(idx % (b - 1));
-          const long t = st - (long)kDelta * idx;
-          if (t < 0) valid = false;
-          else if (t == 0) {
-            p = k + d - 1;
-            kc = k;
-            if (k + d > N - 1) valid = false;
-          } else {
-            p = k + d - 1 + (int)t * b;
-            kc = p - b;
-            if (p + 1 > N - 1) valid = false;
-          }
-        }
-        const int q = p + 1;
-        R cs = R(1), sn = R(0);
-        if (valid && glane == 0) {
-          const R x = TB(tb, N, p, kc);
-          const R y = TB(tb, N, q, kc);
-          const R r2 = x * x + y * y;
-          if (r2 > R(0)) {
-            // correctly rounded sqrt and divisions: the rotation stays orthogonal to
-            // ~1 ulp, which the estimates' accuracy depends on
-            const R r = sqrt(r2);
-            cs = x / r;
-            sn = y / r;
-            TB(tb, N, p, kc) = r;
-            TB(tb, N, q, kc) = R(0);
-          }
-        }
-        const int src = lane & ~(kGroup - 1);
-        cs = __shfl_sync(0xffffffffu, cs, src);
-        sn = __shfl_sync(0xffffffffu, sn, src);
-        if (valid && sn != R(0)) {
-          // items: columns kc+1..p-1, the 2x2 block, rows q+1..min(N-1, p+b+1)
-          const int ncols = p - kc - 1;
-          const int rlast = min(N - 1, p + b + 1);
-          const int nbelow = rlast - q > 0 ? rlast - q : 0;
-          const int nitems = ncols + 1 + nbelow;
-          for (int it = glane; it < nitems; it += kGroup) {
-            if (it < ncols) {
-              const int j = kc + 1 + it;
-              R& u = TB(tb, N, p, j);
-              R& v = TB(tb, N, q, j);
-              const R uu = u, vv = v;
-              u = cs * uu + sn * vv;
-              v = -sn * uu + cs * vv;
-            } else if (it == ncols) {
-              R& app = TB(tb, N, p, p);
-              R& aqp = TB(tb, N, q, p);
-              R& aqq = TB(tb, N, q, q);
-              const R A = app, B = aqp, D = aqq;
-              const R r0 = cs * A + sn * B, r1 = cs * B + sn * D;
-              const R s0 = -sn * A + cs * B, s1 = -sn * B + cs * D;
-              app = cs * r0 + sn * r1;
-              aqp = cs * s0 + sn * s1;
-              aqq = -sn * s0 + cs * s1;
-            } else {
-              const int i = q + 1 + (it - ncols - 1);
-              R& u = TB(tb, N, i, p);
-              R& v = TB(tb, N, i, q);
-              const R uu = u, vv = v;
-              u = cs * uu + sn * vv;
-              v = -sn * uu + cs * vv;
-            }
-          }
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// 1. fp32 tridiagonalisation of T_m / scale (estimates only)
-__global__ void __launch_bounds__(kBandThreads) k_band32(CheckArgs g) {
-  extern __shared__ float smemf[];
-  __shared__ float red[kBandThreads / 32];
+// 1. per check: the fp64 band of T_m and an fp32 copy scaled by its largest entry, the Gershgorin
+// interval of T_m / scale and the fp32 grouping tolerance
+__global__ void __launch_bounds__(256) k_setup_band(CheckArgs g) {
+  __shared__ double red[3][8];
   const int c_idx = blockIdx.x;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
-  const int s = g.s, b = s, N = s * m;
+  const int s = g.s, N = s * m;
   Slot sl = get_slot(g.slots, s, g.nmax, c_idx);
-  float* tb = smemf;  // (b + 2) x N
-  // scale = max |T_ij| over the band
-  float mx = 0.f;
-  for (int t = threadIdx.x; t < (b + 1) * N; t += blockDim.x) {
-    const int dd = t / N, c = t % N;
-    if (c + dd < N) mx = fmaxf(mx, (float)fabs(tval(g.log, s, c + dd, c)));
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  float scale = 0.f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) scale = fmaxf(scale, red[w]);
-  if (!(scale > 0.f)) scale = 1.f;
-  const double inv = 1.0 / (double)scale;
-  for (int t = threadIdx.x; t < (b + 2) * N; t += blockDim.x) {
-    const int dd = t / N, c = t % N;
-    const double v = (dd <= b && c + dd < N) ? tval(g.log, s, c + dd, c) : 0.0;
-    tb[t] = (float)(v * inv);
-    if (dd <= b) sl.Tb[t] = v;
+  double mx = 0.0, lo = INFINITY, hi = -INFINITY;
+  for (int t = threadIdx.x; t < (s + 1) * N; t += blockDim.x) {
+    const int d = t / N, c = t % N;
+    const double v = c + d < N ? tval(g.log, s, c + d, c) : 0.0;
+    sl.Tb[t] = v;
+    mx = fmax(mx, fabs(v));
   }
   __syncthreads();
-  band_sweeps<float>(tb, N, b);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    sl.d32[i] = TB(tb, N, i, i);
-    sl.e32[i] = (i + 1 < N) ? TB(tb, N, i + 1, i) : 0.f;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float lo = INFINITY, hi = -INFINITY, emax = 0.f;
-    for (int i = 0; i < N; ++i) {
-      const float r = (i > 0 ? fabsf(sl.e32[i - 1]) : 0.f) + (i + 1 < N ? fabsf(sl.e32[i]) : 0.f);
-      lo = fminf(lo, sl.d32[i] - r);
-      hi = fmaxf(hi, sl.d32[i] + r);
-      emax = fmaxf(emax, sl.e32[i] * sl.e32[i]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {  // Gershgorin discs by rows
+    double r = 0.0;
+    for (int d = 1; d <= s; ++d) {
+      if (i + d < N) r += fabs(sl.Tb[(size_t)d * N + i]);
+      if (i - d >= 0) r += fabs(sl.Tb[(size_t)d * N + i - d]);
     }
-    const float span = fmaxf(fabsf(lo), fabsf(hi));
-    sl.hdr[0] = lo - 8.f * FLT_EPSILON * span;
-    sl.hdr[1] = hi + 8.f * FLT_EPSILON * span;
-    sl.hdr[2] = emax;
-    sl.hdr[3] = scale;
-    sl.clist[0] = 0;
-    // clusters: estimates closer than 8 sqrt(N) eps32 ||T||.  The fp32 reduction and
-    // bisection errors observed on the Laplacian workloads stay below 0.3 sqrt(N) eps32 ||T||;
-    // the acceptance tests below turn any larger error into a reported failure
-    sl.hdr[4] = 8.0 * sqrt((double)N) * FLT_EPSILON * (double)scale * (double)span;
+    lo = fmin(lo, sl.Tb[i] - r);
+    hi = fmax(hi, sl.Tb[i] + r);
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = mx;
+    red[1][w] = lo;
+    red[2][w] = hi;
+  }
+  __syncthreads();
+  __shared__ double sc;
+  if (threadIdx.x == 0) {
+    double a = 0.0, l = INFINITY, h = -INFINITY;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a = fmax(a, red[0][k]);
+      l = fmin(l, red[1][k]);
+      h = fmax(h, red[2][k]);
+    }
+    if (!(a > 0.0)) a = 1.0;
+    const double span = fmax(fabs(l), fabs(h)) / a;
+    sl.hdr[0] = l / a - 8.0 * FLT_EPSILON * span;
+    sl.hdr[1] = h / a + 8.0 * FLT_EPSILON * span;
+    sl.hdr[2] = 0.0;
+    sl.hdr[3] = a;
+    // estimates closer than this form a group refined in fp64 (Sturm counts of the fp32 band
+    // carry an error of a few eps32 ||T||; the tolerance keeps a wide margin over it)
+    sl.hdr[4] = 2.4 * sqrt((double)N) * FLT_EPSILON * a * span;
+    sl.clist[0] = 0;
+    sc = 1.0 / a;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < (s + 1) * N; t += blockDim.x) sl.Tb32[t] = (float)(sl.Tb[t] * sc);
 }
 
-// 2. fp32 bisection, one thread per eigenvalue index
-__global__ void k_bisect32(CheckArgs g) {
+// Number of eigenvalues of the fp32 band below x: inertia of the unpivoted LDL^T of T - x I, a
+// tiny pivot replaced by -pivmin (the fp32 counterpart of band_sturm below)
+template <int S>
+__device__ int band_sturm32(const float* __restrict__ Tb, int N, float x, float pivmin) {
+  float dinv[S], L[S][S];
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    dinv[r] = 0.f;
+#pragma unroll
+    for (int t = 0; t < S; ++t) L[r][t] = 0.f;
+  }
+  int cnt = 0;
+  for (int k = 0; k < N; ++k) {
+    float w[S], nl[S];
+#pragma unroll
+    for (int r = S - 1; r >= 0; --r) {
+      const int j = k - 1 - r;
+      float v = j >= 0 ? Tb[(size_t)(r + 1) * N + j] : 0.f;
+#pragma unroll
+      for (int q = S - 1; q > r; --q) v = fmaf(-w[q], L[r][q - r - 1], v);
+      w[r] = v;
+      nl[r] = v * dinv[r];
+    }
+    float dk = Tb[k] - x;
+#pragma unroll
+    for (int r = 0; r < S; ++r) dk = fmaf(-nl[r], w[r], dk);
+    if (fabsf(dk) <= pivmin) dk = -pivmin;
+    cnt += dk < 0.f;
+#pragma unroll
+    for (int r = S - 1; r > 0; --r) {
+      dinv[r] = dinv[r - 1];
+#pragma unroll
+      for (int t = 0; t < S; ++t) L[r][t] = L[r - 1][t];
+    }
+    dinv[0] = 1.f / dk;
+#pragma unroll
+    for (int t = 0; t < S; ++t) L[0][t] = nl[t];
+  }
+  return cnt;
+}
+
+// 2. fp32 bisection of every eigenvalue on the band itself, one thread per eigenvalue index
+template <int S>
+__global__ void k_bisect_band32(CheckArgs g) {
   const int c_idx = blockIdx.y;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
-  const int N = g.s * m;
+  const int N = S * m;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
-  const float pivmin = FLT_MIN * fmaxf(1.f, (float)sl.hdr[2]);
+  Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   float lo = (float)sl.hdr[0], hi = (float)sl.hdr[1];
+  const float pivmin = 16.f * FLT_MIN;
   for (int it = 0; it < 64; ++it) {
     const float mid = 0.5f * (lo + hi);
     if (!(hi - lo > 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi))) || mid <= lo || mid >= hi) break;
-    int cnt = 0;
-    float q = sl.d32[0] - mid;
-    if (fabsf(q) <= pivmin) q = -pivmin;
-    cnt += q < 0.f;
-    for (int k = 1; k < N; ++k) {
-      q = (sl.d32[k] - mid) - sl.e32[k - 1] * sl.e32[k - 1] / q;
-      if (fabsf(q) <= pivmin) q = -pivmin;
-      cnt += q < 0.f;
-    }
-    if (cnt <= i) lo = mid;
+    if (band_sturm32<S>(sl.Tb32, N, mid, pivmin) <= i) lo = mid;
     else hi = mid;
   }
   sl.est[i] = 0.5 * ((double)lo + (double)hi) * sl.hdr[3];
 }
 
-// 2b. per-estimate cluster tolerance: members of fp32 clusters larger than kRefineAt get the
+// 2b. per-estimate cluster tolerance: members of fp32 groups larger than kRefineAt get the
 // fp64 grouping tolerance (and are refined by 2c), all others the fp32 one
 __global__ void k_mark_refine(CheckArgs g) {
   const int c_idx = blockIdx.x;
@@ -446,7 +378,8 @@ __device__ __forceinline__ double mval(const double* __restrict__ Tb, int N, dou
   return r == c ? v - sigma : v;
 }
 
-// X[:, col] <- (T_m - sigma I)^{-1} (xscale X[:, col]) by a banded LU with partial pivoting
+// X[:, col] <- (T_m - sigma I)^{-1} (xscale X[:, col]) by a banded LU with partial pivoting; returns
+// max_k |X[k, col]| of the result
 // (bandwidth S; U gets 2S+1 diagonals).  The active (S+1) x (2S+1) window, the pivot swaps
 // (predicated selects) and the back-substitution window live in registers: every index is a
 // compile-time constant.  U rows go to per-thread scratch ([k][e][tid] layout, coalesced).
@@ -454,8 +387,8 @@ __device__ __forceinline__ double mval(const double* __restrict__ Tb, int N, dou
 // formed in fp64 and then rounded, so the shift stays exact), fp64 to finish.  U points at the
 // double scratch reinterpreted as R.
 template <int S, typename R = double>
-__device__ void solve1(const double* __restrict__ Tb, int N, double sigma, R tiny, double xscale,
-                       double* __restrict__ X, size_t ld, int col, R* __restrict__ U, int tid, size_t ldu) {
+__device__ double solve1(const double* __restrict__ Tb, int N, double sigma, R tiny, double xscale,
+                         double* __restrict__ X, size_t ld, int col, R* __restrict__ U, int tid, size_t ldu) {
   constexpr int W = 2 * S + 1;
   // a thread's U entries are doubles at ((k W + e) ldu + tid); an fp32 solve stores its value in
   // the first half of the same double, so no thread ever touches another's scratch
@@ -515,6 +448,7 @@ __device__ void solve1(const double* __restrict__ Tb, int N, double sigma, R tin
     for (int c = 0; c < W; ++c) win[S][c] = (R)mval<S>(Tb, N, sigma, rn, k + 1 + c);
     yw[S] = rn < N ? (R)(X[(size_t)rn * ld + col] * xscale) : R(0);
   }
+  double amax = 0.0;
   R xs[W - 1];  // xs[e - 1] = x_{k+e}; entries beyond N stay 0 (so do their U coefficients)
 #pragma unroll
   for (int e = 0; e < W - 1; ++e) xs[e] = R(0);
@@ -530,10 +464,12 @@ __device__ void solve1(const double* __restrict__ Tb, int N, double sigma, R tin
     for (int e = 1; e < W; ++e) t = fma(-U[(((size_t)k * W + e) * ldu + tid) * us], xs[e - 1], t);
     const R xk = t / U[(((size_t)k * W) * ldu + tid) * us];
     X[(size_t)k * ld + col] = (double)xk;
+    amax = fmax(amax, fabs((double)xk));
 #pragma unroll
     for (int e = W - 2; e > 0; --e) xs[e] = xs[e - 1];
     xs[0] = xk;
   }
+  return amax;
 }
 
 // x^T T x and x^T x for column col in one pass (register window of 2S+1 entries of x)
@@ -658,8 +594,14 @@ __global__ void k_invit(CheckArgs g) {
     {
       float* U32 = reinterpret_cast<float*>(sl.U);
       const float tiny32 = FLT_EPSILON * (float)tnorm + FLT_MIN;
+      // between fp32 solves the iterate is scaled by its largest entry; only the last one gets
+      // its fp64 Rayleigh quotient
       for (int it = 0; it < kIters32 && warm; ++it) {
-        solve1<S, float>(sl.Tb, N, est, tiny32, xscale, sl.X, ld, i, U32, i, ld);
+        const double amax = solve1<S, float>(sl.Tb, N, est, tiny32, xscale, sl.X, ld, i, U32, i, ld);
+        warm = isfinite(amax) && amax > 0.0;
+        xscale = warm ? 1.0 / amax : 1.0;
+      }
+      if (warm) {
         double num, den;
         rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
         warm = isfinite(num) && isfinite(den) && den > 0.0;
@@ -674,26 +616,51 @@ __global__ void k_invit(CheckArgs g) {
       prev = rq;
       if (warm && !refined && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
     }
-    int extra = -1;  // iterations still to run after the Rayleigh quotient settled
-    for (int it = 0; it < kMaxIters; ++it) {
-      solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i, ld);
-      double num, den;
-      rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
-      rq = num / den;
-      xscale = 1.0 / sqrt(den);
-      if (extra == 0) break;
-      if (extra > 0) --extra;
-      // settled: one more Rayleigh-quotient step brings the vector to full precision (from a
-      // fresh start the first step cannot count as settled)
-      if (extra < 0 && (warm || it >= 1) && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
+    // fp64 steps.  From an iterate at fp32 accuracy whose Rayleigh quotient has settled, one
+    // inverse-iteration step at that shift (or at the fp64-refined estimate) brings the vector to
+    // fp64 accuracy (Rayleigh-quotient iteration converges cubically); the residual test below
+    // confirms it, and a pair that fails it gets the full iteration.
+    bool have_res = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const bool quick = attempt == 0 && warm;
+      int extra = -1;  // iterations still to run after the Rayleigh quotient settled
+      for (int it = 0; it < kMaxIters; ++it) {
+        solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i, ld);
+        double num, den;
+        rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
+        rq = num / den;
+        xscale = 1.0 / sqrt(den);
+        if (quick) break;
+        if (extra == 0) break;
+        if (extra > 0) --extra;
+        // settled: one more Rayleigh-quotient step brings the vector to full precision (from a
+        // fresh start the first step cannot count as settled)
+        if (extra < 0 && (warm || it >= 1) && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
+        prev = rq;
+        // Rayleigh-quotient shifts while the iterate is dominated by the wanted eigenvector; an
+        // fp64-refined estimate is already within a few eps ||T|| and stays the shift, so the
+        // iteration cannot drift to a neighbour closer than the fp32 tolerance
+        if (!refined && (warm || it >= 1) && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
+      }
+      if (!quick) break;
+      // the quick step: accept it if its residual passes, else iterate from where it is
+      double r2 = 0.0, rqq = 0.0;
+      for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
+      xscale = 1.0;
+      rayleigh(sl.Tb, S, N, sl.X, ld, i, &rqq, &r2);
+      if (r2 <= kResTol * tnorm && isfinite(rqq) && fabs(rqq - est) <= 0.5 * tolc) {
+        rq = rqq;
+        res = r2;
+        have_res = true;
+        break;
+      }
       prev = rq;
-      // Rayleigh-quotient shifts while the iterate is dominated by the wanted eigenvector; an
-      // fp64-refined estimate is already within a few eps ||T|| and stays the shift, so the
-      // iteration cannot drift to a neighbour closer than the fp32 tolerance
-      if (!refined && (warm || it >= 1) && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
+      if (!refined && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
     }
-    for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
-    rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
+    if (!have_res) {
+      for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
+      rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
+    }
     sl.lam[i] = rq;
     // the windows est +- tolc/2 of different groups are disjoint, so this also excludes
     // two singletons converging to the same eigenpair
@@ -1207,11 +1174,15 @@ CheckArgs make_args(lyap_handle* h, int opi, int m_lo, int nchk, int every, int 
 }
 
 int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
-  const size_t smem = (size_t)(g.s + 2) * nmax_batch * sizeof(float);
-  cudaFuncSetAttribute(k_band32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_band32<<<g.nchk, kBandThreads, smem, st>>>(g);
+  k_setup_band<<<g.nchk, 256, 0, st>>>(g);
   dim3 gv((nmax_batch + 31) / 32, g.nchk);
-  k_bisect32<<<gv, 32, 0, st>>>(g);
+  switch (g.s) {
+    case 1: k_bisect_band32<1><<<gv, 32, 0, st>>>(g); break;
+    case 2: k_bisect_band32<2><<<gv, 32, 0, st>>>(g); break;
+    case 3: k_bisect_band32<3><<<gv, 32, 0, st>>>(g); break;
+    case 4: k_bisect_band32<4><<<gv, 32, 0, st>>>(g); break;
+    case 8: k_bisect_band32<8><<<gv, 32, 0, st>>>(g); break;
+  }
   // fp64 estimates for the members of oversized fp32 clusters
   k_mark_refine<<<g.nchk, 256, 0, st>>>(g);
   switch (g.s) {
@@ -1295,7 +1266,7 @@ void check_slot0(lyap_handle* h, int opi, double** lam, double** a, double** w) 
   const size_t sd = slot_doubles(h->s, h->plan.nmax);
   double* p = reinterpret_cast<double*>(h->check_ws) + sd * (size_t)(opi * h->plan.check_batch);
   const int nmax = h->plan.nmax, s = h->s;
-  p += 8 + nmax;          // hdr, d32/e32
+  p += 8 + ((size_t)(s + 1) * nmax + 1) / 2;  // hdr, Tb32
   p += nmax;              // est
   *lam = p;
   p += 2 * (size_t)nmax;        // lam, part
@@ -1319,19 +1290,10 @@ namespace {
 
 constexpr int kNoAllocMaxS = 4;
 constexpr int kNoAllocMaxN = 256;  // s * m
-constexpr size_t kNoAllocSlot = 8 + 4 * (size_t)kNoAllocMaxN + (size_t)(kNoAllocMaxS + 1) * kNoAllocMaxN +
-                                2 * (size_t)kNoAllocMaxS * kNoAllocMaxN + ((size_t)kNoAllocMaxN + 16) +
-                                (size_t)(2 * kNoAllocMaxS + 3) * kNoAllocMaxN * kNoAllocMaxN + (size_t)kNoAllocMaxN;
+constexpr size_t kNoAllocSlot = slot_doubles(kNoAllocMaxS, kNoAllocMaxN);  // one check slot
 constexpr size_t kNoAllocLog = (size_t)(kNoAllocMaxN + 1) * LOG_NREC * kNoAllocMaxS * kNoAllocMaxS;
 constexpr size_t kNoAllocInts = 4 + kNoAllocMaxN;  // flags, per-m error bits
 constexpr size_t kNoAllocDoubles = kNoAllocSlot + kNoAllocLog + kNoAllocMaxN + (kNoAllocInts + 1) / 2;
-
-static_assert(kNoAllocSlot >= 8 + (size_t)kNoAllocMaxN + 3 * (size_t)kNoAllocMaxN +
-                                   (size_t)(kNoAllocMaxS + 1) * kNoAllocMaxN + 2 * (size_t)kNoAllocMaxS * kNoAllocMaxN +
-                                   ((size_t)kNoAllocMaxN + 16) + (size_t)kNoAllocMaxN * kNoAllocMaxN +
-                                   (size_t)(2 * kNoAllocMaxS + 1) * kNoAllocMaxN * kNoAllocMaxN +
-                                   (size_t)kNoAllocMaxN + (size_t)kNoAllocMaxN * kNoAllocMaxN,
-              "scratch slot must hold a check slot of the largest supported size");
 
 __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 

@@ -74,9 +74,10 @@ def test_batch_matches_single_solves_and_oracle(pkg, precision):
             # factor within the mixed tolerances of tests/test_gpu_precision.py
             assert abs(ms[i] - ref.m) <= 1
             k = min(len(h_b), len(ref.history))
-            dev = np.abs(h_b[:k] - ref.history[:k]) / ref.history[:k]
-            print(f"instance {i}: n={P.A.shape[0]} s={P.C1.shape[1]} max rel deviation from the oracle {dev.max():.3e}")
-            assert dev.max() <= 1e-2
+            d = np.abs(h_b[:k] - ref.history[:k])
+            print(f"instance {i}: n={P.A.shape[0]} s={P.C1.shape[1]} max rel deviation from the oracle "
+                  f"{np.max(d / ref.history[:k]):.3e}")
+            assert np.all(d <= 1e-2 * ref.history[:k] + 1e-9)
             assert _xprobe(Z, Zo) <= 1e-4
         one.close()
     bt.close()
