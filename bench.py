@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--paths", default="f32x2,mixed,f64",
                     help="precision paths timed on the n = 1e6 workload; the headline is the fastest one whose "
                          "returned factor has an explicit relative residual <= tol")
+    ap.add_argument("--profile-precision", choices=["f64", "mixed", "f32x2"], default="f32x2",
+                    help="bulk precision of the --profile-case solve")
     ap.add_argument("--profile-case", choices=["lanczos", "check", "sylv-check"], default=None,
                     help="run a short solve of the workload for a profiler and exit: 'lanczos' runs 6 block "
                          "Lanczos steps, 'check' 64 steps with their convergence checks (tol 0), 'sylv-check' "
@@ -668,7 +670,7 @@ def profile_case(args):
         return 0
     P = wl.config_c2(0, k=args.k)
     maxit = 6 if args.profile_case == "lanczos" else 64
-    sol = Solver(P.A, P.C1, tol=0.0, maxit=maxit, precision="mixed",
+    sol = Solver(P.A, P.C1, tol=0.0, maxit=maxit, precision=args.profile_precision, val_dtype="f32",
                  check_batch=8 if args.profile_case == "lanczos" else 32)
     sol.solve()
     torch.cuda.synchronize()

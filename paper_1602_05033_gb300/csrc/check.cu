@@ -39,9 +39,9 @@ constexpr int kMaxCluster = 16;
 constexpr int kClusterBlocks = 16;  // blocks per check of k_invit_clusters
 constexpr int kClusterWarps = 64;   // warps per check of k_invit_clusters (4 per block)
 // Members of every group of fp32 estimates closer than the fp32 tolerance get fp64 estimates
-// by bisection with Sturm counts on the fp64 band, and are then grouped at the fp64 tolerance:
-// any other estimate is farther from its neighbours than twice its error, so its nearest
-// eigenvalue is its own and the singleton iteration cannot produce a duplicate.
+// by multisection with Sturm counts on the fp64 band, and are then grouped at the fp64
+// tolerance: any other estimate is farther from its neighbours than twice its error, so its
+// nearest eigenvalue is its own and the singleton iteration cannot produce a duplicate.
 constexpr int kRefineAt = 1;
 constexpr int kIters32 = 3;   // fp32 inverse iterations at the estimate before the fp64 ones
 constexpr int kRounds32 = 2;  // fp32 rounds of a cluster before its fp64 rounds
@@ -182,9 +182,11 @@ __global__ void __launch_bounds__(256) k_setup_band(CheckArgs g) {
     sl.hdr[1] = h / a + 8.0 * FLT_EPSILON * span;
     sl.hdr[2] = 0.0;
     sl.hdr[3] = a;
-    // estimates closer than this form a group refined in fp64 (Sturm counts of the fp32 band
-    // carry an error of a few eps32 ||T||; the tolerance keeps a wide margin over it)
-    sl.hdr[4] = 2.4 * sqrt((double)N) * FLT_EPSILON * a * span;
+    // estimates closer than this form a group refined in fp64.  Sturm counts of the fp32 band
+    // leave errors up to about 20 eps32 ||T|| on the Laplacian workloads at N < 130; the
+    // tolerance keeps at least a factor two over that (the acceptance test of a singleton allows
+    // half of it)
+    sl.hdr[4] = 8.0 * sqrt((double)N) * FLT_EPSILON * a * span;
     sl.clist[0] = 0;
     sc = 1.0 / a;
   }
@@ -325,16 +327,20 @@ __device__ int band_sturm(const double* __restrict__ Tb, int N, double x, double
   return cnt;
 }
 
-// 2c. fp64 bisection of the marked estimates, one thread per eigenvalue index, started from the
-// fp32 estimate +- the fp32 cluster tolerance (widened to the Gershgorin interval if the counts
-// show the eigenvalue outside it), stopped at 2 eps64 ||T||
+// 2c. fp64 multisection of the marked estimates, one warp per eigenvalue index: the 32 lanes
+// count the eigenvalues below 32 interior points of the bracket at once (Sturm counts on the fp64
+// band), so a round narrows it 33-fold; started from the fp32 estimate +- the fp32 grouping
+// tolerance (widened to the Gershgorin interval if the counts show the eigenvalue outside it),
+// stopped at 2 eps64 ||T||.  The lanes share the fp64 pipe's issue slots, which a single thread
+// would leave idle.
 template <int S>
 __global__ void k_refine64(CheckArgs g) {
   const int c_idx = blockIdx.y;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
   const int N = S * m;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // one index per warp
   if (i >= N) return;
   Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   const double tol32 = sl.hdr[4];
@@ -343,16 +349,29 @@ __global__ void k_refine64(CheckArgs g) {
   const double glo = sl.hdr[0] * sc, ghi = sl.hdr[1] * sc;
   const double span = fmax(fabs(glo), fabs(ghi));
   const double pivmin = DBL_MIN * fmax(1.0, span * span);
+  const unsigned full = 0xffffffffu;
   double lo = sl.est[i] - tol32, hi = sl.est[i] + tol32;
-  if (band_sturm<S>(sl.Tb, N, lo, pivmin) > i) lo = glo;
-  if (band_sturm<S>(sl.Tb, N, hi, pivmin) <= i) hi = ghi;
-  for (int it = 0; it < 128; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (!(hi - lo > 2.0 * DBL_EPSILON * span) || mid <= lo || mid >= hi) break;
-    if (band_sturm<S>(sl.Tb, N, mid, pivmin) <= i) lo = mid;
-    else hi = mid;
+  {
+    const int c = lane < 2 ? band_sturm<S>(sl.Tb, N, lane == 0 ? lo : hi, pivmin) : 0;
+    const int clo = __shfl_sync(full, c, 0), chi = __shfl_sync(full, c, 1);
+    if (clo > i) lo = glo;
+    if (chi <= i) hi = ghi;
   }
-  sl.est[i] = 0.5 * (lo + hi);
+  for (int round = 0; round < 40; ++round) {
+    if (!(hi - lo > 2.0 * DBL_EPSILON * span)) break;
+    const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
+    const int c = band_sturm<S>(sl.Tb, N, x, pivmin);
+    // lambda_i >= x exactly when fewer than i + 1 eigenvalues lie below x
+    const unsigned below = __ballot_sync(full, c <= i);
+    const int top = below ? 31 - __clz(below) : -1;  // last point at or below lambda_i
+    const double nlo = __shfl_sync(full, x, top < 0 ? 0 : top);
+    const double nhi = __shfl_sync(full, x, top < 31 ? top + 1 : 31);
+    const double lo2 = top < 0 ? lo : nlo, hi2 = top < 31 ? nhi : hi;
+    if (!(hi2 - lo2 < hi - lo)) break;  // no progress at this resolution
+    lo = lo2;
+    hi = hi2;
+  }
+  if (lane == 0) sl.est[i] = 0.5 * (lo + hi);
 }
 
 __device__ inline double hash_unit(unsigned int k, unsigned int i) {
@@ -1185,12 +1204,13 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
   }
   // fp64 estimates for the members of oversized fp32 clusters
   k_mark_refine<<<g.nchk, 256, 0, st>>>(g);
+  dim3 gr((nmax_batch + 7) / 8, g.nchk);  // eight warps a block, one eigenvalue a warp
   switch (g.s) {
-    case 1: k_refine64<1><<<gv, 32, 0, st>>>(g); break;
-    case 2: k_refine64<2><<<gv, 32, 0, st>>>(g); break;
-    case 3: k_refine64<3><<<gv, 32, 0, st>>>(g); break;
-    case 4: k_refine64<4><<<gv, 32, 0, st>>>(g); break;
-    case 8: k_refine64<8><<<gv, 32, 0, st>>>(g); break;
+    case 1: k_refine64<1><<<gr, 256, 0, st>>>(g); break;
+    case 2: k_refine64<2><<<gr, 256, 0, st>>>(g); break;
+    case 3: k_refine64<3><<<gr, 256, 0, st>>>(g); break;
+    case 4: k_refine64<4><<<gr, 256, 0, st>>>(g); break;
+    case 8: k_refine64<8><<<gr, 256, 0, st>>>(g); break;
   }
   switch (g.s) {
     case 1: k_invit<1><<<gv, 32, 0, st>>>(g); break;
