@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(256) k_setup_band(CheckArgs g) {
   }
   __syncthreads();
   for (int t = threadIdx.x; t < (s + 1) * N; t += blockDim.x) sl.Tb32[t] = (float)(sl.Tb[t] * sc);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) sl.part[t] = 0.0;  // retry marks of k_invit
 }
 
 // Number of eigenvalues of the fp32 band below x: inertia of the unpivoted LDL^T of T - x I, a
@@ -334,7 +335,7 @@ __device__ int band_sturm(const double* __restrict__ Tb, int N, double x, double
 // stopped at 2 eps64 ||T||.  The lanes share the fp64 pipe's issue slots, which a single thread
 // would leave idle.
 template <int S>
-__global__ void k_refine64(CheckArgs g) {
+__global__ void k_refine64(CheckArgs g, int round) {
   const int c_idx = blockIdx.y;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
@@ -344,7 +345,8 @@ __global__ void k_refine64(CheckArgs g) {
   if (i >= N) return;
   Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   const double tol32 = sl.hdr[4];
-  if (!(sl.etol[i] < tol32)) return;
+  // round 0: members of fp32 groups; round 1: the singletons marked for a retry by k_invit
+  if (round == 0 ? !(sl.etol[i] < tol32) : sl.part[i] == 0.0) return;
   const double sc = sl.hdr[3];
   const double glo = sl.hdr[0] * sc, ghi = sl.hdr[1] * sc;
   const double span = fmax(fabs(glo), fabs(ghi));
@@ -580,7 +582,7 @@ __device__ void write_aw(const CheckArgs& g, Slot& sl, int m, int N, size_t ld, 
 // 3. fp64 eigenpairs by inverse / Rayleigh-quotient iteration, one thread per eigenvalue
 // (cluster leaders iterate their whole cluster as a subspace)
 template <int S>
-__global__ void k_invit(CheckArgs g) {
+__global__ void k_invit(CheckArgs g, int round) {
   const int c_idx = blockIdx.y;
   const int m = g.m_lo + c_idx;
   if (!checked(g, m)) return;
@@ -589,21 +591,32 @@ __global__ void k_invit(CheckArgs g) {
   if (i >= N) return;
   Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   const size_t ld = (size_t)g.nmax;
-  const double tolc = sl.etol[i];
+  // round 1 retries the singletons of round 0 whose iteration settled away from their fp32
+  // estimate (marked in part[]), now from fp64 estimates refined in between
+  const bool retry = round == 1;
+  if (retry && sl.part[i] == 0.0) return;
+  const double tolc = retry ? sl.hdr[6] : sl.etol[i];
   const double tnorm = sl.hdr[3] * fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
   const double tiny = DBL_EPSILON * tnorm + DBL_MIN;
-  // groups: consecutive estimates closer than the larger of their two tolerances
-  if (i > 0 && sl.est[i] - sl.est[i - 1] <= fmax(tolc, sl.etol[i - 1])) return;  // not a leader
   int c = 1;
-  while (i + c < N && sl.est[i + c] - sl.est[i + c - 1] <= fmax(sl.etol[i + c], sl.etol[i + c - 1])) ++c;
-  if (c > kMaxCluster) {
-    atomicOr(g.chk_err + m - 1, DERR_EIGEN);
-    c = kMaxCluster;
+  if (retry) {
+    if ((i > 0 && sl.est[i] - sl.est[i - 1] <= tolc) || (i + 1 < N && sl.est[i + 1] - sl.est[i] <= tolc)) {
+      atomicOr(g.chk_err + m - 1, DERR_EIGEN);
+      return;
+    }
+  } else {
+    // groups: consecutive estimates closer than the larger of their two tolerances
+    if (i > 0 && sl.est[i] - sl.est[i - 1] <= fmax(tolc, sl.etol[i - 1])) return;  // not a leader
+    while (i + c < N && sl.est[i + c] - sl.est[i + c - 1] <= fmax(sl.etol[i + c], sl.etol[i + c - 1])) ++c;
+    if (c > kMaxCluster) {
+      atomicOr(g.chk_err + m - 1, DERR_EIGEN);
+      c = kMaxCluster;
+    }
   }
   if (c == 1) {
     for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] = hash_unit((unsigned)k, (unsigned)i);
     const double est = sl.est[i];
-    const bool refined = tolc < sl.hdr[4];
+    const bool refined = retry || tolc < sl.hdr[4];
     double sigma = est, rq = est, res = 0.0, prev = est, xscale = 1.0;
     // fp32 inverse iterations at the estimate (fp32 rate, half the scratch traffic) bring the
     // vector to fp32 accuracy; fp64 Rayleigh-quotient steps then finish it in one or two solves
@@ -684,6 +697,10 @@ __global__ void k_invit(CheckArgs g) {
     // the windows est +- tolc/2 of different groups are disjoint, so this also excludes
     // two singletons converging to the same eigenpair
     if (!(res <= kResTol * tnorm) || !isfinite(rq) || fabs(rq - est) > 0.5 * tolc) {
+      if (!refined) {  // an fp32 estimate off by more than half the tolerance: retry in round 1
+        sl.part[i] = 1.0;
+        return;
+      }
       atomicOr(g.chk_err + m - 1, DERR_EIGEN);
 #ifdef LYAP_DEBUG
       printf("eig fail m=%d N=%d i=%d c=1 est=%.17g rq=%.17g res=%.3e tnorm=%.3e tolc=%.3e\n", m, N, i, est, rq, res,
@@ -1202,22 +1219,33 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
     case 4: k_bisect_band32<4><<<gv, 32, 0, st>>>(g); break;
     case 8: k_bisect_band32<8><<<gv, 32, 0, st>>>(g); break;
   }
-  // fp64 estimates for the members of oversized fp32 clusters
+  // fp64 estimates for the members of fp32 groups; the singleton iteration; fp64 estimates and a
+  // second iteration for the singletons whose fp32 estimate proved too far off
   k_mark_refine<<<g.nchk, 256, 0, st>>>(g);
   dim3 gr((nmax_batch + 7) / 8, g.nchk);  // eight warps a block, one eigenvalue a warp
-  switch (g.s) {
-    case 1: k_refine64<1><<<gr, 256, 0, st>>>(g); break;
-    case 2: k_refine64<2><<<gr, 256, 0, st>>>(g); break;
-    case 3: k_refine64<3><<<gr, 256, 0, st>>>(g); break;
-    case 4: k_refine64<4><<<gr, 256, 0, st>>>(g); break;
-    case 8: k_refine64<8><<<gr, 256, 0, st>>>(g); break;
+  for (int round = 0; round < 2; ++round) {
+    switch (g.s) {
+      case 1: k_refine64<1><<<gr, 256, 0, st>>>(g, round); break;
+      case 2: k_refine64<2><<<gr, 256, 0, st>>>(g, round); break;
+      case 3: k_refine64<3><<<gr, 256, 0, st>>>(g, round); break;
+      case 4: k_refine64<4><<<gr, 256, 0, st>>>(g, round); break;
+      case 8: k_refine64<8><<<gr, 256, 0, st>>>(g, round); break;
+    }
+    if (round == 1) break;
+    switch (g.s) {
+      case 1: k_invit<1><<<gv, 32, 0, st>>>(g, 0); break;
+      case 2: k_invit<2><<<gv, 32, 0, st>>>(g, 0); break;
+      case 3: k_invit<3><<<gv, 32, 0, st>>>(g, 0); break;
+      case 4: k_invit<4><<<gv, 32, 0, st>>>(g, 0); break;
+      case 8: k_invit<8><<<gv, 32, 0, st>>>(g, 0); break;
+    }
   }
   switch (g.s) {
-    case 1: k_invit<1><<<gv, 32, 0, st>>>(g); break;
-    case 2: k_invit<2><<<gv, 32, 0, st>>>(g); break;
-    case 3: k_invit<3><<<gv, 32, 0, st>>>(g); break;
-    case 4: k_invit<4><<<gv, 32, 0, st>>>(g); break;
-    case 8: k_invit<8><<<gv, 32, 0, st>>>(g); break;
+    case 1: k_invit<1><<<gv, 32, 0, st>>>(g, 1); break;
+    case 2: k_invit<2><<<gv, 32, 0, st>>>(g, 1); break;
+    case 3: k_invit<3><<<gv, 32, 0, st>>>(g, 1); break;
+    case 4: k_invit<4><<<gv, 32, 0, st>>>(g, 1); break;
+    case 8: k_invit<8><<<gv, 32, 0, st>>>(g, 1); break;
   }
   // groups: packed into warps of up to 32 members; 16 blocks of 4 warps per check take the packs
   // in turn (the SM count is read once: a process uses one GPU model)
@@ -1238,7 +1266,7 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
     case 4: k_invit_clusters<4><<<gc, 128, 0, st>>>(g); break;
     case 8: k_invit_clusters<8><<<gc, 128, 0, st>>>(g); break;
   }
-  return 7;
+  return 9;
 }
 
 }  // namespace
