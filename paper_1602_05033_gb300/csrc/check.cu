@@ -49,6 +49,10 @@ constexpr int kMaxIters = 12; // fp64 inverse iterations (Rayleigh-quotient shif
 constexpr int kMaxRounds = 10;  // cluster rounds (Rayleigh-Ritz between them); converged clusters stop early
 constexpr double kSettle = 1e-12;  // |change of the Rayleigh quotient| / ||T|| after which one more step is run
 constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||T||
+// residual at which the single fp64 step after the fp32 iterations is accepted: a settled
+// Rayleigh-quotient step leaves a residual of a few eps64 ||T||; anything larger means the fp32
+// iterations had not converged (a small gap), and the full iteration takes over
+constexpr double kQuickRes = 4e-14;
 
 struct Slot {
   double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] fp32 cluster
@@ -680,7 +684,7 @@ __global__ void k_invit(CheckArgs g, int round) {
       for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
       xscale = 1.0;
       rayleigh(sl.Tb, S, N, sl.X, ld, i, &rqq, &r2);
-      if (r2 <= kResTol * tnorm && isfinite(rqq) && fabs(rqq - est) <= 0.5 * tolc) {
+      if (r2 <= kQuickRes * tnorm && isfinite(rqq) && fabs(rqq - est) <= 0.5 * tolc) {
         rq = rqq;
         res = r2;
         have_res = true;
