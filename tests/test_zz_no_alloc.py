@@ -66,10 +66,10 @@ def test_noalloc_residual_matches_solve_history(env):
             assert int(status.item()) == L.LYAP_OK
             got = float(rel.item())
             ref = float(hist[m - 1])
-            assert abs(got - ref) <= 1e-10 * ref + 1e-15, (m, got, ref)
+            assert abs(got - ref) <= 1e-10 * ref + 1e-14, (m, got, ref)
             lam, Q = sla.eig_banded(ab, lower=True)
             ora = olyap.cheap_residual(lam, Q, gam, tau, s) / beta**2
-            assert abs(got - ora) <= 1e-10 * ora + 1e-15, (m, got, ora)
+            assert abs(got - ora) <= 1e-10 * ora + 1e-14, (m, got, ora)
     sol.close()
 
 
