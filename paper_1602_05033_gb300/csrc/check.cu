@@ -38,21 +38,28 @@ namespace {
 constexpr int kMaxCluster = 16;
 constexpr int kClusterBlocks = 16;  // blocks per check of k_invit_clusters
 constexpr int kClusterWarps = 64;   // warps per check of k_invit_clusters (4 per block)
-// Members of every group of fp32 estimates closer than the fp32 tolerance get fp64 estimates
-// by multisection with Sturm counts on the fp64 band, and are then grouped at the fp64
-// tolerance: any other estimate is farther from its neighbours than twice its error, so its
-// nearest eigenvalue is its own and the singleton iteration cannot produce a duplicate.
-constexpr int kRefineAt = 1;
+// Members of a group of fp32 estimates larger than this get fp64 estimates by multisection with
+// Sturm counts on the fp64 band, and are then regrouped at the fp64 tolerance below (1: every
+// group).  Estimates that stay farther apart than that tolerance are iterated one by one with
+// their fp64 estimate as a fixed shift; closer ones as a subspace (k_invit_clusters), which keeps
+// the vectors of close eigenvalues orthonormal: a single vector's error is its residual over the
+// gap to its neighbour.  On the 2D Laplacian tests the subspace path for pairs closer than
+// 1e-6 ||T|| keeps every history within a fifth of the 1e-10 bound; at 1e-9 ||T|| the errors of
+// close singletons reached 2.6 times it.
+#ifndef LYAP_REFINE_AT
+#define LYAP_REFINE_AT 1
+#endif
+constexpr int kRefineAt = LYAP_REFINE_AT;
+#ifndef LYAP_TOL64_FLOOR
+#define LYAP_TOL64_FLOOR 1e-6
+#endif
+constexpr double kTol64Floor = LYAP_TOL64_FLOOR;
 constexpr int kIters32 = 3;   // fp32 inverse iterations at the estimate before the fp64 ones
 constexpr int kRounds32 = 2;  // fp32 rounds of a cluster before its fp64 rounds
 constexpr int kMaxIters = 12; // fp64 inverse iterations (Rayleigh-quotient shifts) until converged
 constexpr int kMaxRounds = 10;  // cluster rounds (Rayleigh-Ritz between them); converged clusters stop early
 constexpr double kSettle = 1e-12;  // |change of the Rayleigh quotient| / ||T|| after which one more step is run
 constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||T||
-// residual at which the single fp64 step after the fp32 iterations is accepted: a settled
-// Rayleigh-quotient step leaves a residual of a few eps64 ||T||; anything larger means the fp32
-// iterations had not converged (a small gap), and the full iteration takes over
-constexpr double kQuickRes = 4e-14;
 
 struct Slot {
   double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] fp32 cluster
@@ -272,11 +279,11 @@ __global__ void k_mark_refine(CheckArgs g) {
   const double tol32 = sl.hdr[4];
   const double span = fmax(fabs(sl.hdr[0]), fabs(sl.hdr[1]));
   // refined estimates are accurate to a few eps64 ||T||, so a refined singleton converges to its
-  // own eigenvalue within a few steps whenever its neighbours are more than 1e-9 ||T|| away; closer
-  // ones (near-duplicate Ritz values of the finite-precision recurrence reach 1e-10 ||T||) are
-  // grouped and resolved together
+  // own eigenvalue whenever its neighbours are farther than the fp64 tolerance; closer ones
+  // (near-duplicate Ritz values of the finite-precision recurrence reach 1e-10 ||T||) are grouped
+  // and resolved together
   const double tnorm = sl.hdr[3] * span;
-  const double tol64 = fmax(8.0 * sqrt((double)N) * DBL_EPSILON * tnorm, 1e-9 * tnorm);
+  const double tol64 = fmax(8.0 * sqrt((double)N) * DBL_EPSILON * tnorm, kTol64Floor * tnorm);
   if (threadIdx.x == 0) sl.hdr[6] = tol64;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     if (i > 0 && sl.est[i] - sl.est[i - 1] <= tol32) continue;
@@ -652,51 +659,26 @@ __global__ void k_invit(CheckArgs g, int round) {
       prev = rq;
       if (warm && !refined && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
     }
-    // fp64 steps.  From an iterate at fp32 accuracy whose Rayleigh quotient has settled, one
-    // inverse-iteration step at that shift (or at the fp64-refined estimate) brings the vector to
-    // fp64 accuracy (Rayleigh-quotient iteration converges cubically); the residual test below
-    // confirms it, and a pair that fails it gets the full iteration.
-    bool have_res = false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      const bool quick = attempt == 0 && warm;
-      int extra = -1;  // iterations still to run after the Rayleigh quotient settled
-      for (int it = 0; it < kMaxIters; ++it) {
-        solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i, ld);
-        double num, den;
-        rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
-        rq = num / den;
-        xscale = 1.0 / sqrt(den);
-        if (quick) break;
-        if (extra == 0) break;
-        if (extra > 0) --extra;
-        // settled: one more Rayleigh-quotient step brings the vector to full precision (from a
-        // fresh start the first step cannot count as settled)
-        if (extra < 0 && (warm || it >= 1) && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
-        prev = rq;
-        // Rayleigh-quotient shifts while the iterate is dominated by the wanted eigenvector; an
-        // fp64-refined estimate is already within a few eps ||T|| and stays the shift, so the
-        // iteration cannot drift to a neighbour closer than the fp32 tolerance
-        if (!refined && (warm || it >= 1) && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
-      }
-      if (!quick) break;
-      // the quick step: accept it if its residual passes, else iterate from where it is
-      double r2 = 0.0, rqq = 0.0;
-      for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
-      xscale = 1.0;
-      rayleigh(sl.Tb, S, N, sl.X, ld, i, &rqq, &r2);
-      if (r2 <= kQuickRes * tnorm && isfinite(rqq) && fabs(rqq - est) <= 0.5 * tolc) {
-        rq = rqq;
-        res = r2;
-        have_res = true;
-        break;
-      }
+    int extra = -1;  // iterations still to run after the Rayleigh quotient settled
+    for (int it = 0; it < kMaxIters; ++it) {
+      solve1<S>(sl.Tb, N, sigma, tiny, xscale, sl.X, ld, i, sl.U, i, ld);
+      double num, den;
+      rq_pass<S>(sl.Tb, N, sl.X, ld, i, &num, &den);
+      rq = num / den;
+      xscale = 1.0 / sqrt(den);
+      if (extra == 0) break;
+      if (extra > 0) --extra;
+      // settled: one more Rayleigh-quotient step brings the vector to full precision (from a
+      // fresh start the first step cannot count as settled)
+      if (extra < 0 && (warm || it >= 1) && fabs(rq - prev) <= kSettle * tnorm) extra = 0;
       prev = rq;
-      if (!refined && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
+      // Rayleigh-quotient shifts while the iterate is dominated by the wanted eigenvector; an
+      // fp64-refined estimate is already within a few eps ||T|| and stays the shift, so the
+      // iteration cannot drift to a neighbour closer than the fp32 tolerance
+      if (!refined && (warm || it >= 1) && fabs(rq - est) <= 0.5 * tolc + 8.0 * tiny) sigma = rq;
     }
-    if (!have_res) {
-      for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
-      rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
-    }
+    for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
+    rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
     sl.lam[i] = rq;
     // the windows est +- tolc/2 of different groups are disjoint, so this also excludes
     // two singletons converging to the same eigenpair
