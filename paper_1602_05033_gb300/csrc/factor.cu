@@ -129,103 +129,227 @@ __global__ void k_gram_L(FactorWs f, int nn, int lo, int cnt, int tmax, double* 
   out[(size_t)a * tmax + b] = acc;
 }
 
-// cyclic parallel Jacobi (round-robin pairing) on the symmetric t x t matrix K, one CTA
-__global__ void __launch_bounds__(1024) k_jacobi(FactorWs f, int tmax) {
+// ---- eigenpairs of the symmetric t x t matrix K (eigenvalues to f.ev, eigenvectors to the columns
+// of f.Vk), in three steps:
+//  1. Householder reduction K = H T H^T to tridiagonal form (one CTA; the reflector vectors
+//     overwrite K below its subdiagonal);
+//  2. per eigenvalue (one thread each): bisection with Sturm counts on T, inverse iteration with
+//     the tridiagonal LU (partial pivoting), then the back-transformation by the reflectors;
+//  3. re-orthogonalisation of the vectors of eigenvalues closer than 1e-10 ||K|| (one warp).
+// The scratch of step 1 (d, e, reflector scales) lives in f.chol, free once the shifted solves have
+// run; the U rows of step 2 (3 t^2 doubles) in a scratch area of their own.  O(t^3) fp64 work once,
+// against O(t^3) per sweep for cyclic Jacobi on one SM.
+__global__ void __launch_bounds__(1024) k_tridiag(FactorWs f, int tmax) {
   const int t = f.tcount[0];
-  const int tp = t + (t & 1);  // padded to even; index t is a dummy
   double* K = f.K;
-  double* V = f.Vk;
-  __shared__ double cs_[1024], sn_[1024];
-  __shared__ int pp_[1024], qq_[1024];
-  __shared__ double off_s, tot_s;
-  for (int i = threadIdx.x; i < t * t; i += blockDim.x) {
-    const int r = i / t, c = i % t;
-    V[(size_t)r * tmax + c] = (r == c) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  if (t <= 1) {
-    if (threadIdx.x == 0 && t == 1) f.ev[0] = K[0];
-    return;
-  }
-  __shared__ double red_off[1024 / 32], red_tot[1024 / 32];
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    // off-diagonal and total Frobenius mass, every thread a strided share, fixed-order sums
-    double off = 0.0, tot = 0.0;
-    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
-      const int r = idx / t, c = idx % t;
-      const double v = K[(size_t)r * tmax + c] * K[(size_t)r * tmax + c];
-      tot += v;
-      if (r != c) off += v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red_off[threadIdx.x >> 5] = off;
-      red_tot[threadIdx.x >> 5] = tot;
-    }
+  double* d = f.chol;
+  double* e = f.chol + tmax;
+  double* bet = f.chol + 2 * (size_t)tmax;
+  double* pv = f.chol + 3 * (size_t)tmax;  // work vector
+  __shared__ double red[32];
+  __shared__ double s_val;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto block_sum = [&](double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        a += red_off[w];
-        b += red_tot[w];
-      }
-      off_s = a;
-      tot_s = b;
+      double a = 0.0;
+      for (int w = 0; w < nw; ++w) a += red[w];
+      s_val = a;
     }
     __syncthreads();
-    if (!(off_s > 1e-30 * tot_s)) break;
-    for (int round = 0; round < tp - 1; ++round) {
-      const int npairs = tp / 2;
-      for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
-        // round-robin: position 0 fixed, the others rotate
-        int i0 = k == 0 ? 0 : 1 + (k - 1 + round) % (tp - 1);
-        int j0 = 1 + (tp - 2 - k + round) % (tp - 1);
-        int p = min(i0, j0), q = max(i0, j0);
-        double c = 1.0, s = 0.0;
-        if (q < t) {
-          const double apq = K[(size_t)p * tmax + q];
-          if (apq != 0.0) {
-            const double app = K[(size_t)p * tmax + p], aqq = K[(size_t)q * tmax + q];
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(tt * tt + 1.0);
-            s = tt * c;
-          }
-        }
-        cs_[k] = c; sn_[k] = s; pp_[k] = p; qq_[k] = q;
-      }
-      __syncthreads();
-      // rows: K <- J^T K  (pairs touch disjoint rows)
-      for (int idx = threadIdx.x; idx < npairs * t; idx += blockDim.x) {
-        const int k = idx / t, col = idx % t;
-        const int p = pp_[k], q = qq_[k];
-        if (q >= t || sn_[k] == 0.0) continue;
-        const double c = cs_[k], s = sn_[k];
-        const double kp = K[(size_t)p * tmax + col], kq = K[(size_t)q * tmax + col];
-        K[(size_t)p * tmax + col] = c * kp - s * kq;
-        K[(size_t)q * tmax + col] = s * kp + c * kq;
-      }
-      __syncthreads();
-      // columns: K <- K J, V <- V J
-      for (int idx = threadIdx.x; idx < npairs * t; idx += blockDim.x) {
-        const int k = idx / t, row = idx % t;
-        const int p = pp_[k], q = qq_[k];
-        if (q >= t || sn_[k] == 0.0) continue;
-        const double c = cs_[k], s = sn_[k];
-        const double kp = K[(size_t)row * tmax + p], kq = K[(size_t)row * tmax + q];
-        K[(size_t)row * tmax + p] = c * kp - s * kq;
-        K[(size_t)row * tmax + q] = s * kp + c * kq;
-        const double vp = V[(size_t)row * tmax + p], vq = V[(size_t)row * tmax + q];
-        V[(size_t)row * tmax + p] = c * vp - s * vq;
-        V[(size_t)row * tmax + q] = s * vp + c * vq;
-      }
-      __syncthreads();
+    return s_val;
+  };
+  for (int k = 0; k + 2 < t; ++k) {
+    const int n1 = t - k - 1;  // rows k+1 .. t-1
+    double loc = 0.0;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+      const double x = K[(size_t)(k + 1 + i) * tmax + k];
+      loc += x * x;
+    }
+    const double xx = block_sum(loc);
+    const double x0 = K[(size_t)(k + 1) * tmax + k];
+    const double alpha = xx > 0.0 ? (x0 >= 0.0 ? -sqrt(xx) : sqrt(xx)) : 0.0;
+    // v = x - alpha e_1, H = I - beta v v^T with beta = 2 / v^T v = 1 / (alpha (alpha - x0))
+    const double beta = xx > 0.0 ? 1.0 / (alpha * (alpha - x0)) : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      d[k] = K[(size_t)k * tmax + k];
+      e[k] = xx > 0.0 ? alpha : x0;
+      bet[k] = beta;
+      K[(size_t)(k + 1) * tmax + k] = x0 - alpha;  // v_0; v_i = x_i below it
+    }
+    __syncthreads();
+    if (beta == 0.0) continue;
+    // p = beta A v over the trailing block A = K[k+1.., k+1..]
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+      const double* row = K + (size_t)(k + 1 + i) * tmax + (k + 1);
+      double acc = 0.0;
+      for (int j = 0; j < n1; ++j) acc = fma(row[j], K[(size_t)(k + 1 + j) * tmax + k], acc);
+      pv[i] = beta * acc;
+    }
+    __syncthreads();
+    loc = 0.0;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) loc += pv[i] * K[(size_t)(k + 1 + i) * tmax + k];
+    const double vtp = block_sum(loc);
+    // q = p - (beta/2)(v^T p) v;  A <- A - v q^T - q v^T
+    const double h = 0.5 * beta * vtp;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) pv[i] -= h * K[(size_t)(k + 1 + i) * tmax + k];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n1 * n1; idx += blockDim.x) {
+      const int i = idx / n1, j = idx % n1;
+      const double vi = K[(size_t)(k + 1 + i) * tmax + k], vj = K[(size_t)(k + 1 + j) * tmax + k];
+      double& a = K[(size_t)(k + 1 + i) * tmax + (k + 1 + j)];
+      a = a - vi * pv[j] - pv[i] * vj;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (t >= 2) {
+      d[t - 2] = K[(size_t)(t - 2) * tmax + (t - 2)];
+      e[t - 2] = K[(size_t)(t - 1) * tmax + (t - 2)];
+      bet[t - 2] = 0.0;
+    }
+    if (t >= 1) {
+      d[t - 1] = K[(size_t)(t - 1) * tmax + (t - 1)];
+      e[t - 1] = 0.0;
+      bet[t - 1] = 0.0;
     }
   }
-  for (int i = threadIdx.x; i < t; i += blockDim.x) f.ev[i] = K[(size_t)i * tmax + i];
+}
+
+// number of eigenvalues of the tridiagonal (d, e) below x (Sturm count, tiny pivots replaced)
+__device__ int tri_count(const double* __restrict__ d, const double* __restrict__ e, int t, double x, double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) <= pivmin) q = -pivmin;
+  c += q < 0.0;
+  for (int k = 1; k < t; ++k) {
+    q = (d[k] - x) - e[k - 1] * e[k - 1] / q;
+    if (fabs(q) <= pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+// step 2: eigenvalue i by bisection, its tridiagonal eigenvector by inverse iteration, then the
+// eigenvector of K by the reflectors of k_tridiag (applied last to first)
+__global__ void k_tri_eigvec(FactorWs f, int tmax, double* __restrict__ U3) {
+  const int t = f.tcount[0];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t) return;
+  const double* d = f.chol;
+  const double* e = f.chol + tmax;
+  const double* bet = f.chol + 2 * (size_t)tmax;
+  double* z = f.Vk + i;  // column i, stride tmax
+  const size_t ld = (size_t)tmax;
+  double lo = INFINITY, hi = -INFINITY;
+  for (int k = 0; k < t; ++k) {
+    const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k + 1 < t ? fabs(e[k]) : 0.0);
+    lo = fmin(lo, d[k] - r);
+    hi = fmax(hi, d[k] + r);
+  }
+  const double span = fmax(fmax(fabs(lo), fabs(hi)), DBL_MIN);
+  lo -= 4.0 * DBL_EPSILON * span;
+  hi += 4.0 * DBL_EPSILON * span;
+  const double pivmin = DBL_MIN * fmax(1.0, span * span);
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(hi - lo > 2.0 * DBL_EPSILON * span) || mid <= lo || mid >= hi) break;
+    if (tri_count(d, e, t, mid, pivmin) <= i) lo = mid;
+    else hi = mid;
+  }
+  const double lam = 0.5 * (lo + hi);
+  f.ev[i] = lam;
+  // inverse iteration on T - lam I: LU with partial pivoting, U with two superdiagonals
+  const double tiny = DBL_EPSILON * span + DBL_MIN;
+  for (int k = 0; k < t; ++k) z[k * ld] = 1.0 + 0.1 * (double)((k * 7 + i * 13) % 11) / 11.0;
+  for (int itr = 0; itr < 3; ++itr) {
+    // forward elimination with the right-hand side z; the factors are recomputed each iteration
+    double a0 = d[0] - lam, b0 = t > 1 ? e[0] : 0.0, c0 = 0.0;  // current row: diag, super1, super2
+    double r0 = z[0];
+    // rows of U (diagonal and two superdiagonals): row k of thread i at U3 + 3 (k t + i)
+    double* U = U3 + (size_t)i * 3;
+    const size_t us = (size_t)3 * t;
+    for (int k = 0; k + 1 < t; ++k) {
+      double a1 = e[k], b1 = d[k + 1] - lam, c1 = k + 2 < t ? e[k + 1] : 0.0, r1 = z[(k + 1) * ld];
+      if (fabs(a1) > fabs(a0)) {  // swap rows k and k+1
+        double tmp;
+        tmp = a0; a0 = a1; a1 = tmp;
+        tmp = b0; b0 = b1; b1 = tmp;
+        tmp = c0; c0 = c1; c1 = tmp;
+        tmp = r0; r0 = r1; r1 = tmp;
+      }
+      if (fabs(a0) < tiny) a0 = a0 < 0.0 ? -tiny : tiny;
+      const double l = a1 / a0;
+      U[(size_t)k * us] = a0;
+      U[(size_t)k * us + 1] = b0;
+      U[(size_t)k * us + 2] = c0;
+      z[k * ld] = r0;
+      a0 = b1 - l * b0;
+      b0 = c1 - l * c0;
+      c0 = 0.0;
+      r0 = r1 - l * r0;
+    }
+    if (fabs(a0) < tiny) a0 = a0 < 0.0 ? -tiny : tiny;
+    U[(size_t)(t - 1) * us] = a0;
+    U[(size_t)(t - 1) * us + 1] = 0.0;
+    U[(size_t)(t - 1) * us + 2] = 0.0;
+    z[(t - 1) * ld] = r0;
+    double x1 = 0.0, x2 = 0.0, nrm = 0.0;
+    for (int k = t - 1; k >= 0; --k) {
+      const double x = (z[k * ld] - U[(size_t)k * us + 1] * x1 - U[(size_t)k * us + 2] * x2) / U[(size_t)k * us];
+      z[k * ld] = x;
+      nrm = fmax(nrm, fabs(x));
+      x2 = x1;
+      x1 = x;
+    }
+    const double sc = nrm > 0.0 ? 1.0 / nrm : 1.0;
+    for (int k = 0; k < t; ++k) z[k * ld] *= sc;
+  }
+  // back-transformation: z <- H_0 H_1 ... H_{t-3} z
+  for (int k = t - 3; k >= 0; --k) {
+    const double b = bet[k];
+    if (b == 0.0) continue;
+    double dot = 0.0;
+    for (int r = k + 1; r < t; ++r) dot = fma(f.K[(size_t)r * tmax + k], z[r * ld], dot);
+    const double g = b * dot;
+    for (int r = k + 1; r < t; ++r) z[r * ld] -= g * f.K[(size_t)r * tmax + k];
+  }
+  double n2 = 0.0;
+  for (int k = 0; k < t; ++k) n2 = fma(z[k * ld], z[k * ld], n2);
+  const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  for (int k = 0; k < t; ++k) z[k * ld] *= inv;
+}
+
+// step 3: groups of eigenvalues closer than 1e-10 max |lambda| get their vectors orthonormalised
+// (modified Gram-Schmidt in ascending order, one warp)
+__global__ void k_tri_reorth(FactorWs f, int tmax) {
+  const int t = f.tcount[0];
+  const int lane = threadIdx.x;
+  double big = 0.0;
+  for (int k = 0; k < t; ++k) big = fmax(big, fabs(f.ev[k]));
+  const double tol = 1e-10 * big;
+  for (int i = 1; i < t; ++i) {
+    int j0 = i;
+    while (j0 > 0 && f.ev[i] - f.ev[j0 - 1] <= tol && i - j0 < 64) --j0;
+    for (int j = j0; j < i; ++j) {
+      double dot = 0.0;
+      for (int k = lane; k < t; k += 32) dot = fma(f.Vk[(size_t)k * tmax + j], f.Vk[(size_t)k * tmax + i], dot);
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      for (int k = lane; k < t; k += 32) f.Vk[(size_t)k * tmax + i] -= dot * f.Vk[(size_t)k * tmax + j];
+      __syncwarp();
+    }
+    if (j0 < i) {
+      double n2 = 0.0;
+      for (int k = lane; k < t; k += 32) n2 = fma(f.Vk[(size_t)k * tmax + i], f.Vk[(size_t)k * tmax + i], n2);
+      for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+      for (int k = lane; k < t; k += 32) f.Vk[(size_t)k * tmax + i] *= inv;
+      __syncwarp();
+    }
+  }
 }
 
 // B[:, k] = -(T_m + lambda_{p_k} I)^{-1} E_1 gamma a_{p_k}; one thread per pivot, banded Cholesky
@@ -535,16 +659,17 @@ __global__ void __launch_bounds__(256) k_gemm_accum(int64_t n, int K, int t, con
 
 // Z += Vbuf M with float pairs: V holds rows of S pairs per block (the S high parts, then the S
 // low parts), Z holds pairs in the 8 bytes of each of its doubles until k_pairs_to_double
-template <int S>
+// (BM x BN tiles, 256 threads of 4 x 4 outputs: BM = 4 * 256 / (BN / 4))
+template <int S, int BN>
 __global__ void __launch_bounds__(256) k_gemm_accum_ff(int64_t n, int K, int t, const float* __restrict__ Vb,
                                                        int64_t ldv, const double* __restrict__ Mg, int64_t ldm,
                                                        float2* __restrict__ Z, int64_t ldz) {
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int TXN = BN / 4, BM = 4 * (256 / TXN), BK = 16;
   __shared__ ff As[BK][BM + 1];
   __shared__ ff Bs[BK][BN];
   const int64_t row0 = (int64_t)blockIdx.x * BM;
   const int col0 = blockIdx.y * BN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tx = threadIdx.x % TXN, ty = threadIdx.x / TXN;
   ff acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -620,13 +745,23 @@ void gemm_accum(int bulk, int s, int z_f32, int64_t n, int K, int t, const void*
   if (t <= 0 || K <= 0) return;
   dim3 grid((unsigned)((n + 63) / 64), (unsigned)((t + 63) / 64));
   if (bulk == LYAP_PREC_F32X2) {
-    const int64_t ldvv = ldv;  // values per row of the buffer
+    // the column tile with the fewer padded columns: 64 wide, or 32 wide with 128-row tiles
+    const int w64 = (t + 63) / 64 * 64, w32 = (t + 31) / 32 * 32;
+    const bool narrow = w32 < w64;
+    dim3 gf(narrow ? (unsigned)((n + 127) / 128) : (unsigned)((n + 63) / 64), narrow ? (unsigned)(w32 / 32)
+                                                                                 : (unsigned)(w64 / 64));
+#define LYAP_GFF(SS_)                                                                                          \
+  if (narrow)                                                                                                  \
+    k_gemm_accum_ff<SS_, 32><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float2*)Z, ldz);     \
+  else                                                                                                         \
+    k_gemm_accum_ff<SS_, 64><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float2*)Z, ldz)
     switch (s) {
-      case 1: k_gemm_accum_ff<1><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
-      case 2: k_gemm_accum_ff<2><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
-      case 3: k_gemm_accum_ff<3><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
-      case 4: k_gemm_accum_ff<4><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldvv, Mg, ldm, (float2*)Z, ldz); break;
+      case 1: LYAP_GFF(1); break;
+      case 2: LYAP_GFF(2); break;
+      case 3: LYAP_GFF(3); break;
+      case 4: LYAP_GFF(4); break;
     }
+#undef LYAP_GFF
   } else if (bulk == LYAP_PREC_MIXED && z_f32) {
     k_gemm_accum<float, float><<<grid, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float*)Z, ldz);
   } else if (bulk == LYAP_PREC_MIXED) {
@@ -719,6 +854,7 @@ size_t factor_ws_bytes(int s, int nmax, int sylv) {
   add(sizeof(double) * (size_t)nmax2 * tmax);
   add(sizeof(double) * (size_t)nmax2);  // diagonal scratch of the pivoted Cholesky
   add(sizeof(int) * (size_t)tmax);      // kept-column order
+  if (!sylv) add(sizeof(double) * 3 * (size_t)tmax * tmax);  // U rows of the tridiagonal inverse iteration
   if (sylv) {
     add(sizeof(double) * (size_t)nmax2);          // stacked nodes
     add(sizeof(double) * (size_t)nmax2 * s);      // stacked rows
@@ -877,6 +1013,7 @@ int factor_core(lyap_handle* h, int tcap, int* t_out, double** M_out, int* ldm_o
   char* after = reinterpret_cast<char*>(f.M) + lyap_align256((int64_t)(sizeof(double) * (size_t)nmax * tmax));
   double* dg = reinterpret_cast<double*>(after);
   int* order_d = reinterpret_cast<int*>(after + lyap_align256((int64_t)(sizeof(double) * nmax)));
+  double* ew = reinterpret_cast<double*>(reinterpret_cast<char*>(order_d) + lyap_align256((int64_t)(sizeof(int) * tmax)));
 
   // 1. eigenvalues lambda and rows a = (Q^T E_1 gamma) of T_m (Alg. 3 steps 1-4)
   h->launches += launch_eigen_for_factor(h, 0, m, st);
@@ -907,8 +1044,10 @@ int factor_core(lyap_handle* h, int tcap, int* t_out, double** M_out, int* ldm_o
   h->launches += 2;
   // 4. K = L^T L and its eigendecomposition (eigenpairs of L L^T)
   k_gram_L<<<dim3(tpc, (tpc + 127) / 128), 128, 0, st>>>(f, N, 0, N, tmax, f.K);
-  k_jacobi<<<1, 1024, 0, st>>>(f, tmax);
-  h->launches += 2;
+  k_tridiag<<<1, 1024, 0, st>>>(f, tmax);
+  k_tri_eigvec<<<(tpc + 63) / 64, 64, 0, st>>>(f, tmax, ew);
+  k_tri_reorth<<<1, 32, 0, st>>>(f, tmax);
+  h->launches += 4;
   std::vector<double> ev(tpc);
   LYAP_CUDA_TRY(cudaMemcpyAsync(ev.data(), f.ev, sizeof(double) * tpc, cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
