@@ -166,7 +166,13 @@ int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2,
  * last solve (>= m: the iteration runs ahead of the checks by up to check_batch - 1),
  * out[4] convergence checks of the last solve (sum over batches),
  * out[5] block Lanczos sweeps of the last solve (sum over chunks),
- * out[6] number of kernels the library launched since lyap_create. */
+ * out[6] number of kernels the library launched since lyap_create,
+ * out[7] block Lanczos steps the last solve ran past its converged m (the speculative chunk),
+ * out[8] convergence checks it evaluated past that m.
+ * The chunk of steps launched ahead of its checks is sized from the residual history known
+ * so far: log10 of the residual extrapolated over the last 16 checked m to the steps still
+ * needed, times 1.25, between 4 and twice the previous chunk (at most check_batch); the
+ * convergence test is unchanged. */
 int lyap_phase_times(lyap_handle* h, double* out, int cap);
 
 /* Releases the handle's streams and events and the handle itself.  The caller

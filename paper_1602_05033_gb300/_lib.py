@@ -233,8 +233,8 @@ def lyap_projected_matrix(h: int, op: int, m: int, s: int):
 
 
 def lyap_phase_times(h: int):
-    out = (ct.c_double * 8)()
-    load().lyap_phase_times(ct.c_void_p(h), out, 8)
+    out = (ct.c_double * 9)()
+    load().lyap_phase_times(ct.c_void_p(h), out, 9)
     return list(out)
 
 

@@ -389,6 +389,39 @@ int round_status(lyap_handle* h) {
   return rc;
 }
 
+// Size of the next chunk of block Lanczos steps (launched ahead of its checks).  The steps of a
+// chunk run while the checks of the previous one are evaluated; the checks that find convergence
+// leave the chunk after it discarded.  From the history known on the host, log10 of the residual
+// is extrapolated linearly over the last (up to 16) checked m to the number of steps still needed
+// beyond those already launched; the next chunk covers 1.25 times that, between 4 steps and
+// min(2 x the previous chunk, the check batch).  The convergence test itself is unchanged: every
+// m up to the last launched step is still checked and the first m with rel <= tol is the result.
+int next_chunk(const double* hist, int known, int launched, int prev, int cap, double tol) {
+  const int hi_cap = std::min(2 * prev, cap);
+  const int lo_cap = std::min(4, hi_cap);
+  int n = 0;
+  double sx = 0, sy = 0, sxx = 0, sxy = 0;
+  for (int m = std::max(1, known - 15); m <= known; ++m) {
+    const double v = hist[m - 1];
+    if (!(v > 0.0) || !isfinite(v)) continue;
+    const double y = log10(v);
+    sx += m;
+    sy += y;
+    sxx += (double)m * m;
+    sxy += m * y;
+    ++n;
+  }
+  if (n < 4 || !(tol > 0.0)) return hi_cap;
+  const double den = n * sxx - sx * sx;
+  const double slope = den != 0.0 ? (n * sxy - sx * sy) / den : 0.0;
+  if (!(slope < 0.0)) return hi_cap;
+  const double icpt = (sy - slope * sx) / n;
+  const double m_star = (log10(tol) - icpt) / slope;  // predicted first converged m
+  const double need = 1.25 * (m_star - launched);
+  if (!(need < hi_cap)) return hi_cap;
+  return std::max(lo_cap, (int)ceil(need));
+}
+
 extern "C" {
 
 int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
@@ -425,6 +458,7 @@ int lyap_solve(lyap_handle* h, void* stream) {
   int chunk = std::min(4, p.check_batch_req);
   int done = std::min(p.maxit, chunk);  // last step of the chunk being checked
   int checked = 0;                      // largest m already checked
+  int known = 0;                        // largest m whose history value is on the host
   int c = 0;                            // index of the chunk being checked
   int result = LYAP_NOT_CONVERGED;
   int m_final = p.maxit;
@@ -434,6 +468,7 @@ int lyap_solve(lyap_handle* h, void* stream) {
   while (true) {
     LYAP_CUDA_TRY(cudaStreamWaitEvent(sd, c_end[c & 1], 0));
     cudaEventRecord(h->ev[5], sd);
+    const int first_new = checked + 1;
     while (checked < done) {
       // as many checks as fit in the check area with slots sized by the batch's largest m
       const int lo = checked + 1;
@@ -446,8 +481,10 @@ int lyap_solve(lyap_handle* h, void* stream) {
     cudaEventRecord(h->ev[4], sd);
     LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sd));
     LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 3, cw + (c & 1), sizeof(int), cudaMemcpyDeviceToHost, sd));
-    // the next chunk, while the checks run
-    chunk = std::min(2 * chunk, p.check_batch_req);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(h->hist_host + first_new - 1, h->hist + first_new - 1,
+                                  sizeof(double) * (checked - first_new + 1), cudaMemcpyDeviceToHost, sd));
+    // the next chunk, launched while the checks run (steps past the converged m are discarded)
+    chunk = next_chunk(h->hist_host, known, done, chunk, p.check_batch_req, h->tol);
     const int next = std::min(p.maxit, done + chunk);
     if (next > done) {
       LYAP_CUDA_TRY(cudaMemsetAsync(cw + ((c + 1) & 1), 0, sizeof(int), st));
@@ -455,6 +492,7 @@ int lyap_solve(lyap_handle* h, void* stream) {
     }
     LYAP_CUDA_TRY(cudaGetLastError());
     LYAP_CUDA_TRY(cudaStreamSynchronize(sd));
+    known = checked;
     float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, c_beg[c & 1], c_end[c & 1]);
     cudaEventElapsedTime(&b, h->ev[5], h->ev[4]);
@@ -488,6 +526,7 @@ int lyap_solve(lyap_handle* h, void* stream) {
   h->times_ms[1] = ms;
   h->times_ms[4] = t_check;
   h->times_ms[5] = t_lanczos;
+  h->checked = checked;
   return result;
 }
 
@@ -574,6 +613,8 @@ int lyap_phase_times(lyap_handle* h, double* out, int cap) {
   for (int i = 0; i < cap && i < 6; ++i) out[i] = h->times_ms[i];
   if (cap > 3) out[3] = (double)h->lanczos_done;
   if (cap > 6) out[6] = (double)h->launches;
+  if (cap > 7) out[7] = (double)(h->lanczos_done - h->m);  // steps run past the converged m
+  if (cap > 8) out[8] = (double)(h->checked - h->m);       // checks evaluated past it
   return LYAP_OK;
 }
 

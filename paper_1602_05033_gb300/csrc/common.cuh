@@ -121,6 +121,7 @@ struct lyap_handle {
   int m = 0;                    // iterations of the last solve
   int converged = 0;
   int lanczos_done = 0;         // iterations whose blocks exist
+  int checked = 0;              // largest m the last solve checked
   double* hist_host = nullptr;  // pinned copy
   int* flags_host = nullptr;    // pinned
   cudaStream_t side = nullptr;  // second stream (checks)

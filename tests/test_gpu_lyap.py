@@ -242,3 +242,21 @@ def test_indefinite_operator_detected(pkg):
     with pytest.raises(_lib.LyapError) as e:
         sol.solve()
     assert e.value.status == _lib.LYAP_ERR_NOT_NEGDEF
+
+
+def test_speculative_chunks_follow_the_residual_trend(pkg):
+    """The chunk of steps launched ahead of its checks is sized from the residual trend (the
+    convergence test is unchanged): the result equals the oracle's m and history, and the steps
+    run past the converged m stay below what a blindly doubled chunk can leave (up to 63: the
+    rest of the converging chunk of up to 32, plus a whole speculative chunk of 32)."""
+    A = wl.laplacian_3d(14)
+    C = wl.rhs(A.shape[0], 4, 21)
+    ref, sol, st = _solve_both(pkg, A, C, 1e-9, 400)
+    assert st == 0 and sol.m == ref.m
+    ok, worst = _hist_ok(sol.history(), ref.history)
+    assert ok, worst
+    ph = sol.phase_times()
+    wasted, late_checks = ph[7], ph[8]
+    print(f"m={sol.m}: steps past m {wasted:.0f}, checks past m {late_checks:.0f}")
+    assert 0 <= late_checks <= wasted < 48
+    sol.close()
