@@ -125,6 +125,24 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1,
                 const lyap_options* opt, void* workspace, size_t ws_bytes,
                 void* stream, lyap_handle** out);
 
+/* Large A, small dense B (Sec. 5.2, Alg. 5): only A is projected.  B = P Upsilon P^T is
+ * diagonalised once in lyap_smallb_create; every check then evaluates the residual of the
+ * reduced equation T_m Y + Y B + E_1 gamma_1 C2^T = 0 as Alg. 5 does, and lyap_factor returns
+ * Z1 = V_m (Q Y1) (n1 x t, by the two-pass device) and Z2 = P Y2 (n2 x t) from the truncation
+ * Y~ ~= Y1 Y2^T of the reduced solution in the eigenbases of T_m and B.
+ *  B         : fp64 n2 x n2 row-major, symmetric (its symmetric part is used), in c_mem memory
+ *  n2        : 1 <= n2 <= s * opt.maxit
+ *  C1, C2    : fp64 n1 x s and n2 x s row-major, in c_mem memory
+ * Other arguments, ownership and the returned handle are those of lyap_create; lyap_solve,
+ * lyap_residual_norm, lyap_projected_matrix (op 0), lyap_factor (Z2 required) and
+ * lyap_destroy apply.  The inputs are copied.  LYAP_ERR_NONFINITE if B or C2 holds a NaN or Inf. */
+int lyap_smallb_workspace_size(const lyap_csr* A, int n2, int s,
+                               const lyap_options* opt, size_t* bytes);
+int lyap_smallb_create(const lyap_csr* A, const double* B, int n2, const double* C1,
+                       const double* C2, int c_mem, int s, double tol,
+                       const lyap_options* opt, void* workspace, size_t ws_bytes,
+                       void* stream, lyap_handle** out);
+
 /* Pass 1 (Alg. 1 steps 3-7): block Lanczos (Alg. 2: the block MGS projections and a Cholesky
  * QR normalisation, formed from one reduction per step), the cheap residual norm of Prop. 3.1 / Alg. 3
  * (Alg. 4 for Sylvester) at every check_every-th step, until tol or maxit.

@@ -33,6 +33,8 @@ EXPORTED = (
     "lyap_default_options",
     "lyap_workspace_size",
     "lyap_create",
+    "lyap_smallb_workspace_size",
+    "lyap_smallb_create",
     "lyap_solve",
     "lyap_residual_norm",
     "lyap_factor",
@@ -115,6 +117,10 @@ def load(path: str | None = None) -> ct.CDLL:
                                         ct.POINTER(lyap_options), ct.POINTER(ct.c_size_t)]
     lib.lyap_create.argtypes = [ct.POINTER(lyap_csr), ct.POINTER(lyap_csr), P, P, ct.c_int, ct.c_int, ct.c_double,
                                 ct.POINTER(lyap_options), P, ct.c_size_t, P, ct.POINTER(P)]
+    lib.lyap_smallb_workspace_size.argtypes = [ct.POINTER(lyap_csr), ct.c_int, ct.c_int, ct.POINTER(lyap_options),
+                                                ct.POINTER(ct.c_size_t)]
+    lib.lyap_smallb_create.argtypes = [ct.POINTER(lyap_csr), P, ct.c_int, P, P, ct.c_int, ct.c_int, ct.c_double,
+                                       ct.POINTER(lyap_options), P, ct.c_size_t, P, ct.POINTER(P)]
     lib.lyap_solve.argtypes = [P, P]
     lib.lyap_residual_norm.argtypes = [P, ct.POINTER(ct.c_double), ct.c_int, ct.POINTER(ct.c_int)]
     lib.lyap_factor.argtypes = [P, P, ct.c_int64, P, ct.c_int64, ct.c_int, ct.c_int, ct.c_int,
@@ -183,6 +189,26 @@ def lyap_create(A, B, C1_ptr: int, C2_ptr: int | None, c_mem: int, s: int, tol: 
                             ct.c_void_p(stream), ct.byref(h))
     if st != LYAP_OK:
         raise LyapError(st, "lyap_create")
+    return h.value
+
+
+def lyap_smallb_workspace_size(A: lyap_csr, n2: int, s: int, opt: lyap_options | None) -> int:
+    nb = ct.c_size_t(0)
+    st = load().lyap_smallb_workspace_size(ct.byref(A), int(n2), int(s), ct.byref(opt) if opt is not None else None,
+                                           ct.byref(nb))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_smallb_workspace_size")
+    return int(nb.value)
+
+
+def lyap_smallb_create(A, B_ptr: int, n2: int, C1_ptr: int, C2_ptr: int, c_mem: int, s: int, tol: float, opt,
+                       ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ct.c_void_p(0)
+    st = load().lyap_smallb_create(ct.byref(A), ct.c_void_p(B_ptr), int(n2), ct.c_void_p(C1_ptr), ct.c_void_p(C2_ptr),
+                                   int(c_mem), int(s), float(tol), ct.byref(opt) if opt is not None else None,
+                                   ct.c_void_p(ws_ptr), ct.c_size_t(ws_bytes), ct.c_void_p(stream), ct.byref(h))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_smallb_create")
     return h.value
 
 

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -80,9 +81,10 @@ int valid_block(int s) { return valid_s(s); }
 int validate_csr(const lyap_csr* A) { return check_csr(A); }
 
 // external: the check slots, factor scratch and host staging of Z are lent by a caller (a batch)
-int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external) {
+int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external, int n2) {
   p.s = s;
   p.sylv = B != nullptr;
+  p.n2 = n2;
   p.bulk = o.precision;
   p.maxit = o.maxit;
   p.check_batch = o.check_batch;
@@ -143,13 +145,23 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
   }
   p.check_bytes = (size_t)(1 + p.sylv) * p.check_batch * check_slot_bytes(s, p.nmax);
   p.check = take(p.check_bytes);
-  p.factor_bytes = factor_ws_bytes(s, p.nmax, p.sylv);
+  // the small-B factor works on a stacked kernel of N + n2 <= 2 nmax rows, as the two-sided one
+  p.factor_bytes = factor_ws_bytes(s, p.nmax, p.sylv || n2 > 0);
   size_t p2 = 0;
   for (int k = 0; k < 1 + p.sylv; ++k) p2 += pass2_ws_bytes(p.op[k].n, s, o.pass2_blocks, p.bulk);
   p.factor = take(p.factor_bytes + p2);
-  p.zstage = take(o.zcap > 0 ? sizeof(double) * (size_t)o.zcap * (A->n + (B ? B->n : 0)) : 0);
+  p.zstage = take(o.zcap > 0 ? sizeof(double) * (size_t)o.zcap * (A->n + (B ? B->n : n2)) : 0);
   p.staging_bytes = staging_bytes(A) + staging_bytes(B);
   p.staging = take(p.staging_bytes);
+  if (n2 > 0) {
+    // B copy (then its reflectors), P, upsilon, P^T C2, C2, Alg. 5 row sums, eigen scratch, ints
+    const size_t nn = (size_t)n2 * n2;
+    p.smallb_bytes = lyap_align256((int64_t)(sizeof(double) * nn)) * 2 + lyap_align256((int64_t)(sizeof(double) * n2)) +
+                     2 * lyap_align256((int64_t)(sizeof(double) * (size_t)n2 * s)) +
+                     lyap_align256((int64_t)(sizeof(double) * (size_t)o.check_batch * n2)) +
+                     lyap_align256((int64_t)(sizeof(double) * (4 * (size_t)n2 + 3 * nn))) + 256;
+    p.smallb = take(p.smallb_bytes);
+  }
   p.total = off;
   return LYAP_OK;
 }
@@ -239,9 +251,9 @@ int lyap_workspace_size(const lyap_csr* A, const lyap_csr* B, int s, const lyap_
 // lyap_create's work; external = 1 leaves the check, factor and Z staging areas to the caller
 int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
                   double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream, int external,
-                  lyap_handle** out) {
+                  lyap_handle** out, int n2) {
   if (!out || !valid_s(s) || !C1 || !(tol >= 0.0)) return LYAP_ERR_ARG;
-  if ((B == nullptr) != (C2 == nullptr)) return LYAP_ERR_ARG;
+  if (n2 == 0 && (B == nullptr) != (C2 == nullptr)) return LYAP_ERR_ARG;
   if (c_mem != LYAP_MEM_DEVICE && c_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
   int rc = check_csr(A);
   if (rc != LYAP_OK) return rc;
@@ -251,7 +263,7 @@ int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const 
     return LYAP_ERR_ARG;
   if (!step_supported(o.precision, s)) return LYAP_ERR_ARG;
   Plan p;
-  rc = make_plan(A, B, s, o, p, external);
+  rc = make_plan(A, B, s, o, p, external, n2);
   if (rc != LYAP_OK) return rc;
   if (!workspace || ws_bytes < p.total || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LYAP_ERR_WORKSPACE;
   *out = nullptr;
@@ -430,6 +442,110 @@ int lyap_create(const lyap_csr* A, const lyap_csr* B, const double* C1, const do
   return create_handle(A, B, C1, C2, c_mem, s, tol, opt, workspace, ws_bytes, stream, 0, out);
 }
 
+int lyap_smallb_workspace_size(const lyap_csr* A, int n2, int s, const lyap_options* opt, size_t* bytes) {
+  if (!bytes || !valid_s(s) || n2 < 1) return LYAP_ERR_ARG;
+  int rc = check_csr(A);
+  if (rc != LYAP_OK) return rc;
+  lyap_options o = resolve(opt);
+  if (o.precision != LYAP_PREC_F64 && o.precision != LYAP_PREC_MIXED && o.precision != LYAP_PREC_F32X2)
+    return LYAP_ERR_ARG;
+  if (!step_supported(o.precision, s) || n2 > s * o.maxit) return LYAP_ERR_ARG;
+  Plan p;
+  rc = make_plan(A, nullptr, s, o, p, 0, n2);
+  if (rc != LYAP_OK) return rc;
+  *bytes = p.total;
+  return LYAP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// B <- (B + B^T) / 2 in place (n2 x n2 row-major); *bad set if an entry is not finite
+__global__ void k_symmetrize(double* B, int n2, int* bad) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n2 * n2) return;
+  if (!isfinite(B[idx])) atomicOr(bad, 1);
+  const int r = (int)(idx / n2), c = (int)(idx % n2);
+  if (r >= c) return;
+  const double v = 0.5 * (B[(size_t)r * n2 + c] + B[(size_t)c * n2 + r]);
+  B[(size_t)r * n2 + c] = v;
+  B[(size_t)c * n2 + r] = v;
+}
+
+// ct = P^T C2 (n2 x s); column i of P is the eigenvector of upsilon_i
+__global__ void k_ptc(const double* __restrict__ P, const double* __restrict__ C2, int n2, int s,
+                      double* __restrict__ ct) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  for (int c = 0; c < s; ++c) {
+    double acc = 0.0;
+    for (int r = 0; r < n2; ++r) acc = fma(P[(size_t)r * n2 + i], C2[(size_t)r * s + c], acc);
+    ct[(size_t)i * s + c] = acc;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lyap_smallb_create(const lyap_csr* A, const double* B, int n2, const double* C1, const double* C2, int c_mem,
+                       int s, double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream,
+                       lyap_handle** out) {
+  if (!out || !B || !C2 || n2 < 1) return LYAP_ERR_ARG;
+  if (c_mem != LYAP_MEM_DEVICE && c_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
+  lyap_options o = resolve(opt);
+  if (n2 > s * o.maxit) return LYAP_ERR_ARG;
+  int rc = create_handle(A, nullptr, C1, nullptr, c_mem, s, tol, opt, workspace, ws_bytes, stream, 0, out, n2);
+  if (rc != LYAP_OK) return rc;
+  lyap_handle* h = *out;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto fail = [&](int code) {
+    lyap_destroy(h);
+    *out = nullptr;
+    return code;
+  };
+  const size_t nn = (size_t)n2 * n2;
+  char* p = h->ws + h->plan.smallb;
+  auto take = [&](size_t bytes) { char* r = p; p += lyap_align256((int64_t)bytes); return r; };
+  double* Bk = (double*)take(sizeof(double) * nn);
+  SmallB& sb = h->smallb;
+  sb.P = (double*)take(sizeof(double) * nn);
+  sb.ups = (double*)take(sizeof(double) * n2);
+  sb.ctil = (double*)take(sizeof(double) * (size_t)n2 * s);
+  double* C2d = (double*)take(sizeof(double) * (size_t)n2 * s);
+  sb.parts = (double*)take(sizeof(double) * (size_t)h->opt.check_batch * n2);
+  double* scratch = (double*)take(sizeof(double) * (4 * (size_t)n2 + 3 * nn));
+  int* ints = (int*)take(256);
+  sb.d_n2 = ints;
+  const cudaMemcpyKind kind = c_mem == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (cudaMemcpyAsync(Bk, B, sizeof(double) * nn, kind, st) != cudaSuccess ||
+      cudaMemcpyAsync(C2d, C2, sizeof(double) * (size_t)n2 * s, kind, st) != cudaSuccess ||
+      cudaMemcpyAsync(sb.d_n2, &n2, sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return fail(LYAP_ERR_CUDA);
+  if (cudaMemsetAsync(ints + 2, 0, sizeof(int), st) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  k_symmetrize<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Bk, n2, ints + 2);
+  int bad = 0;
+  if (cudaMemcpyAsync(&bad, ints + 2, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(LYAP_ERR_CUDA);
+  if (bad) return fail(LYAP_ERR_NONFINITE);
+  // B = P Upsilon P^T, once (the reduced equations of every m share it)
+  rc = dense_eigh(Bk, n2, n2, sb.ups, sb.P, scratch, ints + 1, st);
+  if (rc != LYAP_OK) return fail(rc);
+  k_ptc<<<(n2 + 127) / 128, 128, 0, st>>>(sb.P, C2d, n2, s, sb.ctil);
+  h->launches += 5;
+  std::vector<double> c2h((size_t)n2 * s);
+  if (cudaMemcpyAsync(c2h.data(), C2d, sizeof(double) * c2h.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(LYAP_ERR_CUDA);
+  double nrm = 0.0;
+  for (double v : c2h) nrm += v * v;
+  sb.c2norm = sqrt(nrm);
+  if (!(sb.c2norm > 0.0) || !std::isfinite(sb.c2norm)) return fail(LYAP_ERR_NONFINITE);
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : fail(LYAP_ERR_CUDA);
+}
+
 int lyap_solve(lyap_handle* h, void* stream) {
   if (!h) return LYAP_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -568,7 +684,7 @@ int lyap_projected_matrix(lyap_handle* h, int op, int m, double* ab, int ldab, d
 int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int z_mem, int tcap,
                 int* t_out, void* stream) {
   if (!h || !h->solved || h->factored || !Z1 || !t_out || tcap < 0) return LYAP_ERR_ARG;
-  if ((h->plan.sylv != 0) != (Z2 != nullptr)) return LYAP_ERR_ARG;
+  if ((h->plan.sylv != 0 || h->plan.n2 > 0) != (Z2 != nullptr)) return LYAP_ERR_ARG;
   if (z_dtype != LYAP_F64 && z_dtype != LYAP_F32) return LYAP_ERR_ARG;
   if (z_dtype == LYAP_F32 && h->plan.bulk != LYAP_PREC_MIXED) return LYAP_ERR_ARG;
   if (ldz1 < tcap || (Z2 && ldz2 < tcap)) return LYAP_ERR_ARG;
@@ -594,7 +710,8 @@ int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, 
     const int t = *t_out;
     LYAP_CUDA_TRY(cudaMemcpy2DAsync(Z1, zw * ldz1, z1, zw * l1, zw * t, h->op[0].n, cudaMemcpyDeviceToHost, st));
     if (Z2)
-      LYAP_CUDA_TRY(cudaMemcpy2DAsync(Z2, zw * ldz2, z2, zw * l2, zw * t, h->op[1].n, cudaMemcpyDeviceToHost, st));
+      LYAP_CUDA_TRY(cudaMemcpy2DAsync(Z2, zw * ldz2, z2, zw * l2, zw * t, h->plan.n2 > 0 ? h->plan.n2 : h->op[1].n,
+                                      cudaMemcpyDeviceToHost, st));
   }
   cudaEventRecord(h->ev[1], st);
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));

@@ -1112,6 +1112,75 @@ __global__ void k_cauchy_sylv(CheckArgs ga, CheckArgs gb, int side) {
   if (lane == 0) me.part[i] = tot;
 }
 
+// large A, small B (Alg. 5): one warp per eigenpair j of B,
+//   part_j = ||sum_k (ctil_j . a_k) / (upsilon_j + lambda_k) w_k||^2,
+// (e_j^T S) D_j^{-1} W with S = (P^T C2 gamma^T)(E_1^T Q), D_j = upsilon_j I + Lambda, W = Q^T E_m tau^T
+__global__ void k_cauchy_smallb(CheckArgs g, const double* __restrict__ ups, const double* __restrict__ ct, int n2,
+                                double* __restrict__ parts) {
+  const int c_idx = blockIdx.y;
+  const int m = g.m_lo + c_idx;
+  if (!checked(g, m)) return;
+  const int s = g.s, N = s * m;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= n2) return;
+  Slot sl = get_slot(g.slots, s, g.nmax, c_idx);
+  double cj[LYAP_MAX_S], acc[LYAP_MAX_S];
+  for (int c = 0; c < s; ++c) {
+    cj[c] = ct[(size_t)j * s + c];
+    acc[c] = 0.0;
+  }
+  const double uj = ups[j];
+  bool bad = false;
+  for (int k = lane; k < N; k += 32) {
+    double dot = 0.0;
+    for (int c = 0; c < s; ++c) dot = fma(cj[c], sl.a[(size_t)k * s + c], dot);
+    const double den = uj + sl.lam[k];
+    bad |= !(den < 0.0);
+    const double f = dot / den;
+    for (int c = 0; c < s; ++c) acc[c] = fma(f, sl.w[(size_t)k * s + c], acc[c]);
+  }
+  double tot = 0.0;
+  for (int c = 0; c < s; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    tot = fma(v, v, tot);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(g.chk_err + m - 1, DERR_NOTNEGDEF);
+  if (lane == 0) parts[(size_t)c_idx * n2 + j] = tot;
+}
+
+// Alg. 5's residual: sqrt(sum_j part_j) / (||C1||_F ||C2||_F); history and convergence flags
+__global__ void k_finalize_smallb(CheckArgs g, const double* __restrict__ parts, int n2, double c2norm, double* hist,
+                                  double tol, int* first_conv) {
+  const int c_idx = blockIdx.x;
+  const int m = g.m_lo + c_idx;
+  if (!checked(g, m)) {
+    if (threadIdx.x == 0) hist[m - 1] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  __shared__ double red[256];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < n2; j += blockDim.x) t += parts[(size_t)c_idx * n2 + j];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double beta = g.log[REC_TDIAG * g.s * g.s];
+    const double rel = sqrt(red[0]) / (beta * c2norm);
+    hist[m - 1] = rel;
+    if (g.chk_err[m - 1] != 0 || !isfinite(rel)) {
+      if (!isfinite(rel)) atomicOr(g.chk_err + m - 1, DERR_NONFINITE);
+      atomicMin(first_conv + 1, m);
+    } else if (rel <= tol) {
+      atomicMin(first_conv, m);
+    }
+  }
+}
+
 // sum of the per-row parts in a fixed order; history entry and convergence flag
 __global__ void k_finalize(CheckArgs ga, CheckArgs gb, int sylv, double* hist, double tol, int* first_conv) {
   const int c_idx = blockIdx.x;
@@ -1275,6 +1344,13 @@ int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
   CheckArgs gb = ga;
   const int wpb = 8;
   dim3 gc((nmax_batch + wpb - 1) / wpb, nchk);
+  if (h->plan.n2 > 0) {
+    const int n2 = h->plan.n2;
+    k_cauchy_smallb<<<dim3((n2 + wpb - 1) / wpb, nchk), wpb * 32, 0, st>>>(ga, h->smallb.ups, h->smallb.ctil, n2,
+                                                                          h->smallb.parts);
+    k_finalize_smallb<<<nchk, 256, 0, st>>>(ga, h->smallb.parts, n2, h->smallb.c2norm, h->hist, h->tol, h->flags + 1);
+    return nl + 2;
+  }
   if (h->plan.sylv) {
     gb = make_args(h, 1, m_lo, nchk, every, nb, nchk);
     nl += eigen_pipeline(gb, nmax_batch, st);

@@ -68,6 +68,7 @@ struct OpDev {
 struct Plan {
   int s = 1;
   int sylv = 0;
+  int n2 = 0;             // size of a small dense B (Sec. 5.2: only A is projected), 0 otherwise
   int bulk = LYAP_PREC_F64;  // bulk number type of the basis: LYAP_PREC_F64, _MIXED (fp32), _F32X2 (pairs)
   int maxit = 1000;
   int sweep_grid = 0;     // CTAs of the reducing sweep of a block Lanczos step (and of the init sweeps)
@@ -85,7 +86,7 @@ struct Plan {
     int val_pair;
   } op[2];
   size_t hist = 0, flags = 0, chk_err = 0, check = 0, check_bytes = 0, factor = 0, factor_bytes = 0, zstage = 0,
-         staging = 0, staging_bytes = 0;
+         staging = 0, staging_bytes = 0, smallb = 0, smallb_bytes = 0;
 };
 
 // per-check scratch (fp64 unless noted), one slot per check in a batch
@@ -103,8 +104,19 @@ struct CheckSlot {
 size_t check_slot_bytes(int s, int nmax);
 int batch_nmax(int s, int m_hi);
 
+// A small dense B of A X + X B + C1 C2^T = 0 (Sec. 5.2): B = P Upsilon P^T computed once
+struct SmallB {
+  double* P = nullptr;      // n2 x n2, eigenvector j in column j
+  double* ups = nullptr;    // n2 eigenvalues, ascending
+  double* ctil = nullptr;   // n2 x s: P^T C2
+  double* parts = nullptr;  // check_batch x n2 per-row sums of Alg. 5
+  int* d_n2 = nullptr;      // n2 on the device (inner dimension of the factor's products)
+  double c2norm = 0.0;      // ||C2||_F
+};
+
 struct lyap_handle {
   Plan plan;
+  SmallB smallb;
   char* ws = nullptr;
   OpDev op[2];
   int s = 1;
@@ -176,13 +188,14 @@ int valid_block(int s);
 int validate_csr(const lyap_csr* A);
 int create_handle(const lyap_csr* A, const lyap_csr* B, const double* C1, const double* C2, int c_mem, int s,
                   double tol, const lyap_options* opt, void* workspace, size_t ws_bytes, void* stream, int external,
-                  lyap_handle** out);
-int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external);
+                  lyap_handle** out, int n2 = 0);
+int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o, Plan& p, int external, int n2 = 0);
 void solve_begin(lyap_handle* h, cudaStream_t st);
 int solve_end(lyap_handle* h, int done, int m_final, int result, cudaStream_t st);
 int round_status(lyap_handle* h);
 
 // factor.cu
+int dense_eigh(double* K, int n, int ld, double* ev, double* V, double* scratch, int* cnt, cudaStream_t st);
 size_t factor_ws_bytes(int s, int nmax, int sylv);
 size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk);
 int run_factor_basis(lyap_handle* h, const double* basis, int64_t n, double* Z, int64_t ldz, int tcap, int* t_out,

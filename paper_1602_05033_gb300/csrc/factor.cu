@@ -475,14 +475,15 @@ __device__ double block_sum(double v, double* red) {
 // factor (block 0: rows 0..N-1, block 1: rows N..2N-1; f.L row k holds column k).  The
 // columns are copied to W (column k at W + k N) and reduced in place; R (t x t, row-major,
 // rows >= N zero) is written out.  Only R is needed: Y~ = L_A L_B^T = U_A (R_A R_B^T) U_B^T.
-__global__ void __launch_bounds__(1024) k_householder_r(const double* __restrict__ Lrows, int nn, int N,
+__global__ void __launch_bounds__(1024) k_householder_r(const double* __restrict__ Lrows, int nn, int Na, int Nb,
                                                         const int* __restrict__ tcount, double* __restrict__ Wa,
                                                         double* __restrict__ Wb, double* __restrict__ Ra,
                                                         double* __restrict__ Rb, int tmax) {
   __shared__ double red[32];
   __shared__ double s_vn2;
   const int t = *tcount;
-  const int lo = blockIdx.x == 0 ? 0 : N;
+  const int lo = blockIdx.x == 0 ? 0 : Na;
+  const int N = blockIdx.x == 0 ? Na : Nb;  // rows of this block's part
   double* W = blockIdx.x == 0 ? Wa : Wb;
   double* R = blockIdx.x == 0 ? Ra : Rb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -873,7 +874,9 @@ size_t pass2_ws_bytes(int64_t n, int s, int kb, int bulk) {
 // eps of eq. 2.5: the option, or, when it is 0, min(1e-12, tol / (10 (||T_m|| + ||J_m||))), so that
 // the truncation moves the residual by at most tol / 10 (J_m = T_m for Lyapunov).  ||T_m|| is the
 // largest |eigenvalue|, the first or last of the ascending list.
-int trunc_eps_of(lyap_handle* h, const double* lam_a, const double* lam_b, int N, double* eps, cudaStream_t st) {
+int trunc_eps_of(lyap_handle* h, const double* lam_a, const double* lam_b, int N, double* eps, cudaStream_t st,
+                 int Nb = -1) {
+  if (Nb < 0) Nb = N;
   if (h->opt.trunc_eps > 0.0) {
     *eps = h->opt.trunc_eps;
     return LYAP_OK;
@@ -883,7 +886,7 @@ int trunc_eps_of(lyap_handle* h, const double* lam_a, const double* lam_b, int N
   LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[1], lam_a + N - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
   if (lam_b) {
     LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[2], lam_b, sizeof(double), cudaMemcpyDeviceToHost, st));
-    LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[3], lam_b + N - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(&ends[3], lam_b + Nb - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
   const double na = fmax(fabs(ends[0]), fabs(ends[1]));
@@ -959,7 +962,7 @@ int run_factor_sylv(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ld
                                                              0, N2, h->flags);
   k_apply_lpp<<<(N2 + 127) / 128, 128, 0, st>>>(f, N2, N2, tmax);
   // 4. R_A, R_B; G = R_A R_B^T by columns (G(:, j) = R_A R_B(j, :)^T); its one-sided Jacobi SVD
-  k_householder_r<<<2, 1024, 0, st>>>(f.L, N2, N, f.tcount, WA, WBh, RA, RB, tmax);
+  k_householder_r<<<2, 1024, 0, st>>>(f.L, N2, N, N, f.tcount, WA, WBh, RA, RB, tmax);
   small_gemm(RB, tmax, 0, RA, tmax, 1, nullptr, nullptr, Gc, tmax, tpc, tpc, f.tcount, st);
   k_onesided_jacobi<<<1, 1024, 0, st>>>(Gc, VG, f.tcount, tmax, sig_d);
   h->launches += 6;
@@ -1075,8 +1078,174 @@ int factor_core(lyap_handle* h, int tcap, int* t_out, double** M_out, int* ldm_o
   return LYAP_OK;
 }
 
+namespace {
+
+// ---- large A, small B (Sec. 5.2, Alg. 5): only A is projected; B = P Upsilon P^T once ------------
+// stacked nodes mu = [lambda (N); upsilon (n2)] and rows c = [a (N x s); ctil = P^T C2 (n2 x s)]
+__global__ void k_smallb_stack(const double* __restrict__ lam, const double* __restrict__ a, int N,
+                               const double* __restrict__ ups, const double* __restrict__ ct, int n2, int s,
+                               double* __restrict__ mu, double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N + n2) return;
+  const bool A = i < N;
+  const int r = A ? i : i - N;
+  mu[i] = A ? lam[r] : ups[r];
+  for (int k = 0; k < s; ++k) c[(size_t)i * s + k] = A ? a[(size_t)r * s + k] : ct[(size_t)r * s + k];
+}
+
+// out[i][k] = -(ctil_i . c_{p_k}) / (upsilon_i + mu_{p_k}): the B rows of the stacked kernel at the
+// pivots, before the multiplication by P
+__global__ void k_smallb_brows(FactorWs f, int N, int n2, int s, const double* __restrict__ mu,
+                               const double* __restrict__ c, double* __restrict__ out, int ldo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  const int t = f.tcount[0];
+  if (i >= n2 || k >= t) return;
+  const int p = f.piv[k];
+  double dot = 0.0;
+  for (int q = 0; q < s; ++q) dot = fma(c[(size_t)(N + i) * s + q], c[(size_t)p * s + q], dot);
+  out[(size_t)i * ldo + k] = -dot / (mu[N + i] + mu[p]);
+}
+
+// the rows of M2 (n2 x tk, leading dimension tmax) into the caller's Z2 (fp64 or fp32)
+template <typename TZ>
+__global__ void k_copy_z2(const double* __restrict__ M2, int ldm, int n2, int tk, TZ* __restrict__ Z, int64_t ldz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n2 * tk) return;
+  const int r = (int)(idx / tk), c = (int)(idx % tk);
+  Z[(size_t)r * ldz + c] = (TZ)M2[(size_t)r * ldm + c];
+}
+
+}  // namespace
+
+// Eigenpairs of the symmetric n x n matrix K (row-major, leading dimension ld; overwritten):
+// eigenvalues ascending into ev, eigenvector j into column j of V (leading dimension ld).  scratch:
+// 4 n + 3 n^2 doubles; cnt: one device int.  Same kernels as the factor's t x t problem.
+int dense_eigh(double* K, int n, int ld, double* ev, double* V, double* scratch, int* cnt, cudaStream_t st) {
+  if (n <= 0) return LYAP_OK;
+  FactorWs f{};
+  f.K = K;
+  f.Vk = V;
+  f.ev = ev;
+  f.chol = scratch;
+  f.tcount = cnt;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(cnt, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+  k_tridiag<<<1, 1024, 0, st>>>(f, ld);
+  k_tri_eigvec<<<(n + 63) / 64, 64, 0, st>>>(f, ld, scratch + 4 * (size_t)ld);
+  k_tri_reorth<<<1, 32, 0, st>>>(f, ld);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // n lives on the host stack
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
+}
+
+// Z1 = V_m (Q Y1) by the second pass and Z2 = P Y2, with Y~ = -(a_k . ctil_j)/(lambda_k + upsilon_j)
+// ~= Y1 Y2^T truncated (the end of Sec. 5.2); the truncated SVD as in the two-sided case, on the
+// stacked kernel with nodes [lambda; upsilon] and rows [a; ctil] (unequal halves N and n2).
+int run_factor_smallb(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap,
+                      int* t_out, cudaStream_t st) {
+  const int s = h->s, m = h->m, N = s * m;
+  const int n2 = h->plan.n2, NT = N + n2;
+  const int nmax = h->plan.nmax, nmax2 = 2 * nmax;
+  const int tmax = nmax2 < kTmaxCap ? nmax2 : kTmaxCap;
+  FactorWs f = carve(h->factor_ws, s, nmax2, tmax, nmax);
+  char* p = reinterpret_cast<char*>(f.M) + lyap_align256((int64_t)(sizeof(double) * (size_t)nmax2 * tmax));
+  auto take = [&](size_t bytes) { char* r = p; p += lyap_align256((int64_t)bytes); return r; };
+  double* dg = (double*)take(sizeof(double) * nmax2);
+  int* order_d = (int*)take(sizeof(int) * tmax);
+  double* mu = (double*)take(sizeof(double) * nmax2);
+  double* cst = (double*)take(sizeof(double) * (size_t)nmax2 * s);
+  const size_t tt = (size_t)tmax * tmax;
+  double* RA = (double*)take(sizeof(double) * tt);
+  double* RB = (double*)take(sizeof(double) * tt);
+  double* Gc = (double*)take(sizeof(double) * tt);
+  double* VG = (double*)take(sizeof(double) * tt);
+  double* R1 = (double*)take(sizeof(double) * tt);
+  double* R2 = (double*)take(sizeof(double) * tt);
+  double* WA = (double*)take(sizeof(double) * (size_t)tmax * nmax);
+  double* WBh = (double*)take(sizeof(double) * (size_t)tmax * nmax);
+  double* scl = (double*)take(sizeof(double) * 3 * (size_t)tmax);
+  double* sig_d = scl + 2 * (size_t)tmax;
+  const SmallB& sb = h->smallb;
+
+  // 1. eigenvalues and rows a of T_m (Alg. 5 steps 1-4), stacked with those of B
+  h->launches += launch_eigen_for_factor(h, 0, m, st);
+  double *la, *aa, *wa;
+  check_slot0(h, 0, &la, &aa, &wa);
+  k_smallb_stack<<<(NT + 127) / 128, 128, 0, st>>>(la, aa, N, sb.ups, sb.ctil, n2, s, mu, cst);
+  // 2. pivoted Cholesky of the stacked kernel
+  double teps = 0.0;
+  int rc_e = trunc_eps_of(h, la, sb.ups, N, &teps, st, n2);
+  if (rc_e != LYAP_OK) return rc_e;
+  const double eps_abs = teps * h->op[0].beta * sb.c2norm;
+  k_pivoted_cholesky<<<1, kPcThreads, 0, st>>>(mu, cst, NT, s, tmax, 1e-2 * eps_abs, f, dg);
+  h->launches += 2;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 2, f.tcount, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  const int tpc = h->flags_host[2];
+  if (tpc <= 0) {
+    *t_out = 0;
+    return LYAP_OK;
+  }
+  // 3. [Q L_A; P L_B]: the A rows by shifted band solves with T_m (every pivot, A or B side), the
+  //    B rows as P times the kernel's B rows at the pivots; then L_PP^{-T} on all rows
+  const int nthr = 64;
+  k_shifted_solves<<<(tpc + nthr - 1) / nthr, nthr, 0, st>>>(h->op[0].log, s, m, mu, cst, f, tmax, nmax, 0, 0, NT,
+                                                             h->flags);
+  k_smallb_brows<<<dim3((n2 + 127) / 128, tpc), 128, 0, st>>>(f, N, n2, s, mu, cst, f.M, tmax);
+  small_gemm(sb.P, n2, 0, f.M, tmax, 0, nullptr, nullptr, f.B + (size_t)N * tmax, tmax, n2, tpc, sb.d_n2, st);
+  k_apply_lpp<<<(NT + 127) / 128, 128, 0, st>>>(f, NT, NT, tmax);
+  // 4. R_A, R_B; G = R_A R_B^T; its one-sided Jacobi SVD
+  k_householder_r<<<2, 1024, 0, st>>>(f.L, NT, N, n2, f.tcount, WA, WBh, RA, RB, tmax);
+  small_gemm(RB, tmax, 0, RA, tmax, 1, nullptr, nullptr, Gc, tmax, tpc, tpc, f.tcount, st);
+  k_onesided_jacobi<<<1, 1024, 0, st>>>(Gc, VG, f.tcount, tmax, sig_d);
+  h->launches += 8;
+  std::vector<double> sig(tpc);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(sig.data(), sig_d, sizeof(double) * tpc, cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  // 5. truncation on the singular values, non-increasing (eq. 2.5 applied to the SVD of Y~)
+  std::vector<int> order(tpc);
+  for (int i = 0; i < tpc; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sig[x] > sig[y]; });
+  std::vector<double> tail(tpc + 1, 0.0);
+  for (int i = tpc - 1; i >= 0; --i) tail[i] = tail[i + 1] + sig[order[i]] * sig[order[i]];
+  int tk = 0;
+  while (tk < tpc && !(sqrt(tail[tk]) <= eps_abs)) ++tk;
+  while (tk > 0 && !(sig[order[tk - 1]] > 0.0)) --tk;
+  *t_out = tk;
+  if (tk > tcap) return LYAP_ERR_TCAP;
+  std::vector<double> sc(2 * (size_t)tmax, 0.0);
+  for (int c = 0; c < tk; ++c) {
+    const double sg = sig[order[c]];
+    sc[c] = 1.0 / sqrt(sg);
+    sc[tmax + c] = 1.0 / (sg * sqrt(sg));
+  }
+  if (tk > 0) {
+    LYAP_CUDA_TRY(cudaMemcpyAsync(order_d, order.data(), sizeof(int) * tk, cudaMemcpyHostToDevice, st));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(scl, sc.data(), sizeof(double) * 2 * tmax, cudaMemcpyHostToDevice, st));
+    // 6. R1 = R_B^T V_G,t Sigma^{-1/2}, R2 = R_A^T (G V_G)_t Sigma^{-3/2}; M1 = (Q L_A) R1, M2 = (P L_B) R2
+    small_gemm(RB, tmax, 1, VG, tmax, 1, order_d, scl, R1, tmax, tpc, tk, f.tcount, st);
+    small_gemm(RA, tmax, 1, Gc, tmax, 1, order_d, scl + tmax, R2, tmax, tpc, tk, f.tcount, st);
+    small_gemm(f.B, tmax, 0, R1, tmax, 0, nullptr, nullptr, f.M, tmax, N, tk, f.tcount, st);
+    small_gemm(f.B + (size_t)N * tmax, tmax, 0, R2, tmax, 0, nullptr, nullptr, f.M + (size_t)N * tmax, tmax, n2, tk,
+               f.tcount, st);
+    const int64_t tot = (int64_t)n2 * tk;
+    if (z_dtype == LYAP_F32)
+      k_copy_z2<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(f.M + (size_t)N * tmax, tmax, n2, tk,
+                                                                     (float*)Z2, ldz2);
+    else
+      k_copy_z2<double><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(f.M + (size_t)N * tmax, tmax, n2, tk,
+                                                                      (double*)Z2, ldz2);
+    h->launches += 5;
+  }
+  // 7. Z1 = V_m M1 by the second pass
+  int rc = second_pass(h, 0, f.M, tmax, tk, Z1, ldz1, z_dtype == LYAP_F32, st);
+  if (rc != LYAP_OK) return rc;
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  return LYAP_OK;
+}
+
 int run_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2, int z_dtype, int tcap, int* t_out,
                cudaStream_t st) {
+  if (h->plan.n2 > 0) return run_factor_smallb(h, Z1, ldz1, Z2, ldz2, z_dtype, tcap, t_out, st);
   if (h->plan.sylv) return run_factor_sylv(h, Z1, ldz1, Z2, ldz2, z_dtype, tcap, t_out, st);
   double* M = nullptr;
   int ldm = 0;

@@ -20,6 +20,8 @@ PRECISIONS = {"f64": L.LYAP_PREC_F64, "mixed": L.LYAP_PREC_MIXED, "f32x2": L.LYA
 class Solver:
     """One Lyapunov (B is None) or Sylvester solve through lyap_create/solve/factor.
 
+    A sparse B projects both operators (Sec. 5.1); a dense numpy B (small, n2 x n2) takes the
+    large-A / small-B path of Sec. 5.2 through lyap_smallb_create.
     ``inputs="device"`` uploads A, B, C with PyTorch before calling lyap_create;
     ``inputs="host"`` hands host pointers to lyap_create, which copies them.
     """
@@ -32,6 +34,7 @@ class Solver:
         self.torch = torch
         self.device = torch.device(device)
         self.sylv = B is not None
+        self.small_b = isinstance(B, np.ndarray)
         self.s = int(C1.shape[1])
         self.n1 = int(A.shape[0])
         self.n2 = int(B.shape[0]) if self.sylv else self.n1
@@ -51,9 +54,12 @@ class Solver:
         self._keep = []
         vdt = np.float32 if val_dtype == "f32" else np.float64
         self._csr = [self._make_csr(A, inputs, vdt)]
-        if self.sylv:
+        if self.sylv and not self.small_b:
             self._csr.append(self._make_csr(B, inputs, vdt))
-        self.ws_bytes = L.lyap_workspace_size(self._csr[0], self._csr[1] if self.sylv else None, self.s, opt)
+        if self.small_b:
+            self.ws_bytes = L.lyap_smallb_workspace_size(self._csr[0], self.n2, self.s, opt)
+        else:
+            self.ws_bytes = L.lyap_workspace_size(self._csr[0], self._csr[1] if self.sylv else None, self.s, opt)
         with torch.cuda.device(self.device):
             self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
             self.stream = torch.cuda.current_stream(self.device).cuda_stream
@@ -61,8 +67,14 @@ class Solver:
         cptr = [self._make_rhs(C1, inputs)]
         if self.sylv:
             cptr.append(self._make_rhs(C2, inputs))
-        self.h = L.lyap_create(self._csr[0], self._csr[1] if self.sylv else None, cptr[0], cptr[1] if self.sylv else None,
-                               c_mem, self.s, tol, opt, self.ws.data_ptr(), self.ws_bytes, self.stream)
+        if self.small_b:
+            bptr = self._make_rhs(B, inputs)
+            self.h = L.lyap_smallb_create(self._csr[0], bptr, self.n2, cptr[0], cptr[1], c_mem, self.s, tol, opt,
+                                          self.ws.data_ptr(), self.ws_bytes, self.stream)
+        else:
+            self.h = L.lyap_create(self._csr[0], self._csr[1] if self.sylv else None, cptr[0],
+                                   cptr[1] if self.sylv else None, c_mem, self.s, tol, opt, self.ws.data_ptr(),
+                                   self.ws_bytes, self.stream)
         self._keep.clear()
         self.status = None
         self.m = 0

@@ -161,3 +161,90 @@ def test_sylvester_host_outputs_equal_device_outputs(pkg):
     assert np.array_equal(Za1, Zb1) and np.array_equal(Za2, Zb2)
     a.close()
     b.close()
+
+
+# ---- large A, small dense B (Sec. 5.2, Alg. 5) ----
+from oracle import sylvester_small as osmall  # noqa: E402
+
+SMALLB_CASES = [  # (id, grid k, n2, s, precision, inputs)
+    ("k30_n2is1_s1", 30, 1, 1, "f64", "device"),
+    ("k30_n2_24_s2", 30, 24, 2, "f64", "device"),
+    ("k26_n2_97_s3_host", 26, 97, 3, "f64", "host"),
+    ("k33_n2_40_s4", 33, 40, 4, "f64", "device"),
+    ("k30_n2_57_s2_f32x2", 30, 57, 2, "f32x2", "device"),
+]
+
+
+@pytest.mark.parametrize("name,k,n2,s,precision,inputs", SMALLB_CASES, ids=[c[0] for c in SMALLB_CASES])
+def test_small_b_against_oracle(pkg, name, k, n2, s, precision, inputs):
+    """Whole runs of the small-B path: the history of Alg. 5's residual entry by entry
+    (|d| <= 1e-10 rel + 1e-14), the same m, X = Z1 Z2^T against the oracle's factors on random
+    probes (relative 1e-8), and the explicit residual of the GPU's factors, dense on the host."""
+    A = wl.laplacian_2d(k, shift=1.0)
+    B = wl.random_snd_dense(n2, seed=n2 + 3, lam_min=0.5, lam_max=40.0)
+    C1 = wl.rhs(k * k, s, seed=k + 1)
+    C2 = wl.rhs(n2, s, seed=k + 2)
+    tol = 1e-10
+    ref = osmall.solve(A, B, C1, C2, tol=tol, maxit=300)
+    sol = pkg.Solver(A, C1, B=B, C2=C2, tol=tol, maxit=300, precision=precision, trunc_eps=1e-12, inputs=inputs)
+    st = sol.solve()
+    assert st == 0 and ref.converged
+    assert sol.m == ref.m, (sol.m, ref.m)
+    h = sol.history()
+    d = np.abs(h - ref.history)
+    worst = float(np.max(d / (1e-10 * ref.history + 1e-14)))
+    print(f"{name}: m={sol.m} max |d| {d.max():.3e} worst/bound {worst:.3f}")
+    assert worst <= 1.0
+    Z1, Z2 = sol.factor(out="host" if inputs == "host" else "device")
+    if not isinstance(Z1, np.ndarray):
+        Z1, Z2 = Z1.cpu().numpy(), Z2.cpu().numpy()
+    Z1o, Z2o, _ = osmall.factor(A, C1, C2, ref, trunc_eps=1e-12)
+    assert Z1.shape[1] == Z2.shape[1] and abs(Z1.shape[1] - Z1o.shape[1]) <= 1
+    assert _xprobe(Z1, Z2, Z1o, Z2o) <= 1e-8
+    X = Z1 @ Z2.T
+    R = A @ X + X @ B + C1 @ C2.T
+    rel = np.linalg.norm(R) / (np.linalg.norm(C1) * np.linalg.norm(C2))
+    Xo = Z1o @ Z2o.T
+    relo = np.linalg.norm(A @ Xo + Xo @ B + C1 @ C2.T) / (np.linalg.norm(C1) * np.linalg.norm(C2))
+    print(f"{name}: t={Z1.shape[1]} (oracle {Z1o.shape[1]}), explicit residual {rel:.3e} (oracle {relo:.3e})")
+    # truncating Y~ by trunc_eps adds at most (||A|| + ||B||) trunc_eps to the residual (eq. 2.5)
+    bound = tol + (abs(A).sum(axis=1).max() + np.abs(B).sum(axis=1).max()) * 1e-12
+    assert abs(rel - relo) <= 1e-3 * relo + 1e-13
+    assert rel <= bound, (rel, bound)
+    sol.close()
+
+
+def test_small_b_check_on_gpu_T(pkg):
+    """The check alone: Alg. 5 evaluated by the oracle on the GPU's own T_m (from the logged
+    coefficients) against the GPU history at several m, |d rel| <= 1e-10 max(rel, 1e-2) + 1e-13."""
+    k, n2, s = 28, 33, 3
+    A = wl.laplacian_2d(k, shift=1.0)
+    B = wl.random_snd_dense(n2, seed=5, lam_min=0.5, lam_max=40.0)
+    C1, C2 = wl.rhs(k * k, s, seed=7), wl.rhs(n2, s, seed=8)
+    sol = pkg.Solver(A, C1, B=B, C2=C2, tol=0.0, maxit=40)
+    sol.solve()
+    hist = sol.history()
+    ups, P = osmall.eig_B(B)
+    bb = np.linalg.norm(C1) * np.linalg.norm(C2)
+    worst = 0.0
+    for m in (1, 2, 7, 19, 40):
+        ab, g, tn = sol.projected(m, 0)
+        lam, Q = sla.eig_banded(ab, lower=True)
+        rel = osmall.cheap_residual(lam, Q, ups, P, g, C2, tn, s) / bb
+        worst = max(worst, abs(hist[m - 1] - rel) / (1e-10 * max(rel, 1e-2) + 1e-13))
+    assert worst <= 1.0, worst
+    sol.close()
+
+
+def test_small_b_rejects_bad_arguments(pkg):
+    from paper_1602_05033_gb300 import _lib as L
+
+    A = wl.laplacian_2d(10, shift=1.0)
+    B = wl.random_snd_dense(5, seed=1)
+    C1, C2 = wl.rhs(100, 2, 1), wl.rhs(5, 2, 2)
+    with pytest.raises(L.LyapError):
+        pkg.Solver(A, C1, B=B, C2=C2, maxit=2)  # n2 = 5 > s maxit = 4
+    bad = wl.random_snd_dense(5, seed=2)
+    bad[0, 0] = np.nan
+    with pytest.raises(L.LyapError):
+        pkg.Solver(A, C1, B=bad, C2=C2, maxit=50)
