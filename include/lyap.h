@@ -59,6 +59,9 @@ enum { LYAP_MEM_DEVICE = 0, LYAP_MEM_HOST = 1 }; /* where a pointer lives       
 /* bulk number type of the basis, the SpMM and the row arithmetic of a solve */
 enum { LYAP_PREC_F64 = 0, LYAP_PREC_MIXED = 1, LYAP_PREC_F32X2 = 2 };
 
+/* lyap_options.check_every: the adaptive check schedule */
+enum { LYAP_CHECK_ADAPTIVE = -1 };
+
 /* Sparse matrix in CSR form, read only during lyap_workspace_size and lyap_create.
  * Column indices of each row need not be sorted; the matrix must be symmetric
  * (the method relies on it, Sec. 2) -- symmetry is not checked. */
@@ -75,7 +78,12 @@ typedef struct {
 typedef struct {
   int maxit;             /* iteration cap (default 1000)                                    */
   int check_every;       /* d: test the residual at every d-th space dimension (Sec. 6);
-                            default 1                                                      */
+                            default 1.  LYAP_CHECK_ADAPTIVE: every m <= 8, then every 8th m
+                            until the residual trend (a line through log10 of the last 16
+                            checked residuals) predicts tol within reach, then every m; when a
+                            check meets tol, the m skipped since the last failing check are
+                            checked too, and m is the first of them meeting tol.  Skipped
+                            entries of the history are NaN                                   */
   double trunc_eps;      /* truncation threshold eps of the reduced solution (eq. 2.5), relative
                             to ||C1||_F ||C2||_F: the discarded eigenvalues (singular values for
                             Sylvester) have a tail of Frobenius norm <= eps ||C1|| ||C2||.
@@ -186,7 +194,7 @@ int lyap_factor(lyap_handle* h, void* Z1, int64_t ldz1, void* Z2, int64_t ldz2,
  * out[5] block Lanczos sweeps of the last solve (sum over chunks),
  * out[6] number of kernels the library launched since lyap_create,
  * out[7] block Lanczos steps the last solve ran past its converged m (the speculative chunk),
- * out[8] convergence checks it evaluated past that m.
+ * out[8] convergence checks it evaluated past that m, out[9] convergence checks it evaluated.
  * The chunk of steps launched ahead of its checks is sized from the residual history known
  * so far: log10 of the residual extrapolated over the last 16 checked m to the steps still
  * needed, times 1.25, between 4 and twice the previous chunk (at most check_batch); the

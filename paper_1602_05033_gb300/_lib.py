@@ -27,6 +27,7 @@ LYAP_ERR_EIGEN = 10
 LYAP_F64, LYAP_F32 = 0, 1
 LYAP_MEM_DEVICE, LYAP_MEM_HOST = 0, 1
 LYAP_PREC_F64, LYAP_PREC_MIXED, LYAP_PREC_F32X2 = 0, 1, 2
+LYAP_CHECK_ADAPTIVE = -1
 
 # every symbol include/lyap.h declares
 EXPORTED = (
@@ -259,8 +260,8 @@ def lyap_projected_matrix(h: int, op: int, m: int, s: int):
 
 
 def lyap_phase_times(h: int):
-    out = (ct.c_double * 9)()
-    load().lyap_phase_times(ct.c_void_p(h), out, 9)
+    out = (ct.c_double * 10)()
+    load().lyap_phase_times(ct.c_void_p(h), out, 10)
     return list(out)
 
 

@@ -55,7 +55,7 @@ lyap_options resolve(const lyap_options* opt) {
   lyap_default_options(&o);
   if (opt) {
     if (opt->maxit > 0) o.maxit = opt->maxit;
-    if (opt->check_every > 0) o.check_every = opt->check_every;
+    if (opt->check_every > 0 || opt->check_every == LYAP_CHECK_ADAPTIVE) o.check_every = opt->check_every;
     o.trunc_eps = opt->trunc_eps > 0 ? opt->trunc_eps : 0.0;
     o.precision = opt->precision;
     if (opt->sell_sigma > 0) o.sell_sigma = opt->sell_sigma;
@@ -401,19 +401,13 @@ int round_status(lyap_handle* h) {
   return rc;
 }
 
-// Size of the next chunk of block Lanczos steps (launched ahead of its checks).  The steps of a
-// chunk run while the checks of the previous one are evaluated; the checks that find convergence
-// leave the chunk after it discarded.  From the history known on the host, log10 of the residual
-// is extrapolated linearly over the last (up to 16) checked m to the number of steps still needed
-// beyond those already launched; the next chunk covers 1.25 times that, between 4 steps and
-// min(2 x the previous chunk, the check batch).  The convergence test itself is unchanged: every
-// m up to the last launched step is still checked and the first m with rel <= tol is the result.
-int next_chunk(const double* hist, int known, int launched, int prev, int cap, double tol) {
-  const int hi_cap = std::min(2 * prev, cap);
-  const int lo_cap = std::min(4, hi_cap);
+// Predicted first m with a residual <= tol: least-squares line through log10 of the last 16
+// residuals on record (m <= known; skipped m are NaN), extrapolated to log10(tol).  Returns
+// false without a prediction (fewer than 4 values, a slope >= 0, or tol <= 0).
+bool predict_converged_m(const double* hist, int known, double tol, double* m_star) {
   int n = 0;
   double sx = 0, sy = 0, sxx = 0, sxy = 0;
-  for (int m = std::max(1, known - 15); m <= known; ++m) {
+  for (int m = known; m >= 1 && n < 16; --m) {
     const double v = hist[m - 1];
     if (!(v > 0.0) || !isfinite(v)) continue;
     const double y = log10(v);
@@ -423,15 +417,51 @@ int next_chunk(const double* hist, int known, int launched, int prev, int cap, d
     sxy += m * y;
     ++n;
   }
-  if (n < 4 || !(tol > 0.0)) return hi_cap;
+  if (n < 4 || !(tol > 0.0)) return false;
   const double den = n * sxx - sx * sx;
   const double slope = den != 0.0 ? (n * sxy - sx * sy) / den : 0.0;
-  if (!(slope < 0.0)) return hi_cap;
+  if (!(slope < 0.0)) return false;
   const double icpt = (sy - slope * sx) / n;
-  const double m_star = (log10(tol) - icpt) / slope;  // predicted first converged m
+  *m_star = (log10(tol) - icpt) / slope;
+  return isfinite(*m_star);
+}
+
+// Size of the next chunk of block Lanczos steps (launched ahead of its checks).  The steps of a
+// chunk run while the checks of the previous one are evaluated; the checks that find convergence
+// leave the chunk after it discarded.  From the history known on the host, the number of steps
+// still needed beyond those already launched is predicted (above); the next chunk covers 1.25
+// times that, between 4 steps and min(2 x the previous chunk, the check batch).  The chunk size
+// does not change the convergence test: the first checked m with rel <= tol is the result.
+int next_chunk(const double* hist, int known, int launched, int prev, int cap, double tol) {
+  const int hi_cap = std::min(2 * prev, cap);
+  const int lo_cap = std::min(4, hi_cap);
+  double m_star = 0.0;
+  if (!predict_converged_m(hist, known, tol, &m_star)) return hi_cap;
   const double need = 1.25 * (m_star - launched);
   if (!(need < hi_cap)) return hi_cap;
   return std::max(lo_cap, (int)ceil(need));
+}
+
+// The m of (from, upto] whose residual is evaluated.  A period d >= 1 takes the multiples of d
+// (Sec. 6).  The adaptive schedule takes every m <= kDenseHead, every kSparseStride-th m
+// after that, and every m from the predicted first converged m minus a margin on: the margin is
+// 2 plus a quarter of the distance the prediction extrapolates over, so a prediction made from
+// far away opens the dense window early.
+constexpr int kDenseHead = 8;
+constexpr int kSparseStride = 8;
+void pick_checks(const lyap_handle* h, int from, int upto, int known, std::vector<int>& out) {
+  out.clear();
+  const int d = h->opt.check_every;
+  if (d >= 1) {
+    for (int m = from + 1; m <= upto; ++m)
+      if (m % d == 0) out.push_back(m);
+    return;
+  }
+  double m_star = 0.0;
+  const bool pred = predict_converged_m(h->hist_host, known, h->tol, &m_star);
+  const double dense_from = pred ? m_star - (2.0 + 0.25 * std::max(0.0, m_star - known)) : 1e300;
+  for (int m = from + 1; m <= upto; ++m)
+    if (m <= kDenseHead || m % kSparseStride == 0 || (double)m >= dense_from) out.push_back(m);
 }
 
 extern "C" {
@@ -571,6 +601,22 @@ int lyap_solve(lyap_handle* h, void* stream) {
         h->launches += launch_lanczos_step(h->op[k], s, p.bulk, p.sweep_grid, p.sweep_grid_b, j, fw, st);
     cudaEventRecord(c_end[c & 1], st);
   };
+  // checks in batches: as many as fit in the check area with slots sized by the batch's largest m
+  std::vector<int> todo;
+  std::vector<unsigned char> was_checked((size_t)p.maxit + 1, 0);
+  int nchecks = 0;
+  auto launch_checks = [&](const std::vector<int>& ms) {
+    size_t i = 0;
+    while (i < ms.size()) {
+      size_t n = std::min(ms.size() - i, (size_t)p.check_batch_req);
+      while (n > 1 && (size_t)(1 + p.sylv) * n * check_slot_bytes(s, batch_nmax(s, ms[i + n - 1])) > p.check_bytes)
+        --n;
+      h->launches += launch_check_list(h, ms.data() + i, (int)n, sd);
+      for (size_t k = i; k < i + n; ++k) was_checked[ms[k]] = 1;
+      i += n;
+    }
+    nchecks += (int)ms.size();
+  };
   int chunk = std::min(4, p.check_batch_req);
   int done = std::min(p.maxit, chunk);  // last step of the chunk being checked
   int checked = 0;                      // largest m already checked
@@ -585,15 +631,9 @@ int lyap_solve(lyap_handle* h, void* stream) {
     LYAP_CUDA_TRY(cudaStreamWaitEvent(sd, c_end[c & 1], 0));
     cudaEventRecord(h->ev[5], sd);
     const int first_new = checked + 1;
-    while (checked < done) {
-      // as many checks as fit in the check area with slots sized by the batch's largest m
-      const int lo = checked + 1;
-      int hi = std::min(done, checked + p.check_batch_req);
-      while (hi > lo && (size_t)(1 + p.sylv) * (hi - lo + 1) * check_slot_bytes(s, batch_nmax(s, hi)) > p.check_bytes)
-        --hi;
-      h->launches += launch_check_batch(h, lo, hi, sd);
-      checked = hi;
-    }
+    pick_checks(h, checked, done, known, todo);
+    launch_checks(todo);
+    checked = done;
     cudaEventRecord(h->ev[4], sd);
     LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sd));
     LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host + 3, cw + (c & 1), sizeof(int), cudaMemcpyDeviceToHost, sd));
@@ -620,6 +660,27 @@ int lyap_solve(lyap_handle* h, void* stream) {
     rc = round_status(h);
     if (rc != LYAP_OK) break;
     if (h->flags_host[1] != INT_MAX) {
+      // the adaptive schedule may have skipped m just before the first converged one: check
+      // them, so that m is the first converged m after the last check that failed the test (a
+      // period d keeps the multiples of d, Sec. 6)
+      int mc = h->flags_host[1], last = mc - 1;
+      while (last >= 1 && !was_checked[last]) --last;
+      todo.clear();
+      if (h->opt.check_every == LYAP_CHECK_ADAPTIVE)
+        for (int m = last + 1; m < mc; ++m) todo.push_back(m);
+      if (!todo.empty()) {
+        cudaEventRecord(h->ev[5], sd);
+        launch_checks(todo);
+        cudaEventRecord(h->ev[4], sd);
+        LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sd));
+        LYAP_CUDA_TRY(cudaStreamSynchronize(sd));
+        float bf = 0.f;
+        cudaEventElapsedTime(&bf, h->ev[5], h->ev[4]);
+        t_check += bf;
+        h->flags_host[0] |= h->flags_host[3];
+        rc = round_status(h);
+        if (rc != LYAP_OK) break;
+      }
       m_final = h->flags_host[1];
       result = LYAP_OK;
       break;
@@ -643,6 +704,9 @@ int lyap_solve(lyap_handle* h, void* stream) {
   h->times_ms[4] = t_check;
   h->times_ms[5] = t_lanczos;
   h->checked = checked;
+  h->nchecks = nchecks;
+  h->checks_past = 0;
+  for (int m = h->m + 1; m <= p.maxit; ++m) h->checks_past += was_checked[m];
   return result;
 }
 
@@ -731,7 +795,8 @@ int lyap_phase_times(lyap_handle* h, double* out, int cap) {
   if (cap > 3) out[3] = (double)h->lanczos_done;
   if (cap > 6) out[6] = (double)h->launches;
   if (cap > 7) out[7] = (double)(h->lanczos_done - h->m);  // steps run past the converged m
-  if (cap > 8) out[8] = (double)(h->checked - h->m);       // checks evaluated past it
+  if (cap > 8) out[8] = (double)h->checks_past;            // checks evaluated past it
+  if (cap > 9) out[9] = (double)h->nchecks;                // checks evaluated in all
   return LYAP_OK;
 }
 

@@ -25,6 +25,7 @@
 // Every fp64 step runs one thread per eigenpair across the whole GPU.  Reductions
 // are in a fixed order.
 #include "common.cuh"
+#include "ff.cuh"
 
 #include <float.h>
 #include <limits.h>
@@ -36,6 +37,7 @@
 namespace {
 
 constexpr int kMaxCluster = 16;
+constexpr int kMaxChecks = 256;  // checks per batch (the check_batch option is capped there)
 constexpr int kClusterBlocks = 16;  // blocks per check of k_invit_clusters
 constexpr int kClusterWarps = 64;   // warps per check of k_invit_clusters (4 per block)
 // Members of a group of fp32 estimates larger than this get fp64 estimates by multisection with
@@ -60,6 +62,14 @@ constexpr int kMaxIters = 12; // fp64 inverse iterations (Rayleigh-quotient shif
 constexpr int kMaxRounds = 10;  // cluster rounds (Rayleigh-Ritz between them); converged clusters stop early
 constexpr double kSettle = 1e-12;  // |change of the Rayleigh quotient| / ||T|| after which one more step is run
 constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||T||
+#ifndef LYAP_REFINE_RES
+#define LYAP_REFINE_RES 1e-10
+#endif
+#ifndef LYAP_PAIR_INVIT
+#define LYAP_PAIR_INVIT 1
+#endif
+constexpr double kRefineRes = LYAP_REFINE_RES;  // width at which multisection stops, relative to ||T||
+constexpr bool kPairInvit = LYAP_PAIR_INVIT;    // singleton iteration in float pairs (else fp64)
 
 struct Slot {
   double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] fp32 cluster
@@ -76,12 +86,13 @@ struct Slot {
   double* U;     // nmax x (2s+1) x nmax, [k][e][i]: row k of the LU factor of thread i
   double* etol;  // nmax   cluster tolerance of each estimate (fp32 one, or fp64 one once refined)
   double* Xc;    // nmax x nmax, [i][k]: eigenvector i of a cluster member, contiguous
+  float2* Tbf;   // (s+1) x N   the fp64 band as float pairs (hi, lo), same indexing as Tb
 };
 
 __host__ __device__ constexpr size_t slot_doubles(int s, int nmax) {
   return 8 + ((size_t)(s + 1) * nmax + 1) / 2 /* Tb32 */ + 3 * (size_t)nmax + (size_t)(s + 1) * nmax + 2 * (size_t)s * nmax +
          ((size_t)nmax + 16) /* cluster list */ + (size_t)nmax * nmax + (size_t)(2 * s + 1) * nmax * nmax +
-         (size_t)nmax /* etol */ + (size_t)nmax * nmax /* Xc */;
+         (size_t)nmax /* etol */ + (size_t)nmax * nmax /* Xc */ + (size_t)(s + 1) * nmax /* Tbf */;
 }
 
 __device__ inline Slot get_slot(double* base, int s, int nmax, int idx) {
@@ -100,7 +111,8 @@ __device__ inline Slot get_slot(double* base, int s, int nmax, int idx) {
   sl.X = p; p += (size_t)nmax * nmax;
   sl.U = p; p += (size_t)(2 * s + 1) * nmax * nmax;
   sl.etol = p; p += nmax;
-  sl.Xc = p;
+  sl.Xc = p; p += (size_t)nmax * nmax;
+  sl.Tbf = reinterpret_cast<float2*>(p);
   return sl;
 }
 
@@ -109,14 +121,11 @@ struct CheckArgs {
   double* slots;      // slot array for this operator
   int s;
   int nmax;
-  int m_lo;           // slot c <-> m = m_lo + c
   int nchk;
-  int every;          // check period d
   int* flags;
   int* chk_err;       // per-m error bits of the check (index m - 1)
+  int ms[kMaxChecks]; // slot c holds the check at m = ms[c]
 };
-
-__device__ inline bool checked(const CheckArgs& g, int m) { return (m % g.every) == 0; }
 
 // T_m[i][c] for i >= c, i - c <= s: symmetric part of tau_jj on the diagonal blocks,
 // tau_{j+1,j} below them (Sec. 2)
@@ -146,8 +155,7 @@ __device__ __forceinline__ double tband(const double* __restrict__ Tb, int N, in
 __global__ void __launch_bounds__(256) k_setup_band(CheckArgs g) {
   __shared__ double red[3][8];
   const int c_idx = blockIdx.x;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int s = g.s, N = s * m;
   Slot sl = get_slot(g.slots, s, g.nmax, c_idx);
   double mx = 0.0, lo = INFINITY, hi = -INFINITY;
@@ -155,6 +163,8 @@ __global__ void __launch_bounds__(256) k_setup_band(CheckArgs g) {
     const int d = t / N, c = t % N;
     const double v = c + d < N ? tval(g.log, s, c + d, c) : 0.0;
     sl.Tb[t] = v;
+    const ff vf = ff_from_double(v);
+    sl.Tbf[t] = make_float2(vf.hi, vf.lo);
     mx = fmax(mx, fabs(v));
   }
   __syncthreads();
@@ -247,33 +257,43 @@ __device__ int band_sturm32(const float* __restrict__ Tb, int N, float x, float 
   return cnt;
 }
 
-// 2. fp32 bisection of every eigenvalue on the band itself, one thread per eigenvalue index
+// 2. fp32 multisection of every eigenvalue on the band itself, one warp per eigenvalue index:
+// the 32 lanes count the eigenvalues below 32 interior points of the bracket at once, so a round
+// narrows it 33-fold (about 5 rounds from the Gershgorin interval to fp32 resolution, where
+// bisection takes 24 dependent Sturm counts)
 template <int S>
 __global__ void k_bisect_band32(CheckArgs g) {
   const int c_idx = blockIdx.y;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int N = S * m;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // one index per warp
   if (i >= N) return;
   Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   float lo = (float)sl.hdr[0], hi = (float)sl.hdr[1];
   const float pivmin = 16.f * FLT_MIN;
-  for (int it = 0; it < 64; ++it) {
-    const float mid = 0.5f * (lo + hi);
-    if (!(hi - lo > 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi))) || mid <= lo || mid >= hi) break;
-    if (band_sturm32<S>(sl.Tb32, N, mid, pivmin) <= i) lo = mid;
-    else hi = mid;
+  const unsigned full = 0xffffffffu;
+  for (int round = 0; round < 16; ++round) {
+    if (!(hi - lo > 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)))) break;
+    const float x = lo + (hi - lo) * ((float)(lane + 1) / 33.f);
+    const int c = band_sturm32<S>(sl.Tb32, N, x, pivmin);
+    const unsigned below = __ballot_sync(full, c <= i);
+    const int top = below ? 31 - __clz(below) : -1;  // last point at or below lambda_i
+    const float nlo = __shfl_sync(full, x, top < 0 ? 0 : top);
+    const float nhi = __shfl_sync(full, x, top < 31 ? top + 1 : 31);
+    const float lo2 = top < 0 ? lo : nlo, hi2 = top < 31 ? nhi : hi;
+    if (!(hi2 - lo2 < hi - lo)) break;  // no progress at this resolution
+    lo = lo2;
+    hi = hi2;
   }
-  sl.est[i] = 0.5 * ((double)lo + (double)hi) * sl.hdr[3];
+  if (lane == 0) sl.est[i] = 0.5 * ((double)lo + (double)hi) * sl.hdr[3];
 }
 
 // 2b. per-estimate cluster tolerance: members of fp32 groups larger than kRefineAt get the
 // fp64 grouping tolerance (and are refined by 2c), all others the fp32 one
 __global__ void k_mark_refine(CheckArgs g) {
   const int c_idx = blockIdx.x;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int N = g.s * m;
   Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
   const double tol32 = sl.hdr[4];
@@ -339,17 +359,63 @@ __device__ int band_sturm(const double* __restrict__ Tb, int N, double x, double
   return cnt;
 }
 
-// 2c. fp64 multisection of the marked estimates, one warp per eigenvalue index: the 32 lanes
-// count the eigenvalues below 32 interior points of the bracket at once (Sturm counts on the fp64
-// band), so a round narrows it 33-fold; started from the fp32 estimate +- the fp32 grouping
+// band_sturm in float pairs on the pair band: the same recurrence with every operation on the
+// fp32 pipe (about 48 significant bits; the counts resolve eigenvalues to ~1e-13 ||T||)
+template <int S>
+__device__ int band_sturm_ff(const float2* __restrict__ Tb, int N, ff x, float pivmin) {
+  ff dinv[S], L[S][S];
+#pragma unroll
+  for (int r = 0; r < S; ++r) {
+    dinv[r] = ff_make(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < S; ++t) L[r][t] = ff_make(0.f, 0.f);
+  }
+  const ff nx = ff_make(-x.hi, -x.lo);
+  const ff one = ff_make(1.f, 0.f);
+  int cnt = 0;
+  for (int k = 0; k < N; ++k) {
+    ff w[S], nl[S];
+#pragma unroll
+    for (int r = S - 1; r >= 0; --r) {
+      const int j = k - 1 - r;
+      const float2 t = j >= 0 ? __ldg(Tb + (size_t)(r + 1) * N + j) : make_float2(0.f, 0.f);
+      ff v = ff_make(t.x, t.y);
+#pragma unroll
+      for (int q = S - 1; q > r; --q) ff_sub_acc(v, w[q], L[r][q - r - 1]);
+      w[r] = ff_norm(v);
+      nl[r] = ff_mul(w[r], dinv[r]);
+    }
+    const float2 t = __ldg(Tb + k);
+    ff dk = ff_add(ff_make(t.x, t.y), nx);
+#pragma unroll
+    for (int r = 0; r < S; ++r) ff_sub_acc(dk, nl[r], w[r]);
+    dk = ff_norm(dk);
+    if (fabsf(dk.hi) <= pivmin) dk = ff_make(-pivmin, 0.f);
+    cnt += dk.hi < 0.f;
+#pragma unroll
+    for (int r = S - 1; r > 0; --r) {
+      dinv[r] = dinv[r - 1];
+#pragma unroll
+      for (int t2 = 0; t2 < S; ++t2) L[r][t2] = L[r - 1][t2];
+    }
+    dinv[0] = ff_div(one, dk);
+#pragma unroll
+    for (int t2 = 0; t2 < S; ++t2) L[0][t2] = nl[t2];
+  }
+  return cnt;
+}
+
+// 2c. multisection of the marked estimates, one warp per eigenvalue index: the 32 lanes count the
+// eigenvalues below 32 interior points of the bracket at once (float-pair Sturm counts on the
+// pair band), so a round narrows it 33-fold; started from the fp32 estimate +- the fp32 grouping
 // tolerance (widened to the Gershgorin interval if the counts show the eigenvalue outside it),
-// stopped at 2 eps64 ||T||.  The lanes share the fp64 pipe's issue slots, which a single thread
-// would leave idle.
+// stopped at kRefineRes ||T||: four rounds.  The estimate only has to separate eigenvalues at the
+// fp64 grouping tolerance (>= 1e-6 ||T||) and to serve as a shift; the eigenvalue itself is the
+// Rayleigh quotient of the converged vector.
 template <int S>
 __global__ void k_refine64(CheckArgs g, int round) {
   const int c_idx = blockIdx.y;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int N = S * m;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // one index per warp
@@ -361,19 +427,19 @@ __global__ void k_refine64(CheckArgs g, int round) {
   const double sc = sl.hdr[3];
   const double glo = sl.hdr[0] * sc, ghi = sl.hdr[1] * sc;
   const double span = fmax(fabs(glo), fabs(ghi));
-  const double pivmin = DBL_MIN * fmax(1.0, span * span);
+  const float pivmin = 1e-30f * (float)fmax(1.0, span * span);
   const unsigned full = 0xffffffffu;
   double lo = sl.est[i] - tol32, hi = sl.est[i] + tol32;
   {
-    const int c = lane < 2 ? band_sturm<S>(sl.Tb, N, lane == 0 ? lo : hi, pivmin) : 0;
+    const int c = lane < 2 ? band_sturm_ff<S>(sl.Tbf, N, ff_from_double(lane == 0 ? lo : hi), pivmin) : 0;
     const int clo = __shfl_sync(full, c, 0), chi = __shfl_sync(full, c, 1);
     if (clo > i) lo = glo;
     if (chi <= i) hi = ghi;
   }
   for (int round = 0; round < 40; ++round) {
-    if (!(hi - lo > 2.0 * DBL_EPSILON * span)) break;
+    if (!(hi - lo > kRefineRes * span)) break;
     const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
-    const int c = band_sturm<S>(sl.Tb, N, x, pivmin);
+    const int c = band_sturm_ff<S>(sl.Tbf, N, ff_from_double(x), pivmin);
     // lambda_i >= x exactly when fewer than i + 1 eigenvalues lie below x
     const unsigned below = __ballot_sync(full, c <= i);
     const int top = below ? 31 - __clz(below) : -1;  // last point at or below lambda_i
@@ -570,6 +636,277 @@ __device__ double normalize_col(double* X, size_t ld, int N, int i) {
 
 
 
+// ---- singleton inverse iteration in float pairs ------------------------------------------------
+// The vector lives in the eigenvector array as pairs (hi, lo in the 8 bytes of an entry) until it
+// has converged; then its first and last S rows are rewritten as doubles for write_aw.  fp64 runs
+// at 1/64 of the fp32 rate on this GPU, so the pair arithmetic (about 48 significant bits, a few
+// fp32 operations per pair operation) finishes the same iteration several times sooner.
+template <typename R>
+__device__ __forceinline__ R from_ff(ff v);
+template <>
+__device__ __forceinline__ float from_ff<float>(ff v) { return v.hi; }
+template <>
+__device__ __forceinline__ fd from_ff<fd>(ff v) { return fd(v); }
+__device__ __forceinline__ float2 to_f2(float x) { return make_float2(x, 0.f); }
+__device__ __forceinline__ float2 to_f2(fd x) { return make_float2(x.v.hi, x.v.lo); }
+__device__ __forceinline__ float lead(float x) { return x; }
+__device__ __forceinline__ float lead(fd x) { return x.v.hi; }
+
+// (T_m - sigma I)[r][c] from the pair band (nsig = -sigma), zero outside the matrix
+template <int S>
+__device__ __forceinline__ ff mval_ff(const float2* __restrict__ Tb, int N, ff nsig, int r, int c) {
+  if (r >= N || c >= N || c < 0) return ff_make(0.f, 0.f);
+  const int d = r > c ? r - c : c - r;
+  if (d > S) return ff_make(0.f, 0.f);
+  const float2 t = __ldg(Tb + (size_t)d * N + (r < c ? r : c));
+  const ff v = ff_make(t.x, t.y);
+  return r == c ? ff_add(v, nsig) : v;
+}
+
+// X[:, col] <- (T_m - sigma I)^{-1} (xscale X[:, col]) with X holding pairs: the banded LU with
+// partial pivoting of solve1, in fp32 (R = float: leading parts only) or in pairs (R = fd).
+// Returns max_k |x_k| (leading parts); not finite if the solve overflowed.
+template <int S, typename R>
+__device__ float solve_pair(const float2* __restrict__ Tb, int N, ff sigma, R tiny, ff xscale, float2* __restrict__ X,
+                            size_t ld, int col, R* __restrict__ U, int tid, size_t ldu) {
+  constexpr int W = 2 * S + 1;
+  constexpr size_t us = sizeof(double) / sizeof(R);
+  const ff nsig = ff_make(-sigma.hi, -sigma.lo);
+  const R xsc = from_ff<R>(xscale);
+  auto ldx = [&](int r) -> R {
+    const float2 v = X[(size_t)r * ld + col];
+    return from_ff<R>(ff_make(v.x, v.y)) * xsc;
+  };
+  R win[S + 1][W];
+  R yw[S + 1];
+#pragma unroll
+  for (int r = 0; r <= S; ++r) {
+#pragma unroll
+    for (int c = 0; c < W; ++c) win[r][c] = from_ff<R>(mval_ff<S>(Tb, N, nsig, r, c));
+    yw[r] = r < N ? ldx(r) : R(0);
+  }
+  for (int k = 0; k < N; ++k) {
+    if (k + S + 1 + kPf < N) prefetch_l2(X + (size_t)(k + S + 1 + kPf) * ld + col);
+    const int nr = min(S, N - 1 - k);
+    R best = fabs(win[0][0]);
+    int p = 0;
+#pragma unroll
+    for (int r = 1; r <= S; ++r) {
+      const R a = fabs(win[r][0]);
+      if (r <= nr && a > best) { best = a; p = r; }
+    }
+#pragma unroll
+    for (int r = 1; r <= S; ++r) {
+      const bool sw = p == r;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const R a = win[0][c], b = win[r][c];
+        win[0][c] = sw ? b : a;
+        win[r][c] = sw ? a : b;
+      }
+      const R a = yw[0], b = yw[r];
+      yw[0] = sw ? b : a;
+      yw[r] = sw ? a : b;
+    }
+    if (fabs(win[0][0]) < tiny) win[0][0] = lead(win[0][0]) < 0.f ? -tiny : tiny;
+    const R pinv = R(1) / win[0][0];
+#pragma unroll
+    for (int r = 1; r <= S; ++r) {
+      const R l = r <= nr ? win[r][0] * pinv : R(0);
+#pragma unroll
+      for (int c = 1; c < W; ++c) win[r][c] = fma(-l, win[0][c], win[r][c]);
+      yw[r] = fma(-l, yw[0], yw[r]);
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) U[(((size_t)k * W + c) * ldu + tid) * us] = win[0][c];
+    X[(size_t)k * ld + col] = to_f2(yw[0]);
+#pragma unroll
+    for (int r = 0; r < S; ++r) {
+#pragma unroll
+      for (int c = 0; c < W - 1; ++c) win[r][c] = win[r + 1][c + 1];
+      win[r][W - 1] = R(0);
+      yw[r] = yw[r + 1];
+    }
+    const int rn = k + S + 1;
+#pragma unroll
+    for (int c = 0; c < W; ++c) win[S][c] = from_ff<R>(mval_ff<S>(Tb, N, nsig, rn, k + 1 + c));
+    yw[S] = rn < N ? ldx(rn) : R(0);
+  }
+  float amax = 0.f;
+  R xs[W - 1];
+#pragma unroll
+  for (int e = 0; e < W - 1; ++e) xs[e] = R(0);
+  for (int k = N - 1; k >= 0; --k) {
+    if (k >= kPf) {
+      const int kp = k - kPf;
+      prefetch_l2(X + (size_t)kp * ld + col);
+#pragma unroll
+      for (int e = 0; e < W; ++e) prefetch_l2(U + (((size_t)kp * W + e) * ldu + tid) * us);
+    }
+    const float2 xv = X[(size_t)k * ld + col];
+    R t = from_ff<R>(ff_make(xv.x, xv.y));
+#pragma unroll
+    for (int e = 1; e < W; ++e) t = fma(-U[(((size_t)k * W + e) * ldu + tid) * us], xs[e - 1], t);
+    const R xk = t / U[(((size_t)k * W) * ldu + tid) * us];
+    X[(size_t)k * ld + col] = to_f2(xk);
+    amax = fmaxf(amax, fabsf(lead(xk)));
+    if (!isfinite(lead(xk))) amax = INFINITY;
+#pragma unroll
+    for (int e = W - 2; e > 0; --e) xs[e] = xs[e - 1];
+    xs[0] = xk;
+  }
+  return amax;
+}
+
+// x^T T x and x^T x (pairs) for column col of the pair vectors, one pass with a window of 2S+1
+template <int S>
+__device__ void rq_pair(const float2* __restrict__ Tb, int N, const float2* __restrict__ X, size_t ld, int col, ff* num,
+                        ff* den) {
+  ff xw[2 * S + 1];
+  auto ldv = [&](int r) -> ff {
+    if (r < 0 || r >= N) return ff_make(0.f, 0.f);
+    const float2 v = X[(size_t)r * ld + col];
+    return ff_make(v.x, v.y);
+  };
+#pragma unroll
+  for (int j = 0; j <= 2 * S; ++j) xw[j] = ldv(j - S);
+  ff nu = ff_make(0.f, 0.f), de = ff_make(0.f, 0.f);
+  const ff zero = ff_make(0.f, 0.f);
+  for (int k = 0; k < N; ++k) {
+    if (k + S + 1 + kPf < N) prefetch_l2(X + (size_t)(k + S + 1 + kPf) * ld + col);
+    ff tx = zero;
+#pragma unroll
+    for (int j = 0; j <= 2 * S; ++j) {
+      const int c = k - S + j;
+      if (c >= 0 && c < N) ff_acc(tx, mval_ff<S>(Tb, N, zero, k, c), xw[j]);
+    }
+    tx = ff_norm(tx);
+    ff_acc(nu, xw[S], tx);
+    ff_acc(de, xw[S], xw[S]);
+    nu = ff_norm(nu);
+    de = ff_norm(de);
+#pragma unroll
+    for (int j = 0; j < 2 * S; ++j) xw[j] = xw[j + 1];
+    xw[2 * S] = ldv(k + S + 1);
+  }
+  *num = nu;
+  *den = de;
+}
+
+// ||T x - theta x|| (pairs, leading part returned) for the pair vector of column col
+template <int S>
+__device__ double resid_pair(const float2* __restrict__ Tb, int N, const float2* __restrict__ X, size_t ld, int col,
+                             ff theta) {
+  const ff zero = ff_make(0.f, 0.f);
+  const ff nth = ff_make(-theta.hi, -theta.lo);
+  ff r2 = zero;
+  for (int k = 0; k < N; ++k) {
+    ff tx = zero;
+    for (int c = max(0, k - S); c <= min(N - 1, k + S); ++c) {
+      const float2 v = X[(size_t)c * ld + col];
+      ff_acc(tx, mval_ff<S>(Tb, N, c == k ? nth : zero, k, c), ff_make(v.x, v.y));
+    }
+    tx = ff_norm(tx);
+    ff_acc(r2, tx, tx);
+    r2 = ff_norm(r2);
+  }
+  return sqrt(ff_to_double(r2));
+}
+
+// The inverse iteration of one singleton (the fp64 loop of k_invit, in pairs).  Returns false
+// if a value went non-finite (the caller then runs the fp64 iteration from a fresh vector);
+// otherwise the vector is normalised, its first and last S rows are doubles in X, and *lam and
+// *res hold its Rayleigh quotient and residual norm.
+template <int S>
+__device__ bool invit_pair(Slot& sl, int N, size_t ld, int i, double est, bool refined, double tolc, double tnorm,
+                           double* lam, double* res) {
+  float2* X = reinterpret_cast<float2*>(sl.X);
+  for (int k = 0; k < N; ++k) X[(size_t)k * ld + i] = make_float2((float)hash_unit((unsigned)k, (unsigned)i), 0.f);
+  const ff estf = ff_from_double(est);
+  const ff one = ff_make(1.f, 0.f);
+  const double tiny = 8.0 * 0x1.0p-48 * tnorm + 1e-30;
+  const fd tinyf(tiny);
+  ff xscale = one, sigma = estf;
+  bool warm = true;
+  {
+    float* U32 = reinterpret_cast<float*>(sl.U);
+    const float tiny32 = FLT_EPSILON * (float)tnorm + FLT_MIN;
+    for (int it = 0; it < kIters32 && warm; ++it) {
+      const float amax = solve_pair<S, float>(sl.Tbf, N, estf, tiny32, xscale, X, ld, i, U32, i, ld);
+      warm = isfinite(amax) && amax > 0.f;
+      xscale = ff_make(warm ? 1.f / amax : 1.f, 0.f);
+    }
+  }
+  ff rq = estf;
+  if (warm) {
+    ff num, den;
+    rq_pair<S>(sl.Tbf, N, X, ld, i, &num, &den);
+    warm = isfinite(num.hi) && isfinite(den.hi) && den.hi > 0.f;
+    if (warm) {
+      rq = ff_div(num, den);
+      xscale = ff_from_double(1.0 / sqrt(ff_to_double(den)));
+    }
+  }
+  if (!warm) {
+    for (int k = 0; k < N; ++k) X[(size_t)k * ld + i] = make_float2((float)hash_unit((unsigned)k, (unsigned)i), 0.f);
+    rq = estf;
+    xscale = one;
+  }
+  // Rayleigh-quotient shifts while the iterate is dominated by the wanted eigenvector: for an
+  // fp32 estimate within half its tolerance; for a refined estimate (kRefineRes ||T|| from the
+  // eigenvalue, neighbours at least the fp64 tolerance away) within a thousandth of that
+  auto may_shift = [&](ff q) {
+    const double d = fabs(ff_to_double(q) - est);
+    return d <= 0.5 * tolc + 8.0 * tiny && (!refined || d <= 1e-3 * tolc);
+  };
+  double prev = ff_to_double(rq);
+  if (warm && may_shift(rq)) sigma = rq;
+  int extra = -1;
+  for (int it = 0; it < kMaxIters; ++it) {
+    const float amax = solve_pair<S, fd>(sl.Tbf, N, sigma, tinyf, xscale, X, ld, i, reinterpret_cast<fd*>(sl.U), i, ld);
+    if (!isfinite(amax)) return false;
+    ff num, den;
+    rq_pair<S>(sl.Tbf, N, X, ld, i, &num, &den);
+    if (!(isfinite(num.hi) && isfinite(den.hi) && den.hi > 0.f)) return false;
+    rq = ff_div(num, den);
+    xscale = ff_from_double(1.0 / sqrt(ff_to_double(den)));
+    const double rqd = ff_to_double(rq);
+    if (extra == 0) break;
+    if (extra > 0) --extra;
+    if (extra < 0 && (warm || it >= 1) && fabs(rqd - prev) <= kSettle * tnorm) extra = 0;
+    prev = rqd;
+    if ((warm || it >= 1) && may_shift(rq)) sigma = rq;
+  }
+  for (int k = 0; k < N; ++k) {
+    const float2 v = X[(size_t)k * ld + i];
+    const ff y = ff_mul(ff_make(v.x, v.y), xscale);
+    X[(size_t)k * ld + i] = make_float2(y.hi, y.lo);
+  }
+  ff num, den;
+  rq_pair<S>(sl.Tbf, N, X, ld, i, &num, &den);
+  if (!(isfinite(num.hi) && isfinite(den.hi) && den.hi > 0.f)) return false;
+  // the residual of the converged pair vector (the acceptance test of the caller)
+  rq = ff_div(num, den);
+  *res = resid_pair<S>(sl.Tbf, N, X, ld, i, rq);
+  // one fp64 inverse-iteration step at the pair Rayleigh quotient brings every component to
+  // fp64 accuracy (the pair vector is accurate to about 2^-48 absolute, which the tiny last
+  // components of converged Ritz vectors would feel); its Rayleigh quotient is the eigenvalue
+  double* Xd = reinterpret_cast<double*>(X);
+  for (int k = 0; k < N; ++k) {
+    const float2 a = X[(size_t)k * ld + i];
+    Xd[(size_t)k * ld + i] = (double)a.x + (double)a.y;
+  }
+  solve1<S>(sl.Tb, N, ff_to_double(rq), DBL_EPSILON * tnorm + DBL_MIN, 1.0, Xd, ld, i, sl.U, i, ld);
+  double nu, de;
+  rq_pass<S>(sl.Tb, N, Xd, ld, i, &nu, &de);
+  if (!(isfinite(nu) && isfinite(de) && de > 0.0)) return false;
+  *lam = nu / de;
+  const double sc = 1.0 / sqrt(de);
+  for (int k = 0; k < N; k = (k + 1 == S && N - S > S) ? N - S : k + 1)  // rows 0..S-1 and N-S..N-1, once
+    Xd[(size_t)k * ld + i] *= sc;
+  return isfinite(*lam) && isfinite(*res);
+}
+
 // first and last s components of eigenvectors i..i+c-1 ->
 // a_i = (Q^T E_1 gamma)_i, w_i = (Q^T E_m tau^T)_i
 template <int S>
@@ -595,8 +932,7 @@ __device__ void write_aw(const CheckArgs& g, Slot& sl, int m, int N, size_t ld, 
 template <int S>
 __global__ void k_invit(CheckArgs g, int round) {
   const int c_idx = blockIdx.y;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int N = S * m;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -625,10 +961,13 @@ __global__ void k_invit(CheckArgs g, int round) {
     }
   }
   if (c == 1) {
-    for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] = hash_unit((unsigned)k, (unsigned)i);
     const double est = sl.est[i];
     const bool refined = retry || tolc < sl.hdr[4];
-    double sigma = est, rq = est, res = 0.0, prev = est, xscale = 1.0;
+    double rq = est, res = 0.0;
+    if (!kPairInvit || !invit_pair<S>(sl, N, ld, i, est, refined, tolc, tnorm, &rq, &res)) {
+    // fp64 from a fresh vector where the pair iteration overflowed
+    for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] = hash_unit((unsigned)k, (unsigned)i);
+    double sigma = est, prev = est, xscale = 1.0;
     // fp32 inverse iterations at the estimate (fp32 rate, half the scratch traffic) bring the
     // vector to fp32 accuracy; fp64 Rayleigh-quotient steps then finish it in one or two solves
     // (near-duplicate eigenvalues of T_m can put several tiny pivots in one factorisation; their
@@ -679,6 +1018,7 @@ __global__ void k_invit(CheckArgs g, int round) {
     }
     for (int k = 0; k < N; ++k) sl.X[(size_t)k * ld + i] *= xscale;
     rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
+    }
     sl.lam[i] = rq;
     // the windows est +- tolc/2 of different groups are disjoint, so this also excludes
     // two singletons converging to the same eigenpair
@@ -749,8 +1089,7 @@ __device__ __forceinline__ int* pack_list(const Slot& sl, int nmax) { return sl.
 // warp per check, the sizes read 32 at a time.
 __global__ void k_pack_clusters(CheckArgs g, int dense) {
   const int c_idx = blockIdx.x;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   Slot sl = get_slot(g.slots, g.s, g.nmax, c_idx);
   const int lane = threadIdx.x;
   const int ncl = sl.clist[0];
@@ -807,8 +1146,7 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
   __shared__ int ords[WPB][kMaxCluster];
   __shared__ int qis[WPB][kPackMax], qcs[WPB][kPackMax], qos[WPB][kPackMax], qss[WPB][kPackMax];
   const int c_idx = blockIdx.y;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int N = S * m;
   Slot sl = get_slot(g.slots, S, g.nmax, c_idx);
   const size_t ld = (size_t)g.nmax;
@@ -1041,8 +1379,7 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
 // one warp per row i of Y~ W: ||sum_j (a_i.a_j)/(lam_i+lam_j) w_j||^2
 __global__ void k_cauchy_lyap(CheckArgs g) {
   const int c_idx = blockIdx.y;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int s = g.s, N = s * m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -1076,8 +1413,7 @@ __global__ void k_cauchy_lyap(CheckArgs g) {
 // Sylvester: one warp per row i (rows of Y~ G, A side) or column j (Y~^T F, B side)
 __global__ void k_cauchy_sylv(CheckArgs ga, CheckArgs gb, int side) {
   const int c_idx = blockIdx.y;
-  const int m = ga.m_lo + c_idx;
-  if (!checked(ga, m)) return;
+  const int m = ga.ms[c_idx];
   const int s = ga.s, N = s * m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -1118,8 +1454,7 @@ __global__ void k_cauchy_sylv(CheckArgs ga, CheckArgs gb, int side) {
 __global__ void k_cauchy_smallb(CheckArgs g, const double* __restrict__ ups, const double* __restrict__ ct, int n2,
                                 double* __restrict__ parts) {
   const int c_idx = blockIdx.y;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) return;
+  const int m = g.ms[c_idx];
   const int s = g.s, N = s * m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -1154,11 +1489,7 @@ __global__ void k_cauchy_smallb(CheckArgs g, const double* __restrict__ ups, con
 __global__ void k_finalize_smallb(CheckArgs g, const double* __restrict__ parts, int n2, double c2norm, double* hist,
                                   double tol, int* first_conv) {
   const int c_idx = blockIdx.x;
-  const int m = g.m_lo + c_idx;
-  if (!checked(g, m)) {
-    if (threadIdx.x == 0) hist[m - 1] = __longlong_as_double(0x7ff8000000000000LL);
-    return;
-  }
+  const int m = g.ms[c_idx];
   __shared__ double red[256];
   double t = 0.0;
   for (int j = threadIdx.x; j < n2; j += blockDim.x) t += parts[(size_t)c_idx * n2 + j];
@@ -1184,11 +1515,7 @@ __global__ void k_finalize_smallb(CheckArgs g, const double* __restrict__ parts,
 // sum of the per-row parts in a fixed order; history entry and convergence flag
 __global__ void k_finalize(CheckArgs ga, CheckArgs gb, int sylv, double* hist, double tol, int* first_conv) {
   const int c_idx = blockIdx.x;
-  const int m = ga.m_lo + c_idx;
-  if (!checked(ga, m)) {
-    if (threadIdx.x == 0) hist[m - 1] = __longlong_as_double(0x7ff8000000000000LL);
-    return;
-  }
+  const int m = ga.ms[c_idx];
   const int s = ga.s, N = s * m;
   Slot sa = get_slot(ga.slots, s, ga.nmax, c_idx);
   __shared__ double red[256];
@@ -1249,16 +1576,15 @@ __global__ void k_finalize(CheckArgs ga, CheckArgs gb, int sylv, double* hist, d
 }
 
 // nslots slots of leading dimension nmax per operator, operator 1's after operator 0's
-CheckArgs make_args(lyap_handle* h, int opi, int m_lo, int nchk, int every, int nmax, int nslots) {
+CheckArgs make_args(lyap_handle* h, int opi, const int* ms, int nchk, int nmax, int nslots) {
   CheckArgs g;
   g.log = h->op[opi].log;
   g.s = h->s;
   g.nmax = nmax;
   const size_t sd = slot_doubles(h->s, nmax);
   g.slots = reinterpret_cast<double*>(h->check_ws) + sd * (size_t)(opi * nslots);
-  g.m_lo = m_lo;
   g.nchk = nchk;
-  g.every = every;
+  for (int c = 0; c < kMaxChecks; ++c) g.ms[c] = c < nchk ? ms[c] : 0;
   g.flags = h->flags;
   g.chk_err = h->chk_err;
   return g;
@@ -1267,17 +1593,17 @@ CheckArgs make_args(lyap_handle* h, int opi, int m_lo, int nchk, int every, int 
 int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
   k_setup_band<<<g.nchk, 256, 0, st>>>(g);
   dim3 gv((nmax_batch + 31) / 32, g.nchk);
-  switch (g.s) {
-    case 1: k_bisect_band32<1><<<gv, 32, 0, st>>>(g); break;
-    case 2: k_bisect_band32<2><<<gv, 32, 0, st>>>(g); break;
-    case 3: k_bisect_band32<3><<<gv, 32, 0, st>>>(g); break;
-    case 4: k_bisect_band32<4><<<gv, 32, 0, st>>>(g); break;
-    case 8: k_bisect_band32<8><<<gv, 32, 0, st>>>(g); break;
-  }
-  // fp64 estimates for the members of fp32 groups; the singleton iteration; fp64 estimates and a
-  // second iteration for the singletons whose fp32 estimate proved too far off
-  k_mark_refine<<<g.nchk, 256, 0, st>>>(g);
   dim3 gr((nmax_batch + 7) / 8, g.nchk);  // eight warps a block, one eigenvalue a warp
+  switch (g.s) {
+    case 1: k_bisect_band32<1><<<gr, 256, 0, st>>>(g); break;
+    case 2: k_bisect_band32<2><<<gr, 256, 0, st>>>(g); break;
+    case 3: k_bisect_band32<3><<<gr, 256, 0, st>>>(g); break;
+    case 4: k_bisect_band32<4><<<gr, 256, 0, st>>>(g); break;
+    case 8: k_bisect_band32<8><<<gr, 256, 0, st>>>(g); break;
+  }
+  // refined estimates for the members of fp32 groups; the singleton iteration; refined
+  // estimates and a second iteration for the singletons whose fp32 estimate proved too far off
+  k_mark_refine<<<g.nchk, 256, 0, st>>>(g);
   for (int round = 0; round < 2; ++round) {
     switch (g.s) {
       case 1: k_refine64<1><<<gr, 256, 0, st>>>(g, round); break;
@@ -1331,15 +1657,16 @@ size_t check_slot_bytes(int s, int nmax) { return slot_doubles(s, nmax) * sizeof
 // leading dimension of the slots of a batch whose largest check is at m_hi
 int batch_nmax(int s, int m_hi) { return (s * m_hi + 7) / 8 * 8; }
 
-// Evaluates the checks for m = m_lo..m_hi; the slots of the batch have leading dimension
-// batch_nmax(s, m_hi) and must fit in the check area (the caller sizes the batch).
-int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
+// Evaluates the checks at m = ms[0..nchk-1] (ascending, nchk <= the check batch); the slots of
+// the batch have leading dimension batch_nmax(s, ms[nchk-1]) and must fit in the check area (the
+// caller sizes the batch).
+int launch_check_list(lyap_handle* h, const int* ms, int nchk, cudaStream_t st) {
+  if (nchk <= 0) return 0;
   int nl = 0;
-  const int nchk = m_hi - m_lo + 1;
-  const int every = h->opt.check_every > 0 ? h->opt.check_every : 1;
+  const int m_hi = ms[nchk - 1];
   const int nmax_batch = h->s * m_hi;
   const int nb = batch_nmax(h->s, m_hi);
-  CheckArgs ga = make_args(h, 0, m_lo, nchk, every, nb, nchk);
+  CheckArgs ga = make_args(h, 0, ms, nchk, nb, nchk);
   nl += eigen_pipeline(ga, nmax_batch, st);
   CheckArgs gb = ga;
   const int wpb = 8;
@@ -1352,7 +1679,7 @@ int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
     return nl + 2;
   }
   if (h->plan.sylv) {
-    gb = make_args(h, 1, m_lo, nchk, every, nb, nchk);
+    gb = make_args(h, 1, ms, nchk, nb, nchk);
     nl += eigen_pipeline(gb, nmax_batch, st);
     k_cauchy_sylv<<<gc, wpb * 32, 0, st>>>(ga, gb, 0);
     k_cauchy_sylv<<<gc, wpb * 32, 0, st>>>(ga, gb, 1);
@@ -1365,9 +1692,19 @@ int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
   return nl + 1;
 }
 
+// every m = m_lo..m_hi that the check period d selects (m % d == 0)
+int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st) {
+  const int every = h->opt.check_every > 0 ? h->opt.check_every : 1;
+  int ms[kMaxChecks];
+  int n = 0;
+  for (int m = m_lo; m <= m_hi && n < kMaxChecks; ++m)
+    if (m % every == 0) ms[n++] = m;
+  return launch_check_list(h, ms, n, st);
+}
+
 // Eigenvalues and a, w rows of T_m (slot 0 of operator opi) for the factor step.
 int launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st) {
-  CheckArgs g = make_args(h, opi, m, 1, 1, h->plan.nmax, h->plan.check_batch);
+  CheckArgs g = make_args(h, opi, &m, 1, h->plan.nmax, h->plan.check_batch);
   return eigen_pipeline(g, h->s * m, st);
 }
 
@@ -1489,9 +1826,8 @@ extern "C" int lyap_residual_noalloc(int s, int m, const double* ab, int ldab, c
   g.slots = slot;
   g.s = s;
   g.nmax = kNoAllocMaxN;
-  g.m_lo = m;
   g.nchk = 1;
-  g.every = 1;
+  g.ms[0] = m;
   g.flags = ints;
   g.chk_err = chk_err;
   eigen_pipeline(g, s * m, st);

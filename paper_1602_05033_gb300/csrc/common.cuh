@@ -134,6 +134,8 @@ struct lyap_handle {
   int converged = 0;
   int lanczos_done = 0;         // iterations whose blocks exist
   int checked = 0;              // largest m the last solve checked
+  int nchecks = 0;              // checks the last solve evaluated
+  int checks_past = 0;          // of those, checks at m past its converged m
   double* hist_host = nullptr;  // pinned copy
   int* flags_host = nullptr;    // pinned
   cudaStream_t side = nullptr;  // second stream (checks)
@@ -180,6 +182,7 @@ int batch_blocks_per_sm(int s, int bulk_f32);
 
 // check.cu
 int launch_check_batch(lyap_handle* h, int m_lo, int m_hi, cudaStream_t st);
+int launch_check_list(lyap_handle* h, const int* ms, int nchk, cudaStream_t st);
 int launch_eigen_for_factor(lyap_handle* h, int opi, int m, cudaStream_t st);
 
 // api.cu (used by the batched solver)

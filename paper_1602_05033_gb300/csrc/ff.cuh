@@ -96,3 +96,45 @@ __host__ __device__ __forceinline__ ff ff_from_double(double d) {
 }
 
 __host__ __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// a - b, normalised
+__host__ __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_make(-b.hi, -b.lo)); }
+
+// a / b, normalised: the quotient of the leading parts, corrected once by the remainder
+// a - q1 b (formed as a pair), about 2^-47 relative
+__host__ __device__ __forceinline__ ff ff_div(ff a, ff b) {
+  const float q1 = a.hi / b.hi;
+  ff p = ff_make(0.f, 0.f);
+  ff_acc(p, q1, b);
+  const ff r = ff_sub(a, ff_norm(p));
+  const float q2 = r.hi / b.hi;
+  ff q;
+  ff_fast_two_sum(q1, q2, q.hi, q.lo);
+  return q;
+}
+
+// The pair as an arithmetic type for code templated on its number type (a banded solver run in
+// fp32, pairs or fp64): conversions from and to double, the four operations, fma, fabs and
+// comparisons.  Comparisons order by the leading part, then the trailing one.
+struct fd {
+  ff v;
+  fd() = default;
+  __host__ __device__ __forceinline__ fd(double d) : v(ff_from_double(d)) {}
+  __host__ __device__ __forceinline__ explicit fd(ff x) : v(x) {}
+  __host__ __device__ __forceinline__ explicit operator double() const { return ff_to_double(v); }
+};
+__host__ __device__ __forceinline__ fd operator-(fd a) { return fd(ff_make(-a.v.hi, -a.v.lo)); }
+__host__ __device__ __forceinline__ fd operator+(fd a, fd b) { return fd(ff_add(a.v, b.v)); }
+__host__ __device__ __forceinline__ fd operator-(fd a, fd b) { return fd(ff_sub(a.v, b.v)); }
+__host__ __device__ __forceinline__ fd operator*(fd a, fd b) { return fd(ff_mul(a.v, b.v)); }
+__host__ __device__ __forceinline__ fd operator/(fd a, fd b) { return fd(ff_div(a.v, b.v)); }
+__host__ __device__ __forceinline__ fd fma(fd a, fd b, fd c) {
+  ff r = c.v;
+  ff_acc(r, a.v, b.v);
+  return fd(ff_norm(r));
+}
+__host__ __device__ __forceinline__ fd fabs(fd a) { return a.v.hi < 0.f ? -a : a; }
+__host__ __device__ __forceinline__ bool operator<(fd a, fd b) {
+  return a.v.hi < b.v.hi || (a.v.hi == b.v.hi && a.v.lo < b.v.lo);
+}
+__host__ __device__ __forceinline__ bool operator>(fd a, fd b) { return b < a; }

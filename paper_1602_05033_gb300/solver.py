@@ -42,7 +42,7 @@ class Solver:
         self.maxit = int(maxit)
         opt = L.lyap_default_options()
         opt.maxit = int(maxit)
-        opt.check_every = int(check_every)
+        opt.check_every = L.LYAP_CHECK_ADAPTIVE if check_every == "adaptive" else int(check_every)
         opt.trunc_eps = float(trunc_eps)
         opt.precision = self.precision
         opt.sell_sigma = int(sell_sigma)

@@ -260,3 +260,59 @@ def test_speculative_chunks_follow_the_residual_trend(pkg):
     print(f"m={sol.m}: steps past m {wasted:.0f}, checks past m {late_checks:.0f}")
     assert 0 <= late_checks <= wasted < 48
     sol.close()
+
+
+ADAPTIVE_TARGETS = [11, 13, 19, 27, 37, 53, 71]
+
+
+def test_adaptive_schedule_finds_the_first_converged_m(pkg):
+    """The adaptive check schedule (every m up to 8, every 8th m until the residual trend
+    predicts tol within reach, then every m; the m skipped before the first converged check are
+    checked afterwards).  For each target m0 the tolerance is placed between the oracle's
+    residuals at m0 - 1 and m0 on a stretch where the history decreases, so the first m meeting
+    it is m0: the GPU must return exactly m0, its checked entries must match the oracle's
+    history, and the skipped entries are NaN.  Targets inside the sparse stretch take the
+    backfill path."""
+    A = wl.laplacian_2d(40)
+    C = wl.rhs(A.shape[0], 2, 5)
+    full = olyap.solve(A, C, tol=0.0, maxit=90).history
+    skipped_total = 0
+    for m0 in ADAPTIVE_TARGETS:
+        assert np.all(np.diff(full[: m0]) < 0), m0
+        tol = float(np.sqrt(full[m0 - 2] * full[m0 - 1]))
+        sol = pkg.Solver(A, C, tol=tol, maxit=200, check_every="adaptive")
+        st = sol.solve()
+        assert st == 0 and sol.m == m0, (m0, sol.m)
+        h = sol.history()
+        chk = ~np.isnan(h)
+        assert chk[: min(8, m0)].all() and chk[m0 - 1]
+        ok, worst = _hist_ok(h[chk], full[: m0][chk])
+        assert ok, (m0, worst)
+        ph = sol.phase_times()
+        skipped_total += int((~chk).sum())
+        print(f"m0={m0}: checks {ph[9]:.0f} (past m {ph[8]:.0f}), skipped {int((~chk).sum())}, worst/bound {worst:.3f}")
+        sol.close()
+    assert skipped_total > 0
+
+
+@pytest.mark.parametrize("s,k,tol", [(1, 50, 1e-8), (4, 14, 1e-9), (3, 24, 1e-10)])
+def test_adaptive_schedule_matches_oracle_run(pkg, s, k, tol):
+    """Whole runs under the adaptive schedule: the same m as the oracle checking every m, the
+    checked entries within the history bound, the factor's X on probes within 1e-8."""
+    A = wl.laplacian_3d(k) if s == 4 else wl.laplacian_2d(k)
+    C = wl.rhs(A.shape[0], s, 31 + s)
+    ref = olyap.solve(A, C, tol=tol, maxit=600)
+    sol = pkg.Solver(A, C, tol=tol, maxit=600, check_every="adaptive")
+    st = sol.solve()
+    assert st == 0 and sol.m == ref.m, (sol.m, ref.m)
+    h = sol.history()
+    chk = ~np.isnan(h)
+    ok, worst = _hist_ok(h[chk], ref.history[chk])
+    assert ok, worst
+    ph = sol.phase_times()
+    print(f"s={s} k={k}: m={sol.m}, checks {ph[9]:.0f} of {sol.m}, worst/bound {worst:.3f}")
+    assert ph[9] < sol.m + ph[8]
+    Z = sol.factor().cpu().numpy()
+    Zo, _ = olyap.factor(A, C, ref)
+    assert _xprobe(Z, Zo) <= 1e-8
+    sol.close()
