@@ -449,7 +449,8 @@ def batch_line(args):
             clocks.start()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
-        bt = Batch([(P.A, P.C1) for P in probs], tol=1e-8, maxit=1000, precision="mixed")
+        bt = Batch([(P.A, P.C1) for P in probs], tol=1e-8, maxit=1000, precision="mixed",
+                   check_every=args.check if args.check == "adaptive" else int(args.check))
         st = bt.solve(autotune=(it == 0))
         e1.record()
         stat_i, m_i = bt.status()
@@ -476,7 +477,7 @@ def batch_line(args):
         "data": "synthetic",
         "config": {"workload": f"batched Lyapunov, {len(probs)} instances A_i = -(2D Laplacian k_i x k_i) - d_i I, "
                                "k_i in [64, 512], d_i in [0, 10], s_i in {1, 2, 4}, tol 1e-8, maxit 1000, mixed",
-                   "sum_n": n_tot, "sum_nnz": nnz_tot},
+                   "sum_n": n_tot, "sum_nnz": nnz_tot, "check": args.check},
         "status": int(st), "instances_converged": int(sum(1 for x in stat if x == 0)),
         "iterations": {"min": int(min(ms)), "max": int(max(ms)), "sum": int(sum(ms))},
         "instance_iterations_per_s": round(sum(ms) / (solve_ms * 1e-3), 1),

@@ -18,9 +18,17 @@
 
 namespace {
 
-constexpr int kPools = 12;  // most pools (streams with check and factor scratch)
+#ifndef LYAP_BATCH_POOLS
+#define LYAP_BATCH_POOLS 12
+#endif
+constexpr int kPools = LYAP_BATCH_POOLS;  // most pools (streams with check and factor scratch)
 constexpr int kRowChoices[3] = {1024, 4096, 16384};
-constexpr size_t kPoolCheckMin = (size_t)2 << 30;  // check slots of one pool
+// check slots of one pool: room for several checks of a large instance in one launch (their
+// eigenpair iterations run side by side instead of one launch after another)
+#ifndef LYAP_POOL_CHECK_GB
+#define LYAP_POOL_CHECK_GB 6
+#endif
+constexpr size_t kPoolCheckMin = (size_t)LYAP_POOL_CHECK_GB << 30;
 
 struct Group {
   int s = 1;
@@ -357,6 +365,21 @@ int lyap_batch_solve(lyap_batch* b, int autotune_flag, void* stream) {
   }
   if (!b->graph && (rc = capture_graph(b)) != LYAP_OK) return rc;
   std::vector<int> checked(K, 0), finished(K, 0);
+  std::vector<std::vector<unsigned char>> was(K, std::vector<unsigned char>((size_t)o.maxit + 1, 0));
+  std::vector<int> todo;
+  // the checks at the m of a list for instance i, in batches that fit its pool's check area
+  auto check_list = [&](int i, const std::vector<int>& ms, cudaStream_t sp) {
+    lyap_handle* h = b->h[i];
+    const int si = b->s[i];
+    size_t a = 0;
+    while (a < ms.size()) {
+      size_t n = std::min(ms.size() - a, (size_t)o.check_batch);
+      while (n > 1 && check_slot_bytes(si, batch_nmax(si, ms[a + n - 1])) * n > b->plan.pool_check) --n;
+      h->launches += launch_check_list(h, ms.data() + a, (int)n, sp);
+      for (size_t k = a; k < a + n; ++k) was[i][ms[k]] = 1;
+      a += n;
+    }
+  };
   for (int i = 0; i < K; ++i) b->status[i] = LYAP_NOT_CONVERGED;
   int chunk = std::min(4, o.check_batch);
   float t_lanczos = 0.f, t_check = 0.f;
@@ -386,16 +409,15 @@ int lyap_batch_solve(lyap_batch* b, int autotune_flag, void* stream) {
       const int p = next++ % b->plan.npools;
       cudaStream_t sp = b->streams[p];
       h->check_ws = b->pool[p];
-      const int si = b->s[i];
-      while (checked[i] < b->done[i]) {
-        const int lo = checked[i] + 1;
-        int hi = std::min(b->done[i], checked[i] + o.check_batch);
-        while (hi > lo && check_slot_bytes(si, batch_nmax(si, hi)) * (size_t)(hi - lo + 1) > b->plan.pool_check) --hi;
-        h->launches += launch_check_batch(h, lo, hi, sp);
-        checked[i] = hi;
-      }
+      // the history up to checked[i] is on the host (copied after the previous round)
+      pick_checks(h, checked[i], b->done[i], checked[i], todo);
+      check_list(i, todo, sp);
+      const int first_new = checked[i] + 1;
+      checked[i] = b->done[i];
       h->lanczos_done = b->done[i];
       LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sp));
+      LYAP_CUDA_TRY(cudaMemcpyAsync(h->hist_host + first_new - 1, h->hist + first_new - 1,
+                                    sizeof(double) * (checked[i] - first_new + 1), cudaMemcpyDeviceToHost, sp));
       pending.push_back(i);
     }
     for (int p = 0; p < b->plan.npools; ++p) {
@@ -407,6 +429,38 @@ int lyap_batch_solve(lyap_batch* b, int autotune_flag, void* stream) {
     LYAP_CUDA_TRY(cudaGetLastError());
     cudaEventElapsedTime(&a, b->ev[2], b->ev[3]);
     t_check += a;
+    if (o.check_every == LYAP_CHECK_ADAPTIVE) {
+      // the adaptive schedule may have skipped m before an instance's first converged check:
+      // check them, so that its m is the first converged m after its last failing check
+      cudaEventRecord(b->ev[2], st);
+      for (int p = 0; p < b->plan.npools; ++p) cudaStreamWaitEvent(b->streams[p], b->ev[2], 0);
+      int nb = 0;
+      for (int i : pending) {
+        lyap_handle* h = b->h[i];
+        const int mc = h->flags_host[1];
+        if (mc == INT_MAX) continue;
+        int last = mc - 1;
+        while (last >= 1 && !was[i][last]) --last;
+        todo.clear();
+        for (int mm = last + 1; mm < mc; ++mm) todo.push_back(mm);
+        if (todo.empty()) continue;
+        cudaStream_t sp = b->streams[nb++ % b->plan.npools];
+        h->check_ws = b->pool[(nb - 1) % b->plan.npools];
+        check_list(i, todo, sp);
+        LYAP_CUDA_TRY(cudaMemcpyAsync(h->flags_host, h->flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, sp));
+      }
+      if (nb > 0) {
+        for (int p = 0; p < b->plan.npools; ++p) {
+          cudaEventRecord(b->join[p], b->streams[p]);
+          cudaStreamWaitEvent(st, b->join[p], 0);
+        }
+        cudaEventRecord(b->ev[3], st);
+        LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+        LYAP_CUDA_TRY(cudaGetLastError());
+        cudaEventElapsedTime(&a, b->ev[2], b->ev[3]);
+        t_check += a;
+      }
+    }
     bool stop_changed = false;
     for (int i : pending) {
       lyap_handle* h = b->h[i];

@@ -70,6 +70,12 @@ constexpr double kResTol = 1e-11;  // accepted ||T x - lambda x|| relative to ||
 #endif
 constexpr double kRefineRes = LYAP_REFINE_RES;  // width at which multisection stops, relative to ||T||
 constexpr bool kPairInvit = LYAP_PAIR_INVIT;    // singleton iteration in float pairs (else fp64)
+// threads per block of k_invit (each thread iterates one eigenpair alone; smaller blocks, spread
+// over more SM sub-partitions, measured slower on the n = 1e6 workload)
+#ifndef LYAP_INVIT_THREADS
+#define LYAP_INVIT_THREADS 32
+#endif
+constexpr int kInvitThreads = LYAP_INVIT_THREADS;
 
 struct Slot {
   double* hdr;   // [0] Gershgorin lo, [1] hi (scaled), [2] max e^2 (scaled), [3] scale, [4] fp32 cluster
@@ -1594,6 +1600,7 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
   k_setup_band<<<g.nchk, 256, 0, st>>>(g);
   dim3 gv((nmax_batch + 31) / 32, g.nchk);
   dim3 gr((nmax_batch + 7) / 8, g.nchk);  // eight warps a block, one eigenvalue a warp
+  dim3 gi((nmax_batch + kInvitThreads - 1) / kInvitThreads, g.nchk);
   switch (g.s) {
     case 1: k_bisect_band32<1><<<gr, 256, 0, st>>>(g); break;
     case 2: k_bisect_band32<2><<<gr, 256, 0, st>>>(g); break;
@@ -1614,19 +1621,19 @@ int eigen_pipeline(const CheckArgs& g, int nmax_batch, cudaStream_t st) {
     }
     if (round == 1) break;
     switch (g.s) {
-      case 1: k_invit<1><<<gv, 32, 0, st>>>(g, 0); break;
-      case 2: k_invit<2><<<gv, 32, 0, st>>>(g, 0); break;
-      case 3: k_invit<3><<<gv, 32, 0, st>>>(g, 0); break;
-      case 4: k_invit<4><<<gv, 32, 0, st>>>(g, 0); break;
-      case 8: k_invit<8><<<gv, 32, 0, st>>>(g, 0); break;
+      case 1: k_invit<1><<<gi, kInvitThreads, 0, st>>>(g, 0); break;
+      case 2: k_invit<2><<<gi, kInvitThreads, 0, st>>>(g, 0); break;
+      case 3: k_invit<3><<<gi, kInvitThreads, 0, st>>>(g, 0); break;
+      case 4: k_invit<4><<<gi, kInvitThreads, 0, st>>>(g, 0); break;
+      case 8: k_invit<8><<<gi, kInvitThreads, 0, st>>>(g, 0); break;
     }
   }
   switch (g.s) {
-    case 1: k_invit<1><<<gv, 32, 0, st>>>(g, 1); break;
-    case 2: k_invit<2><<<gv, 32, 0, st>>>(g, 1); break;
-    case 3: k_invit<3><<<gv, 32, 0, st>>>(g, 1); break;
-    case 4: k_invit<4><<<gv, 32, 0, st>>>(g, 1); break;
-    case 8: k_invit<8><<<gv, 32, 0, st>>>(g, 1); break;
+    case 1: k_invit<1><<<gi, kInvitThreads, 0, st>>>(g, 1); break;
+    case 2: k_invit<2><<<gi, kInvitThreads, 0, st>>>(g, 1); break;
+    case 3: k_invit<3><<<gi, kInvitThreads, 0, st>>>(g, 1); break;
+    case 4: k_invit<4><<<gi, kInvitThreads, 0, st>>>(g, 1); break;
+    case 8: k_invit<8><<<gi, kInvitThreads, 0, st>>>(g, 1); break;
   }
   // groups: packed into warps of up to 32 members; 16 blocks of 4 warps per check take the packs
   // in turn (the SM count is read once: a process uses one GPU model)

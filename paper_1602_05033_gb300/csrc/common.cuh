@@ -17,6 +17,8 @@
 #include <stddef.h>
 #include "lyap.h"
 
+#include <vector>
+
 #define LYAP_SLICE 32
 #define LYAP_MAX_S 8
 
@@ -196,6 +198,9 @@ int make_plan(const lyap_csr* A, const lyap_csr* B, int s, const lyap_options& o
 void solve_begin(lyap_handle* h, cudaStream_t st);
 int solve_end(lyap_handle* h, int done, int m_final, int result, cudaStream_t st);
 int round_status(lyap_handle* h);
+// the m of (from, upto] the check schedule (period or adaptive) evaluates, given the history on
+// the host up to m = known
+void pick_checks(const lyap_handle* h, int from, int upto, int known, std::vector<int>& out);
 
 // factor.cu
 int dense_eigh(double* K, int n, int ld, double* ev, double* V, double* scratch, int* cnt, cudaStream_t st);

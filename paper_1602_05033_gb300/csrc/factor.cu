@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(256) k_gemm_accum(int64_t n, int K, int t, con
 // (BM x BN tiles, 256 threads of 4 x 4 outputs: BM = 4 * 256 / (BN / 4))
 template <int S, int BN>
 __global__ void __launch_bounds__(256) k_gemm_accum_ff(int64_t n, int K, int t, const float* __restrict__ Vb,
-                                                       int64_t ldv, const double* __restrict__ Mg, int64_t ldm,
+                                                       int64_t ldv, const float2* __restrict__ Mp, int64_t ldm,
                                                        float2* __restrict__ Z, int64_t ldz) {
   constexpr int TXN = BN / 4, BM = 4 * (256 / TXN), BK = 16;
   __shared__ ff As[BK][BM + 1];
@@ -691,8 +691,8 @@ __global__ void __launch_bounds__(256) k_gemm_accum_ff(int64_t n, int K, int t, 
     }
     for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
       const int kk = idx / BN, c = idx % BN;
-      Bs[kk][c] = (k0 + kk < K && col0 + c < t) ? ff_from_double(Mg[(int64_t)(k0 + kk) * ldm + col0 + c])
-                                                 : ff_make(0.f, 0.f);
+      const float2 b = (k0 + kk < K && col0 + c < t) ? Mp[(int64_t)(k0 + kk) * ldm + col0 + c] : make_float2(0.f, 0.f);
+      Bs[kk][c] = ff_make(b.x, b.y);
     }
     __syncthreads();
 #pragma unroll
@@ -725,6 +725,15 @@ __global__ void __launch_bounds__(256) k_gemm_accum_ff(int64_t n, int K, int t, 
   }
 }
 
+// doubles -> the pairs nearest them, in place (rows x cols of leading dimension ld)
+__global__ void k_double_to_pairs(double* A, int64_t rows, int64_t ld, int cols) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  double* a = A + (i / cols) * ld + (i % cols);
+  const ff p = ff_from_double(*a);
+  *reinterpret_cast<float2*>(a) = make_float2(p.hi, p.lo);
+}
+
 // the pairs accumulated in Z's doubles -> their fp64 values
 __global__ void k_pairs_to_double(double* Z, int64_t n, int64_t ldz, int t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -746,16 +755,19 @@ void gemm_accum(int bulk, int s, int z_f32, int64_t n, int K, int t, const void*
   if (t <= 0 || K <= 0) return;
   dim3 grid((unsigned)((n + 63) / 64), (unsigned)((t + 63) / 64));
   if (bulk == LYAP_PREC_F32X2) {
-    // the column tile with the fewer padded columns: 64 wide, or 32 wide with 128-row tiles
-    const int w64 = (t + 63) / 64 * 64, w32 = (t + 31) / 32 * 32;
-    const bool narrow = w32 < w64;
-    dim3 gf(narrow ? (unsigned)((n + 127) / 128) : (unsigned)((n + 63) / 64), narrow ? (unsigned)(w32 / 32)
-                                                                                 : (unsigned)(w64 / 64));
+    // the column tile (16, 32 or 64 wide; 256, 128 or 64-row tiles) with the fewest padded
+    // columns: the pair products are the cost, re-reading the basis rows per column tile is not
+    const float2* Mp = reinterpret_cast<const float2*>(Mg);  // converted in place by the caller
+    const int w64 = (t + 63) / 64 * 64, w32 = (t + 31) / 32 * 32, w16 = (t + 15) / 16 * 16;
+    const int bn = w16 < w32 ? 16 : (w32 < w64 ? 32 : 64);
+    dim3 gf((unsigned)((n + 4096 / bn - 1) / (4096 / bn)), (unsigned)((t + bn - 1) / bn));
 #define LYAP_GFF(SS_)                                                                                          \
-  if (narrow)                                                                                                  \
-    k_gemm_accum_ff<SS_, 32><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float2*)Z, ldz);     \
+  if (bn == 16)                                                                                                \
+    k_gemm_accum_ff<SS_, 16><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mp, ldm, (float2*)Z, ldz);     \
+  else if (bn == 32)                                                                                           \
+    k_gemm_accum_ff<SS_, 32><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mp, ldm, (float2*)Z, ldz);     \
   else                                                                                                         \
-    k_gemm_accum_ff<SS_, 64><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mg, ldm, (float2*)Z, ldz)
+    k_gemm_accum_ff<SS_, 64><<<gf, 256, 0, st>>>(n, K, t, (const float*)Vb, ldv, Mp, ldm, (float2*)Z, ldz)
     switch (s) {
       case 1: LYAP_GFF(1); break;
       case 2: LYAP_GFF(2); break;
@@ -806,6 +818,12 @@ int second_pass(lyap_handle* h, int opi, const double* M, int ldm, int tk, void*
     const int g = (j - 1) / kb, c = (j - 1) % kb;
     return buf[g & 1] + (size_t)c * s * w;
   };
+  if (tk > 0 && bulk == LYAP_PREC_F32X2) {
+    // the pair GEMM reads M as pairs: rows 0..m s - 1, columns 0..tk - 1, converted in place
+    const int64_t tot = (int64_t)m * s * tk;
+    k_double_to_pairs<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(const_cast<double*>(M), (int64_t)m * s, ldm, tk);
+    h->launches += 1;
+  }
   if (tk > 0) {
     const int64_t tot = n * tk;
     if (z_f32) k_zero_cols<float><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((float*)Z, n, ldz, tk);

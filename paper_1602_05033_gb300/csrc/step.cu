@@ -48,12 +48,18 @@ struct NumF {
   static constexpr int kUnroll = 8;
   static constexpr int kMinBlocks = 2;
 };
+#ifndef LYAP_FF_UNROLL
+#define LYAP_FF_UNROLL 4
+#endif
+#ifndef LYAP_FF_MINB
+#define LYAP_FF_MINB 1
+#endif
 struct NumFF {
   using V = float;  // a row of S pairs is 2S floats: the S high parts, then the S low parts
   using R = ff;
   using Acc = ff;
-  static constexpr int kUnroll = 4;
-  static constexpr int kMinBlocks = 1;
+  static constexpr int kUnroll = LYAP_FF_UNROLL;
+  static constexpr int kMinBlocks = LYAP_FF_MINB;
 };
 
 // ---- row loads and stores (row i of a block with leading dimension ld, in values) ----------

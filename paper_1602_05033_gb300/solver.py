@@ -169,7 +169,7 @@ class Batch:
     """
 
     def __init__(self, problems, *, tol=1e-8, maxit=1000, precision="mixed", check_batch=32, pass2_blocks=16,
-                 inputs="device", device="cuda:0", val_dtype="f32"):
+                 inputs="device", device="cuda:0", val_dtype="f32", check_every=1):
         import torch
 
         self.torch = torch
@@ -182,6 +182,7 @@ class Batch:
         opt.precision = self.precision
         opt.check_batch = int(check_batch)
         opt.pass2_blocks = int(pass2_blocks)
+        opt.check_every = L.LYAP_CHECK_ADAPTIVE if check_every == "adaptive" else int(check_every)
         self.opt = opt
         self.s = [int(C.shape[1]) for _, C in problems]
         self.n = [int(A.shape[0]) for A, _ in problems]

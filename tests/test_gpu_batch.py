@@ -116,3 +116,28 @@ def test_batch_maxit_and_uneven_sizes(pkg):
     one.solve()
     assert ms[1] == one.m
     bt.close()
+
+
+def test_batch_adaptive_schedule_against_oracle(pkg):
+    """The batched solve under the adaptive check schedule: every instance stops at the oracle's
+    m (the skipped m before its first converged check are checked afterwards), its checked
+    history entries match the oracle's, and its factor matches on probes."""
+    probs = _small_batch(seed=11, count=6)
+    bt = pkg.Batch([(P.A, P.C1) for P in probs], tol=1e-9, maxit=400, precision="f64", check_every="adaptive")
+    assert bt.solve() == 0
+    st, ms = bt.status()
+    skipped = 0
+    for i, P in enumerate(probs):
+        ref = olyap.solve(P.A, P.C1, tol=1e-9, maxit=400)
+        assert st[i] == 0 and ms[i] == ref.m, (i, ms[i], ref.m)
+        h = bt.history(i)
+        chk = ~np.isnan(h)
+        skipped += int((~chk).sum())
+        assert chk[ms[i] - 1]
+        assert np.all(np.abs(h[chk] - ref.history[chk]) <= 1e-14 + 1e-10 * np.abs(ref.history[chk]))
+        Z = bt.factor(i).double().cpu().numpy()
+        Zo, _ = olyap.factor(P.A, P.C1, ref)
+        assert _xprobe(Z, Zo) <= 1e-8
+    print(f"adaptive batch: m {list(ms)}, skipped checks {skipped}")
+    assert skipped > 0
+    bt.close()
