@@ -333,6 +333,31 @@ int lyap_ek_cnn_grad(lyap_ek* e, const float* params, int K, const double* B, co
 int lyap_ek_param_count(void);
 int lyap_ek_destroy(lyap_ek* e);
 
+/* Generalised Lyapunov equation A X E + E X A + C C^T = 0 with E symmetric positive definite (the
+ * example with a mass matrix, Sec. 6).  With E = L L^T it is the standard equation for
+ * L^{-1} A L^{-T} and L^{-1} C, solved by Alg. 1-3 without forming L: the block Lanczos basis V
+ * is E-orthonormal (the Krylov space of E^{-1} A from E^{-1} C), T_m = V^T A V, and the history
+ * is that residual norm relative to ||L^{-1} C||_F^2.  Each step solves with E by Jacobi-
+ * preconditioned conjugate gradients to relative residual inner_tol (an E-solve that stops short
+ * of it ends the solve with LYAP_ERR_BREAKDOWN) and E-orthogonalises against every stored block
+ * twice.  The basis is stored (n x s per iteration, maxit + 1 blocks) and lyap_gen_factor returns
+ * Z with X ~= Z Z^T in the original coordinates.
+ *  A, E : CSR with fp64 values, same n (host or device memory, read during create); s in {1, 2, 4}
+ *  C    : n x s row-major fp64, memory kind c_mem */
+typedef struct lyap_gen lyap_gen;
+
+int lyap_gen_workspace_size(const lyap_csr* A, const lyap_csr* E, int s, int maxit, size_t* bytes);
+int lyap_gen_create(const lyap_csr* A, const lyap_csr* E, const double* C, int c_mem, int s,
+                    double tol, int maxit, double inner_tol, void* workspace, size_t ws_bytes,
+                    void* stream, lyap_gen** out);
+int lyap_gen_solve(lyap_gen* g, void* stream);
+int lyap_gen_residual_norm(lyap_gen* g, double* hist_host, int cap, int* m_out);
+/* Z: device fp64, n x tcap row-major, leading dimension ldz >= tcap */
+int lyap_gen_factor(lyap_gen* g, double* Z, int64_t ldz, int tcap, int* t_out, void* stream);
+/* out[0] solve ms, [1] solves with E, [2] their conjugate-gradient iterations, [3] the most in one */
+int lyap_gen_stats(lyap_gen* g, double* out, int cap);
+int lyap_gen_destroy(lyap_gen* g);
+
 #ifdef __cplusplus
 }
 #endif

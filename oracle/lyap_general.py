@@ -17,6 +17,13 @@ The factor uses the stored basis.  The two-pass device (Sec. 3.3) of ``lyap.fact
 the recurrence from the logged coefficients with a rounding different from the first pass's
 MGS sweeps, and on the transformed mass-matrix operators (||A~|| / |lambda_max(A~)| ~ 270)
 that replay drifts from the stored basis exponentially, by about 10^3 every five steps.
+
+For the same reason the basis loses orthogonality within a few tens of steps, after which the
+residual histories of two correct implementations part company (their roundings differ).  The
+default step therefore takes Alg. 2's block Gram-Schmidt (twice) against every stored block,
+not only V_{j-1} and V_j: in exact arithmetic the coefficients are the same (the other
+projections vanish), and in floating point the basis stays orthonormal to rounding, so the
+history is a function of the operator alone.  ``reorth=False`` gives the plain step of Alg. 2.
 """
 from __future__ import annotations
 
@@ -48,9 +55,51 @@ def transform(A, E, C):
     return L, At, Ct
 
 
-def solve(A, E, C, tol=1e-8, maxit=1000) -> GeneralResult:
+def lanczos_step_full(A, basis, Vcur):
+    """Alg. 2's step with the block Gram-Schmidt run (twice) against every stored block: W = A V_j;
+    for l = 1, 2 and i = 1..j: alpha = V_i^T W, W -= V_i alpha, with tau_{j-1,j} and tau_jj the sums
+    of the alphas of V_{j-1} and V_j; finally W = V_{j+1} tau_{j+1,j}.  ``basis`` holds V_1..V_j."""
+    s = Vcur.shape[1]
+    W = A @ Vcur
+    tau_prev = np.zeros((s, s))
+    tau_diag = np.zeros((s, s))
+    j = len(basis)
+    for _ in range(2):
+        for i, Vi in enumerate(basis, start=1):
+            alpha = Vi.T @ W
+            if i == j:
+                tau_diag += alpha
+            elif i == j - 1:
+                tau_prev += alpha
+            W = W - Vi @ alpha
+    Vnext, tau_next = lyap.qr_pos(W)
+    return Vnext, tau_prev, tau_diag, tau_next
+
+
+def solve_full(A, C, tol=1e-8, maxit=1000) -> lyap.SolveResult:
+    """Algorithm 1 (steps 1-7) with ``lanczos_step_full``; the check is Prop. 3.1 at every m."""
+    V1, log = lyap.start(C, keep_basis=True)
+    hist, converged, m = [], False, 0
+    for j in range(1, maxit + 1):
+        Vnext, tp, td, tn = lanczos_step_full(A, log.basis[:j], log.basis[j - 1])
+        log.tau_prev.append(tp)
+        log.tau_diag.append(td)
+        log.tau_next.append(tn)
+        log.basis.append(Vnext)
+        m = j
+        rel = lyap.residual_at(log, j)
+        hist.append(rel)
+        if rel <= tol:
+            converged = True
+            break
+    return lyap.SolveResult(log=log, history=np.array(hist), m=m, converged=converged, tol=tol)
+
+
+def solve(A, E, C, tol=1e-8, maxit=1000, reorth=True) -> GeneralResult:
     L, At, Ct = transform(A, E, C)
-    return GeneralResult(lyap.solve(At, Ct, tol=tol, maxit=maxit, keep_basis=True), L, At, Ct)
+    inner = solve_full(At, Ct, tol=tol, maxit=maxit) if reorth else lyap.solve(At, Ct, tol=tol, maxit=maxit,
+                                                                                keep_basis=True)
+    return GeneralResult(inner, L, At, Ct)
 
 
 def factor(res: GeneralResult, trunc_eps: float = 1e-12):

@@ -29,4 +29,4 @@ from ._lib import (  # noqa: F401
     lyap_workspace_size,
     status_string,
 )
-from .solver import Batch, ExtendedKrylov, Solver, csr_arrays  # noqa: F401
+from .solver import Batch, ExtendedKrylov, Generalized, Solver, csr_arrays  # noqa: F401

@@ -62,6 +62,13 @@ EXPORTED = (
     "lyap_ek_cnn_grad",
     "lyap_ek_param_count",
     "lyap_ek_destroy",
+    "lyap_gen_workspace_size",
+    "lyap_gen_create",
+    "lyap_gen_solve",
+    "lyap_gen_residual_norm",
+    "lyap_gen_factor",
+    "lyap_gen_stats",
+    "lyap_gen_destroy",
 )
 
 
@@ -153,6 +160,14 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_ek_cnn_grad.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int, P, P, DP, DP, P]
     lib.lyap_ek_param_count.argtypes = []
     lib.lyap_ek_destroy.argtypes = [P]
+    lib.lyap_gen_workspace_size.argtypes = [CSRP, CSRP, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
+    lib.lyap_gen_create.argtypes = [CSRP, CSRP, P, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double, P,
+                                    ct.c_size_t, P, ct.POINTER(P)]
+    lib.lyap_gen_solve.argtypes = [P, P]
+    lib.lyap_gen_residual_norm.argtypes = [P, DP, ct.c_int, IP]
+    lib.lyap_gen_factor.argtypes = [P, P, ct.c_int64, ct.c_int, IP, P]
+    lib.lyap_gen_stats.argtypes = [P, DP, ct.c_int]
+    lib.lyap_gen_destroy.argtypes = [P]
     lib.lyap_status_string.argtypes = [ct.c_int]
     lib.lyap_status_string.restype = ct.c_char_p
     for name in EXPORTED:
@@ -436,3 +451,61 @@ def lyap_ek_destroy(h: int) -> None:
 def lyap_destroy(h: int) -> None:
     if h:
         load().lyap_destroy(ct.c_void_p(h))
+
+
+def lyap_gen_workspace_size(A: lyap_csr, E: lyap_csr, s: int, maxit: int) -> int:
+    nb = ct.c_size_t(0)
+    st = load().lyap_gen_workspace_size(ct.byref(A), ct.byref(E), int(s), int(maxit), ct.byref(nb))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_gen_workspace_size")
+    return int(nb.value)
+
+
+def lyap_gen_create(A: lyap_csr, E: lyap_csr, C_ptr: int, c_mem: int, s: int, tol: float, maxit: int,
+                    inner_tol: float, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ct.c_void_p(0)
+    st = load().lyap_gen_create(ct.byref(A), ct.byref(E), ct.c_void_p(C_ptr), int(c_mem), int(s), float(tol),
+                                int(maxit), float(inner_tol), ct.c_void_p(ws_ptr), ct.c_size_t(ws_bytes),
+                                ct.c_void_p(stream), ct.byref(h))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_gen_create")
+    return h.value
+
+
+def lyap_gen_solve(h: int, stream: int) -> int:
+    st = load().lyap_gen_solve(ct.c_void_p(h), ct.c_void_p(stream))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_gen_solve")
+    return st
+
+
+def lyap_gen_residual_norm(h: int, cap: int):
+    import numpy as np
+
+    buf = np.full(max(cap, 1), np.nan)
+    m = ct.c_int(0)
+    st = load().lyap_gen_residual_norm(ct.c_void_p(h), buf.ctypes.data_as(ct.POINTER(ct.c_double)), int(cap),
+                                       ct.byref(m))
+    if st not in (LYAP_OK, LYAP_NOT_CONVERGED):
+        raise LyapError(st, "lyap_gen_residual_norm")
+    return buf[: m.value].copy(), m.value
+
+
+def lyap_gen_factor(h: int, Z_ptr: int, ldz: int, tcap: int, stream: int) -> int:
+    t = ct.c_int(0)
+    st = load().lyap_gen_factor(ct.c_void_p(h), ct.c_void_p(Z_ptr), ct.c_int64(ldz), int(tcap), ct.byref(t),
+                                ct.c_void_p(stream))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_gen_factor")
+    return t.value
+
+
+def lyap_gen_stats(h: int):
+    out = (ct.c_double * 4)()
+    load().lyap_gen_stats(ct.c_void_p(h), out, 4)
+    return list(out)
+
+
+def lyap_gen_destroy(h: int) -> None:
+    if h:
+        load().lyap_gen_destroy(ct.c_void_p(h))

@@ -685,6 +685,7 @@ void project(lyap_ek* e, const double* X, int nb, const double* Wm, cudaStream_t
   const int g = grid_for(e->n);
   dim3 grid(g, nb);
   switch (S) {
+    case 1: k_proj<1><<<grid, kT, 0, st>>>(X, e->n * S, nb, Wm, e->n, e->partials); break;
     case 2: k_proj<2><<<grid, kT, 0, st>>>(X, e->n * S, nb, Wm, e->n, e->partials); break;
     case 4: k_proj<4><<<grid, kT, 0, st>>>(X, e->n * S, nb, Wm, e->n, e->partials); break;
     case 8: k_proj<8><<<grid, kT, 0, st>>>(X, e->n * S, nb, Wm, e->n, e->partials); break;
@@ -695,6 +696,7 @@ void project(lyap_ek* e, const double* X, int nb, const double* Wm, cudaStream_t
 void subtract(lyap_ek* e, const double* X, int nb, double* Wm, cudaStream_t st) {
   const int g = grid_for(e->n) * 4;
   switch (e->S) {
+    case 1: k_subtract<1><<<g, kT, 0, st>>>(X, e->n * 1, nb, e->P, Wm, e->n); break;
     case 2: k_subtract<2><<<g, kT, 0, st>>>(X, e->n * 2, nb, e->P, Wm, e->n); break;
     case 4: k_subtract<4><<<g, kT, 0, st>>>(X, e->n * 4, nb, e->P, Wm, e->n); break;
     case 8: k_subtract<8><<<g, kT, 0, st>>>(X, e->n * 8, nb, e->P, Wm, e->n); break;
@@ -729,6 +731,7 @@ int cholqr2(lyap_ek* e, double* Wm, std::vector<double>& gamma, cudaStream_t st)
     LYAP_CUDA_TRY(cudaMemcpyAsync(e->dR, R.data(), sizeof(double) * S * S, cudaMemcpyHostToDevice, st));
     const int g = grid_for(e->n) * 4;
     switch (S) {
+      case 1: k_trsm<1><<<g, kT, 0, st>>>(Wm, e->n, e->dR); break;
       case 2: k_trsm<2><<<g, kT, 0, st>>>(Wm, e->n, e->dR); break;
       case 4: k_trsm<4><<<g, kT, 0, st>>>(Wm, e->n, e->dR); break;
       case 8: k_trsm<8><<<g, kT, 0, st>>>(Wm, e->n, e->dR); break;
@@ -938,14 +941,25 @@ int lyap_ek_workspace_size(const lyap_csr* A, int s, int maxit, int nx, int ny, 
   return LYAP_OK;
 }
 
-int lyap_ek_destroy(lyap_ek* e) {
-  if (!e) return LYAP_OK;
+}  // extern "C"
+
+namespace {
+// events and pinned host buffers of a context (the object itself stays)
+void ek_release(lyap_ek* e) {
   for (int i = 0; i < 4; ++i)
     if (e->ev[i]) cudaEventDestroy(e->ev[i]);
   if (e->hk.ev[0]) cudaEventDestroy(e->hk.ev[0]);
   if (e->hk.ev[1]) cudaEventDestroy(e->hk.ev[1]);
   if (e->hk.hist_host) cudaFreeHost(e->hk.hist_host);
   if (e->hk.flags_host) cudaFreeHost(e->hk.flags_host);
+}
+}  // namespace
+
+extern "C" {
+
+int lyap_ek_destroy(lyap_ek* e) {
+  if (!e) return LYAP_OK;
+  ek_release(e);
   delete e;
   return LYAP_OK;
 }
@@ -1216,5 +1230,328 @@ int lyap_ek_cnn_grad(lyap_ek* e, const float* params, int K, const double* B, co
 }
 
 int lyap_ek_param_count(void) { return kNW; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Generalised Lyapunov equation A X E + E X A + C C^T = 0 with E symmetric positive definite (the
+// mass-matrix example of Sec. 6).  With E = L L^T it is the standard equation for
+// A~ = L^{-1} A L^{-T} and C~ = L^{-1} C, whose solution is X~ = L^T X L.  L is never formed: the
+// block Lanczos basis of A~ is V~ = L^T V with V E-orthonormal (V^T E V = I) spanning the Krylov
+// space of E^{-1} A from E^{-1} C.  Then T_m = V~^T A~ V~ = V^T A V, C~ = V~_1 gamma with
+// C = E V_1 gamma, and the relation A~ V~_m = V~_m T_m + V~_{m+1} tau E_m^T holds, so the check
+// (Prop. 3.1 / Alg. 3) is the standard one on T_m and measures the transformed residual, and the
+// factor is Z = V_m (Q Ycheck) directly, since X = L^{-T} X~ L^{-1} = V Y V^T.
+// Step j: W = E^{-1} A V_j by conjugate gradients on E (Jacobi preconditioned; E is well
+// conditioned), E-orthogonalisation against every stored block twice (coefficients V_i^T (E W)
+// with E W by a sparse product), E-CholQR2, and tau_jj = V_j^T A V_j, tau_{j+1,j} = V_{j+1}^T A V_j.
+// The basis is stored: replaying the recurrence from the logged coefficients drifts on these
+// operators, so the factor is accumulated from the stored blocks.
+struct lyap_gen {
+  lyap_ek e;      // the CG solves (e.A = -E), block Gram-Schmidt, the check and factor view
+  Csr Aop{};      // A
+  double* EW = nullptr;
+  size_t total = 0;
+  int iters = 0, solves = 0, max_iters = 0;
+};
+
+namespace {
+
+struct GenLayout {
+  size_t csrA = 0, csrE = 0, basis = 0, AV = 0, EW = 0, C = 0, mdinv = 0, vec = 0, partials = 0, small = 0, log = 0,
+         hist = 0, flags = 0, chk = 0, check = 0, factor = 0, total = 0;
+  size_t factor_bytes = 0;
+};
+
+GenLayout gen_layout(const lyap_csr* A, const lyap_csr* E, int s, int maxit) {
+  GenLayout G;
+  const int64_t n = A->n;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off += lyap_align256((int64_t)bytes); return r; };
+  G.csrA = take(sizeof(int64_t) * (n + 1) + 8);
+  take(sizeof(int32_t) * A->nnz);
+  take(sizeof(double) * A->nnz);
+  G.csrE = take(sizeof(int64_t) * (n + 1) + 8);
+  take(sizeof(int32_t) * E->nnz);
+  take(sizeof(double) * E->nnz);
+  G.basis = take(sizeof(double) * (size_t)(maxit + 1) * n * s);
+  G.AV = take(sizeof(double) * n * s);
+  G.EW = take(sizeof(double) * n * s);
+  G.C = take(sizeof(double) * n * s);
+  G.mdinv = take(sizeof(double) * n);
+  G.vec = take(sizeof(double) * n * s * 5);
+  G.partials = take(sizeof(double) * (size_t)kGrid * (maxit + 2) * s * s);
+  G.small = take(sizeof(double) * ((size_t)(maxit + 2) * s * s + 128));
+  G.log = take(sizeof(double) * (size_t)(maxit + 1) * LOG_NREC * s * s);
+  G.hist = take(sizeof(double) * maxit);
+  G.flags = take(256);
+  G.chk = take(sizeof(int) * maxit);
+  G.check = take(std::max(check_slot_bytes(s, s * maxit), (size_t)1 << 20));
+  G.factor_bytes = factor_ws_bytes(s, s * maxit, 0);
+  G.factor = take(G.factor_bytes);
+  G.total = off;
+  return G;
+}
+
+__global__ void k_scale(double* __restrict__ v, int64_t n, double a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] *= a;
+}
+
+// CSR arrays into the workspace at offset off (fp64 values, scaled by sgn)
+int copy_csr(const lyap_csr* A, char* w, size_t off, double sgn, Csr* out, cudaStream_t st) {
+  const int64_t n = A->n;
+  int64_t* rp = at<int64_t>(w, off);
+  int32_t* cl = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(rp) + lyap_align256((int64_t)(sizeof(int64_t) * (n + 1) + 8)));
+  double* vl = reinterpret_cast<double*>(reinterpret_cast<char*>(cl) + lyap_align256((int64_t)(sizeof(int32_t) * A->nnz)));
+  const cudaMemcpyKind kind = A->mem == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (cudaMemcpyAsync(rp, A->rowptr, sizeof(int64_t) * (n + 1), kind, st) != cudaSuccess ||
+      cudaMemcpyAsync(cl, A->col, sizeof(int32_t) * A->nnz, kind, st) != cudaSuccess ||
+      cudaMemcpyAsync(vl, A->val, sizeof(double) * A->nnz, kind, st) != cudaSuccess)
+    return LYAP_ERR_CUDA;
+  if (sgn != 1.0) k_scale<<<grid_for(A->nnz) * 4, kT, 0, st>>>(vl, A->nnz, sgn);
+  *out = Csr{n, rp, cl, vl};
+  return LYAP_OK;
+}
+
+// W (n x s) E-orthonormalised twice (CholQR2 with Gram matrices W^T (E W)); gamma = R2 R1 (host)
+int cholqr2_E(lyap_gen* g, double* Wm, std::vector<double>& gamma, cudaStream_t st) {
+  lyap_ek* e = &g->e;
+  const int S = e->S;
+  std::vector<double> G(S * S), R(S * S), acc(S * S, 0.0);
+  for (int pass = 0; pass < 2; ++pass) {
+    spmm(e->A, S, Wm, S, g->EW, S, -1.0, st);  // E W (e->A holds -E)
+    project(e, Wm, 1, g->EW, st);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(G.data(), e->P, sizeof(double) * S * S, cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!chol_upper_host(G.data(), R.data(), S)) return LYAP_ERR_BREAKDOWN;
+    LYAP_CUDA_TRY(cudaMemcpyAsync(e->dR, R.data(), sizeof(double) * S * S, cudaMemcpyHostToDevice, st));
+    const int gt = grid_for(e->n) * 4;
+    switch (S) {
+      case 1: k_trsm<1><<<gt, kT, 0, st>>>(Wm, e->n, e->dR); break;
+      case 2: k_trsm<2><<<gt, kT, 0, st>>>(Wm, e->n, e->dR); break;
+      case 4: k_trsm<4><<<gt, kT, 0, st>>>(Wm, e->n, e->dR); break;
+    }
+    if (pass == 0) acc = R;
+    else {
+      std::vector<double> t(S * S, 0.0);
+      for (int i = 0; i < S; ++i)
+        for (int j = 0; j < S; ++j)
+          for (int k = 0; k < S; ++k) t[i * S + j] += R[i * S + k] * acc[k * S + j];
+      acc = t;
+    }
+    LYAP_CUDA_TRY(cudaStreamSynchronize(st));  // dR is reused
+  }
+  gamma = acc;
+  return LYAP_OK;
+}
+
+// dst <- E^{-1} B (n x s) by conjugate gradients on E; counts the iterations
+int solve_E(lyap_gen* g, const double* B, double* dst, cudaStream_t st) {
+  lyap_ek* e = &g->e;
+  int its = 0, used = 0;
+  const int rc = pcg(e, B, e->s, 0, &its, &used, st);  // (-E) X = B
+  if (rc == LYAP_ERR_NONFINITE) return rc;
+  g->iters += its;
+  g->solves += 1;
+  g->max_iters = std::max(g->max_iters, its);
+  if (rc == LYAP_NOT_CONVERGED) return LYAP_ERR_BREAKDOWN;  // an E-solve short of its tolerance
+  const int gcp = (int)std::min<int64_t>((e->n * e->s + kT - 1) / kT, 8192);
+  k_copy_cols<<<gcp, kT, 0, st>>>(e->x, e->s, dst, e->s, 0, e->s, e->n, -1.0);
+  return LYAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lyap_gen_workspace_size(const lyap_csr* A, const lyap_csr* E, int s, int maxit, size_t* bytes) {
+  if (!A || !E || !bytes || (s != 1 && s != 2 && s != 4) || maxit < 1) return LYAP_ERR_ARG;
+  int rc = validate_csr(A);
+  if (rc == LYAP_OK) rc = validate_csr(E);
+  if (rc != LYAP_OK) return rc;
+  if (A->val_dtype != LYAP_F64 || E->val_dtype != LYAP_F64 || E->n != A->n) return LYAP_ERR_ARG;
+  *bytes = gen_layout(A, E, s, maxit).total;
+  return LYAP_OK;
+}
+
+int lyap_gen_destroy(lyap_gen* g) {
+  if (!g) return LYAP_OK;
+  ek_release(&g->e);
+  delete g;
+  return LYAP_OK;
+}
+
+int lyap_gen_create(const lyap_csr* A, const lyap_csr* E, const double* C, int c_mem, int s, double tol, int maxit,
+                    double inner_tol, void* workspace, size_t ws_bytes, void* stream, lyap_gen** out) {
+  if (!out || !C || !(tol >= 0.0) || !(inner_tol > 0.0)) return LYAP_ERR_ARG;
+  size_t need = 0;
+  int rc = lyap_gen_workspace_size(A, E, s, maxit, &need);
+  if (rc != LYAP_OK) return rc;
+  if (!workspace || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LYAP_ERR_WORKSPACE;
+  if (c_mem != LYAP_MEM_DEVICE && c_mem != LYAP_MEM_HOST) return LYAP_ERR_ARG;
+  lyap_gen* g = new (std::nothrow) lyap_gen();
+  if (!g) return LYAP_ERR_ARG;
+  auto fail = [&](int code) {
+    lyap_gen_destroy(g);
+    return code;
+  };
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const GenLayout G = gen_layout(A, E, s, maxit);
+  lyap_ek* e = &g->e;
+  e->s = s;
+  e->S = s;
+  e->maxit = maxit;
+  e->n = A->n;
+  e->tol = tol;
+  e->inner_tol = inner_tol;
+  e->ws = static_cast<char*>(workspace);
+  g->total = G.total;
+  const int64_t n = A->n;
+  char* w = e->ws;
+  if (copy_csr(A, w, G.csrA, 1.0, &g->Aop, st) != LYAP_OK || copy_csr(E, w, G.csrE, -1.0, &e->A, st) != LYAP_OK)
+    return fail(LYAP_ERR_CUDA);
+  e->basis = at<double>(w, G.basis);
+  e->AV = at<double>(w, G.AV);
+  g->EW = at<double>(w, G.EW);
+  e->C = at<double>(w, G.C);
+  e->mdinv = at<double>(w, G.mdinv);
+  double* v = at<double>(w, G.vec);
+  e->x = v;
+  e->r = v + n * s;
+  e->z = v + 2 * n * s;
+  e->p = v + 3 * n * s;
+  e->q = v + 4 * n * s;
+  e->partials = at<double>(w, G.partials);
+  e->small = at<double>(w, G.small);
+  e->sc = e->small + 32;
+  e->dR = e->small + 64;
+  e->P = e->small + 128;
+  e->log = at<double>(w, G.log);
+  if (cudaMemcpyAsync(e->C, C, sizeof(double) * n * s,
+                      c_mem == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return fail(LYAP_ERR_CUDA);
+  k_mdinv<<<grid_for(n) * 4, kT, 0, st>>>(e->A, e->mdinv);  // 1 / diag(E)
+  lyap_handle& hk = e->hk;
+  hk.plan.s = s;
+  hk.plan.sylv = 0;
+  hk.plan.bulk = LYAP_PREC_F64;
+  hk.plan.maxit = maxit;
+  hk.plan.nmax = s * maxit;
+  hk.plan.check_batch = 1;
+  hk.plan.check_batch_req = 1;
+  hk.plan.factor_bytes = G.factor_bytes;
+  hk.s = s;
+  hk.tol = tol;
+  lyap_default_options(&hk.opt);
+  hk.opt.maxit = maxit;
+  hk.op[0].n = n;
+  hk.op[0].log = e->log;
+  hk.hist = at<double>(w, G.hist);
+  hk.flags = at<int>(w, G.flags);
+  hk.chk_err = at<int>(w, G.chk);
+  hk.check_ws = w + G.check;
+  hk.factor_ws = w + G.factor;
+  for (int i = 0; i < 8; ++i) hk.ev[i] = nullptr;
+  if (cudaEventCreate(&hk.ev[0]) != cudaSuccess || cudaEventCreate(&hk.ev[1]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventCreate(&e->ev[i]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  if (cudaMallocHost(&hk.hist_host, sizeof(double) * maxit) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  if (cudaMallocHost(&hk.flags_host, sizeof(int) * 8) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  *out = g;
+  return LYAP_OK;
+}
+
+int lyap_gen_solve(lyap_gen* g, void* stream) {
+  if (!g) return LYAP_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lyap_ek* e = &g->e;
+  const int64_t n = e->n;
+  const int s = e->s, SS = s * s;
+  lyap_handle& hk = e->hk;
+  cudaEventRecord(e->ev[0], st);
+  k_init_ek<<<(e->maxit + 255) / 256, 256, 0, st>>>(hk.hist, hk.flags, hk.chk_err, e->maxit);
+  LYAP_CUDA_TRY(cudaMemsetAsync(e->log, 0, sizeof(double) * (size_t)(e->maxit + 1) * LOG_NREC * SS, st));
+  hk.solved = 0;
+  hk.factored = 0;
+  g->iters = g->solves = g->max_iters = 0;
+  // V_1 gamma = E^{-1} C with V_1 E-orthonormal: C = E V_1 gamma, C~ = V~_1 gamma
+  double* V1 = e->basis;
+  int rc = solve_E(g, e->C, V1, st);
+  if (rc != LYAP_OK) return rc;
+  std::vector<double> gamma;
+  rc = cholqr2_E(g, V1, gamma, st);
+  if (rc != LYAP_OK) return rc;
+  {
+    // record 0: gamma and beta = ||C~||_F = ||gamma||_F
+    double b2 = 0.0;
+    for (double x : gamma) b2 += x * x;
+    std::vector<double> rec(LOG_NREC * SS, 0.0);
+    for (int k = 0; k < SS; ++k) rec[REC_TNEXT * SS + k] = gamma[k];
+    rec[REC_TDIAG * SS] = sqrt(b2);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(e->log, rec.data(), sizeof(double) * rec.size(), cudaMemcpyHostToDevice, st));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  int result = LYAP_NOT_CONVERGED, m_final = e->maxit, done = 0;
+  for (int j = 1; j <= e->maxit; ++j) {
+    double* Vj = e->basis + (size_t)(j - 1) * n * s;
+    double* Vn = e->basis + (size_t)j * n * s;
+    spmm(g->Aop, s, Vj, s, e->AV, s, 1.0, st);  // A V_j
+    rc = solve_E(g, e->AV, Vn, st);            // W = E^{-1} A V_j
+    if (rc != LYAP_OK) return rc;
+    // E-orthogonalisation against every stored block, twice, then E-CholQR2
+    for (int pass = 0; pass < 2; ++pass) {
+      spmm(e->A, s, Vn, s, g->EW, s, -1.0, st);
+      project(e, e->basis, j, g->EW, st);
+      subtract(e, e->basis, j, Vn, st);
+    }
+    rc = cholqr2_E(g, Vn, gamma, st);
+    if (rc != LYAP_OK) return rc;
+    // tau_jj = V_j^T A V_j, tau_{j+1,j} = V_{j+1}^T A V_j (consecutive blocks)
+    project(e, Vj, 2, e->AV, st);
+    double* rec = e->log + (size_t)j * LOG_NREC * SS;
+    LYAP_CUDA_TRY(cudaMemcpyAsync(rec + REC_TDIAG * SS, e->P, sizeof(double) * SS, cudaMemcpyDeviceToDevice, st));
+    LYAP_CUDA_TRY(cudaMemcpyAsync(rec + REC_TNEXT * SS, e->P + SS, sizeof(double) * SS, cudaMemcpyDeviceToDevice, st));
+    launch_check_batch(&hk, j, j, st);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(hk.flags_host, hk.flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+    LYAP_CUDA_TRY(cudaGetLastError());
+    done = j;
+    hk.lanczos_done = j;
+    const int rs = round_status(&hk);
+    if (rs != LYAP_OK) return rs;
+    if (hk.flags_host[1] != INT_MAX) {
+      m_final = hk.flags_host[1];
+      result = LYAP_OK;
+      break;
+    }
+  }
+  e->m = m_final;
+  e->done = done;
+  rc = solve_end(&hk, done, m_final, result, st);
+  if (rc != LYAP_OK) return rc;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e->ev[0], hk.ev[1]);
+  e->times[0] = ms;
+  return result;
+}
+
+int lyap_gen_residual_norm(lyap_gen* g, double* hist, int cap, int* m_out) {
+  if (!g) return LYAP_ERR_ARG;
+  return lyap_residual_norm(&g->e.hk, hist, cap, m_out);
+}
+
+int lyap_gen_factor(lyap_gen* g, double* Z, int64_t ldz, int tcap, int* t_out, void* stream) {
+  if (!g || !Z || !t_out || !g->e.hk.solved || ldz < tcap) return LYAP_ERR_ARG;
+  return run_factor_basis(&g->e.hk, g->e.basis, g->e.n, Z, ldz, tcap, t_out, static_cast<cudaStream_t>(stream));
+}
+
+// out[0] solve ms, [1] E-solves, [2] their conjugate-gradient iterations in all, [3] the most in one
+int lyap_gen_stats(lyap_gen* g, double* out, int cap) {
+  if (!g || !out) return LYAP_ERR_ARG;
+  const double v[4] = {g->e.times[0], (double)g->solves, (double)g->iters, (double)g->max_iters};
+  for (int k = 0; k < 4 && k < cap; ++k) out[k] = v[k];
+  return LYAP_OK;
+}
 
 }  // extern "C"

@@ -308,3 +308,67 @@ class ExtendedKrylov:
             self.close()
         except Exception:
             pass
+
+
+class Generalized:
+    """A X E + E X A + C C^T = 0 with E symmetric positive definite (lyap_gen_*): block Lanczos
+    with an E-orthonormal stored basis; the solves with E by Jacobi-preconditioned CG."""
+
+    def __init__(self, A, E, C, *, tol=1e-8, maxit=300, inner_tol=1e-13, device="cuda:0"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n = int(A.shape[0])
+        self.s = int(C.shape[1])
+        self.maxit = int(maxit)
+        self._keep = []
+        csr = []
+        for M in (A, E):
+            rp, cl, vl = csr_arrays(M)
+            arrs = [torch.from_numpy(x).to(self.device) for x in (rp, cl, vl)]
+            self._keep.append(arrs)
+            c = L.lyap_csr()
+            c.n, c.nnz = self.n, cl.shape[0]
+            c.rowptr, c.col, c.val = (a.data_ptr() for a in arrs)
+            c.val_dtype, c.mem = L.LYAP_F64, L.LYAP_MEM_DEVICE
+            csr.append(c)
+        self.ws_bytes = L.lyap_gen_workspace_size(csr[0], csr[1], self.s, self.maxit)
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+            self.stream = torch.cuda.current_stream(self.device).cuda_stream
+        self._C = torch.from_numpy(np.ascontiguousarray(C, dtype=np.float64)).to(self.device)
+        self.h = L.lyap_gen_create(csr[0], csr[1], self._C.data_ptr(), L.LYAP_MEM_DEVICE, self.s, tol, self.maxit,
+                                   inner_tol, self.ws.data_ptr(), self.ws_bytes, self.stream)
+        self.m = 0
+
+    def solve(self) -> int:
+        st = L.lyap_gen_solve(self.h, self.stream)
+        _, self.m = L.lyap_gen_residual_norm(self.h, 0)
+        return st
+
+    def history(self):
+        return L.lyap_gen_residual_norm(self.h, self.maxit)[0]
+
+    def factor(self, tcap=None):
+        t = self.torch
+        if tcap is None:
+            tcap = max(1, self.s * self.m)
+        Z = t.zeros((self.n, tcap), dtype=t.float64, device=self.device)
+        tk = L.lyap_gen_factor(self.h, Z.data_ptr(), tcap, tcap, self.stream)
+        return Z[:, :tk]
+
+    def stats(self):
+        v = L.lyap_gen_stats(self.h)
+        return {"solve_ms": v[0], "e_solves": int(v[1]), "cg_iterations": int(v[2]), "cg_max": int(v[3])}
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lyap_gen_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
