@@ -19,5 +19,7 @@ ek         extended Krylov space K_m(A, C) + K_m(A^{-1}, A^{-1} C) with exact in
 cnn        convolutional preconditioner of the inner solves: forward, gradients, losses
 pcg        inner solves with A by conjugate gradients: Jacobi, IC(0) and MIC(0) preconditioning
 learned_factor   a network predicting the IC(0)-pattern factor values: loss, gradients
+neumann_ic       IC(0) applied by a truncated Neumann series (products only), and the network-corrected
+                 factor values trained with the energy-norm loss on solve pairs: loss, gradients, Adam
 """
 from . import lyap, sylvester, explicit  # noqa: F401
