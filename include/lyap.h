@@ -298,15 +298,27 @@ int lyap_batch_destroy(lyap_batch* b);
  * Galerkin projection onto K_m(A, C) + K_m(A^{-1}, A^{-1} C): blocks of 2s columns, W =
  * [A V_j^(1), A^{-1} V_j^(2)], block Gram-Schmidt against every stored block (twice; Sec. 4's
  * three-term version loses orthogonality quickly in floating point) and CholQR2; T_m by explicit
- * projection; the convergence check is Prop. 3.1 / Alg. 3 with block size 2s.  The solves with A
- * are conjugate gradients on -A (SPD) to relative residual inner_tol, preconditioned by Jacobi
- * scaling or by a convolutional network on the operator's nx x ny grid (three 3x3 convolutions,
- * 1 -> 16 -> 16 -> 1 channels, ReLU, bf16 activations) trained on the solve pairs (b, A^{-1} b) of
- * the method's first inner solves with the energy-norm loss.  The paper uses direct solves; the
- * iterative solves and the network are additions.
+ * projection; the convergence check is Prop. 3.1 / Alg. 3 with block size 2s.  The paper applies
+ * A^{-1} by direct solves; here they are conjugate gradients on M = -A (SPD) to relative
+ * residual inner_tol, with one of three preconditioners:
+ *   0  Jacobi scaling;
+ *   1  IC(0) of M (zero fill, Meijerink and van der Vorst) for a 5-point operator on the nx x ny
+ *      grid, factored on the device along the grid's anti-diagonals and applied as
+ *      P = B^T B with B = sum_{t=0}^{3} T^t D^{-1}, T = -D^{-1} N (L = D + N), a truncated Neumann
+ *      series of L^{-1}: sparse products only, symmetric positive definite by construction;
+ *   2  the same application with factor values corrected by a network (three 3x3 convolutions,
+ *      5 -> 16 -> 16 -> 3 channels, ReLU, bf16 activations, fp32 accumulation, the 16 -> 16 layer
+ *      on the tensor cores): d = d0 exp(y0), lw = lw0 (1 + y1), ls = ls0 (1 + y2) from the
+ *      operator's stencil row over its diagonal, trained on the device with Adam on the solve
+ *      pairs (b, A^{-1} b) of the method's first inner solves (the first is A^{-1} C), with the
+ *      energy-norm loss (1/K) sum_k ||P b_k - x_k||_M^2 / ||x_k||_M^2.  IC(0) judges it: the trained
+ *      network is used only when its loss is below IC(0)'s, and a network-preconditioned solve that
+ *      needs more than twice the last IC(0) solve's iterations is redone with IC(0).
  *  A : CSR with fp64 values (host or device memory, read during create); s in {1, 2, 4}
  *  C : n x s row-major fp64, memory kind c_mem
- *  nx, ny : grid of the unknowns (x fastest, nx * ny = n) for the network; 0, 0 for none
+ *  nx, ny : grid of the unknowns (x fastest, nx * ny = n) for preconditioners 1 and 2; 0, 0 for
+ *           none.  IC(0) needs a 5-point pattern, positive diagonal, positive pivots and nx <= 1024
+ *           (lyap_ek_precond_status tells).
  * The basis is stored (n x 2s per iteration, maxit + 1 blocks) and the factor is formed from it. */
 typedef struct lyap_ek lyap_ek;
 
@@ -314,22 +326,33 @@ int lyap_ek_workspace_size(const lyap_csr* A, int s, int maxit, int nx, int ny, 
 int lyap_ek_create(const lyap_csr* A, const double* C, int c_mem, int s, double tol, int maxit,
                    double inner_tol, int nx, int ny, void* workspace, size_t ws_bytes, void* stream,
                    lyap_ek** out);
-/* precond 0: Jacobi; 1: the network, trained with train_iters Adam steps (learning rate lr)
- * once train_steps inner solves (with Jacobi) have produced its training pairs. */
-int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, float lr, void* stream);
+/* 0 when IC(0) exists on the context's grid; otherwise a bit set: 1 an entry outside the
+ * 5-point pattern, 2 a non-positive diagonal, 4 a non-positive pivot, 8 nx > 1024; -1 no grid. */
+int lyap_ek_precond_status(lyap_ek* e);
+/* precond 0 Jacobi, 1 IC(0), 2 the network: the first train_solves inner solves use IC(0) and
+ * provide the training pairs (at most 4 columns), then train_iters Adam steps with learning
+ * rate lr; LYAP_ERR_ARG when preconditioner 1 or 2 is not available. */
+int lyap_ek_solve(lyap_ek* e, int precond, int train_solves, int train_iters, float lr, void* stream);
 int lyap_ek_residual_norm(lyap_ek* e, double* hist_host, int cap, int* m_out);
 /* Z: device fp64, n x tcap row-major, leading dimension ldz >= tcap */
 int lyap_ek_factor(lyap_ek* e, double* Z, int64_t ldz, int tcap, int* t_out, void* stream);
-/* out[0] solve ms, [1] training ms, [2] training loss before, [3] after, [4] inner solves,
- * [5] network-preconditioned solves that were redone with Jacobi (non-finite, or more than 3x the
- * last Jacobi solve's iterations), then each inner solve's iteration count (negative when the
- * network's solve was kept) */
+/* out[0] solve ms, [1] training ms, [2] training loss before (IC(0)'s), [3] after, [4] inner
+ * solves ns, [5] network-preconditioned solves redone with IC(0), [6] 1 when the trained
+ * network was accepted, then the ns iteration counts, then the ns preconditioner kinds. */
 int lyap_ek_stats(lyap_ek* e, double* out, int cap);
 /* Energy-norm loss and gradient of the network for caller parameters (host floats, length
- * lyap_ek_param_count()) over K device pairs (n x K column-major B and X with A X = B); grad
- * is a host array of the same length.  Exposes the training kernels for testing. */
-int lyap_ek_cnn_grad(lyap_ek* e, const float* params, int K, const double* B, const double* X,
+ * lyap_ek_param_count(); layout w1[16][5][9], b1[16], w2[16][16][9], b2[16], w3[3][16][9],
+ * b3[3], tap k = 3 dy + dx reading (x + dx - 1, y + dy - 1)) over K <= 4 device pairs (n x K
+ * column-major B and X with A X = B); grad is a host array of the same length.  Overwrites the
+ * context's network parameters. */
+int lyap_ek_net_grad(lyap_ek* e, const float* params, int K, const double* B, const double* X,
                      double* loss, double* grad, void* stream);
+/* Z = P R for K <= 4 device columns (n x K column-major): kind 1 IC(0), kind 2 the network's
+ * values (with params, host, when not NULL: then they replace the context's parameters). */
+int lyap_ek_precond_apply(lyap_ek* e, int kind, const float* params, int K, const double* R,
+                          double* Z, void* stream);
+/* The factor values d (diagonal), lw (west), ls (south) of kind 1 or 2 into host arrays of n. */
+int lyap_ek_precond_values(lyap_ek* e, int kind, double* d, double* lw, double* ls);
 int lyap_ek_param_count(void);
 int lyap_ek_destroy(lyap_ek* e);
 

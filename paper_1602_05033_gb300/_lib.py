@@ -59,7 +59,10 @@ EXPORTED = (
     "lyap_ek_residual_norm",
     "lyap_ek_factor",
     "lyap_ek_stats",
-    "lyap_ek_cnn_grad",
+    "lyap_ek_net_grad",
+    "lyap_ek_precond_apply",
+    "lyap_ek_precond_values",
+    "lyap_ek_precond_status",
     "lyap_ek_param_count",
     "lyap_ek_destroy",
     "lyap_gen_workspace_size",
@@ -157,7 +160,10 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_ek_residual_norm.argtypes = [P, DP, ct.c_int, IP]
     lib.lyap_ek_factor.argtypes = [P, P, ct.c_int64, ct.c_int, IP, P]
     lib.lyap_ek_stats.argtypes = [P, DP, ct.c_int]
-    lib.lyap_ek_cnn_grad.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int, P, P, DP, DP, P]
+    lib.lyap_ek_net_grad.argtypes = [P, ct.POINTER(ct.c_float), ct.c_int, P, P, DP, DP, P]
+    lib.lyap_ek_precond_apply.argtypes = [P, ct.c_int, ct.POINTER(ct.c_float), ct.c_int, P, P, P]
+    lib.lyap_ek_precond_values.argtypes = [P, ct.c_int, DP, DP, DP]
+    lib.lyap_ek_precond_status.argtypes = [P]
     lib.lyap_ek_param_count.argtypes = []
     lib.lyap_ek_destroy.argtypes = [P]
     lib.lyap_gen_workspace_size.argtypes = [CSRP, CSRP, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
@@ -427,7 +433,7 @@ def lyap_ek_param_count() -> int:
     return int(load().lyap_ek_param_count())
 
 
-def lyap_ek_cnn_grad(h: int, params, K: int, B_ptr: int, X_ptr: int, stream: int):
+def lyap_ek_net_grad(h: int, params, K: int, B_ptr: int, X_ptr: int, stream: int):
     import numpy as np
 
     nw = lyap_ek_param_count()
@@ -435,12 +441,41 @@ def lyap_ek_cnn_grad(h: int, params, K: int, B_ptr: int, X_ptr: int, stream: int
     assert p.size == nw
     loss = ct.c_double(0.0)
     grad = np.zeros(nw)
-    st = load().lyap_ek_cnn_grad(ct.c_void_p(h), p.ctypes.data_as(ct.POINTER(ct.c_float)), int(K), ct.c_void_p(B_ptr),
+    st = load().lyap_ek_net_grad(ct.c_void_p(h), p.ctypes.data_as(ct.POINTER(ct.c_float)), int(K), ct.c_void_p(B_ptr),
                                  ct.c_void_p(X_ptr), ct.byref(loss), grad.ctypes.data_as(ct.POINTER(ct.c_double)),
                                  ct.c_void_p(stream))
     if st != LYAP_OK:
-        raise LyapError(st, "lyap_ek_cnn_grad")
+        raise LyapError(st, "lyap_ek_net_grad")
     return loss.value, grad
+
+
+def lyap_ek_precond_apply(h: int, kind: int, params, K: int, R_ptr: int, Z_ptr: int, stream: int) -> None:
+    import numpy as np
+
+    pp = None
+    if params is not None:
+        arr = np.ascontiguousarray(params, dtype=np.float32)
+        assert arr.size == lyap_ek_param_count()
+        pp = arr.ctypes.data_as(ct.POINTER(ct.c_float))
+    st = load().lyap_ek_precond_apply(ct.c_void_p(h), int(kind), pp, int(K), ct.c_void_p(R_ptr), ct.c_void_p(Z_ptr),
+                                      ct.c_void_p(stream))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_precond_apply")
+
+
+def lyap_ek_precond_values(h: int, kind: int, n: int):
+    import numpy as np
+
+    d, lw, ls = np.zeros(n), np.zeros(n), np.zeros(n)
+    st = load().lyap_ek_precond_values(ct.c_void_p(h), int(kind), *(a.ctypes.data_as(ct.POINTER(ct.c_double))
+                                                                      for a in (d, lw, ls)))
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_precond_values")
+    return d, lw, ls
+
+
+def lyap_ek_precond_status(h: int) -> int:
+    return int(load().lyap_ek_precond_status(ct.c_void_p(h)))
 
 
 def lyap_ek_destroy(h: int) -> None:

@@ -38,7 +38,7 @@ def _newer(target: str, deps: list[str]) -> bool:
 
 def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "ff.cuh"), os.path.join(INCLUDE, "lyap.h")]
+    headers = [os.path.join(CSRC, h) for h in ("common.cuh", "ff.cuh", "ekprec.cuh")] + [os.path.join(INCLUDE, "lyap.h")]
     extra = extra or []
     cc = nvcc()
 

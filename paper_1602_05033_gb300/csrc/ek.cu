@@ -23,13 +23,8 @@
 namespace {
 
 constexpr int kT = 256;
-constexpr int kCh = 16;              // CNN channels
 constexpr int kGrid = 304;           // CTAs of the reduction kernels (fixed: deterministic sums)
-constexpr int kTile = 1024;          // pixels per weight-gradient tile
-constexpr int kNW = kCh * 9 + kCh + kCh * kCh * 9 + kCh + kCh * 9 + 1;  // CNN parameters
-// parameter offsets: w1 [c][k], b1 [c], w2 [co][ci][k], b2 [co], w3 [ci][k], b3
-constexpr int oW1 = 0, oB1 = oW1 + kCh * 9, oW2 = oB1 + kCh, oB2 = oW2 + kCh * kCh * 9, oW3 = oB2 + kCh,
-              oB3 = oW3 + kCh * 9;
+constexpr int kTile = 1024;          // pixels per weight-gradient tile of the CUDA-core layers
 
 struct Csr {
   int64_t n;
@@ -332,184 +327,8 @@ __global__ void k_cg_conv(const double* __restrict__ rr, double* __restrict__ sc
   if (!(rr[c] > tol2 * q[4])) q[5] = 0.0;
 }
 
-// ---- convolutional preconditioner (bf16 activations, fp32 accumulation) --------------------
-struct Img {
-  int nx, ny;
-};
-
-__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
-
-// x0 = bf16(r_c / ||r_c||) for column c of r (leading dimension s)
-__global__ void k_cnn_in(const double* __restrict__ r, int s, int c, const double* __restrict__ rr,
-                         __nv_bfloat16* __restrict__ x0, int64_t n) {
-  const double inv = rr[0] > 0.0 ? 1.0 / sqrt(rr[0]) : 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x0[i] = __float2bfloat16((float)(r[i * s + c] * inv));
-}
-
-// out[co][p] = act(b[co] + sum_ci sum_taps w[co][ci][k] in[ci](p + tap)); weights read as bf16
-template <int CI, int CO, bool RELU>
-__global__ void k_conv(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wq,
-                       const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, float* __restrict__ out32, Img im) {
-  __shared__ float w[CO * CI * 9];
-  __shared__ float b[CO];
-  for (int k = threadIdx.x; k < CO * CI * 9; k += blockDim.x) w[k] = bf(wq[k]);
-  for (int k = threadIdx.x; k < CO; k += blockDim.x) b[k] = bias[k];
-  __syncthreads();
-  const int64_t n = (int64_t)im.nx * im.ny;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(p / im.nx), x = (int)(p % im.nx);
-    float acc[CO];
-#pragma unroll
-    for (int co = 0; co < CO; ++co) acc[co] = b[co];
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      const int yy = y + dy - 1;
-      if (yy < 0 || yy >= im.ny) continue;
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        const int xx = x + dx - 1;
-        if (xx < 0 || xx >= im.nx) continue;
-        const int64_t q = (int64_t)yy * im.nx + xx;
-#pragma unroll
-        for (int ci = 0; ci < CI; ++ci) {
-          const float v = bf(in[(int64_t)ci * n + q]);
-#pragma unroll
-          for (int co = 0; co < CO; ++co) acc[co] = fmaf(w[(co * CI + ci) * 9 + dy * 3 + dx], v, acc[co]);
-        }
-      }
-    }
-#pragma unroll
-    for (int co = 0; co < CO; ++co) {
-      const float v = RELU ? fmaxf(acc[co], 0.f) : acc[co];
-      if (out) out[(int64_t)co * n + p] = __float2bfloat16(v);
-      if (out32) out32[(int64_t)co * n + p] = v;
-    }
-  }
-}
-
-// preconditioned residual z_c = mdinv r_c - ||r_c|| y: Jacobi scaling of M = -A plus the network's
-// correction (the network approximates A^{-1} - diag(A)^{-1} on unit residuals; z ~ M^{-1} r)
-__global__ void k_cnn_out(const float* __restrict__ y, const double* __restrict__ rr, const double* __restrict__ mdinv,
-                          const double* __restrict__ r, double* __restrict__ z, int s, int c, int64_t n) {
-  const double sc = -sqrt(fmax(rr[0], 0.0));
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    z[i * s + c] = mdinv[i] * r[i * s + c] + sc * (double)y[i];
-}
-
-// y += r / diag(A) for the unit residual b / ||b|| (||b||^2 in bb[0]): the Jacobi part of the
-// preconditioner in the training loss
-__global__ void k_add_jacobi(float* __restrict__ y, const double* __restrict__ mdinv, const double* __restrict__ b,
-                             const double* __restrict__ bb, int64_t n) {
-  const double inv = 1.0 / sqrt(bb[0]);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] += (float)(-mdinv[i] * b[i] * inv);
-}
-
-// backward through one convolution: gin[ci][p] = mask(ci, p) * sum_co sum_taps w[co][ci][k] gout[co](p - tap)
-// (mask: the layer input's ReLU, from its bf16 activation > 0); gout fp32
-template <int CI, int CO>
-__global__ void k_conv_bwd_data(const float* __restrict__ gout, const __nv_bfloat16* __restrict__ wq,
-                                const __nv_bfloat16* __restrict__ act_in, float* __restrict__ gin, Img im) {
-  __shared__ float w[CO * CI * 9];
-  for (int k = threadIdx.x; k < CO * CI * 9; k += blockDim.x) w[k] = bf(wq[k]);
-  __syncthreads();
-  const int64_t n = (int64_t)im.nx * im.ny;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int y = (int)(p / im.nx), x = (int)(p % im.nx);
-    float acc[CI];
-#pragma unroll
-    for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-      const int yy = y - (dy - 1);  // the output at yy used the input at yy + dy - 1 = y
-      if (yy < 0 || yy >= im.ny) continue;
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx) {
-        const int xx = x - (dx - 1);
-        if (xx < 0 || xx >= im.nx) continue;
-        const int64_t q = (int64_t)yy * im.nx + xx;
-#pragma unroll
-        for (int co = 0; co < CO; ++co) {
-          const float g = gout[(int64_t)co * n + q];
-#pragma unroll
-          for (int ci = 0; ci < CI; ++ci) acc[ci] = fmaf(w[(co * CI + ci) * 9 + dy * 3 + dx], g, acc[ci]);
-        }
-      }
-    }
-#pragma unroll
-    for (int ci = 0; ci < CI; ++ci) gin[(int64_t)ci * n + p] = bf(act_in[(int64_t)ci * n + p]) > 0.f ? acc[ci] : 0.f;
-  }
-}
-
-// weight and bias gradients of one convolution, per tile of kTile pixels:
-// gw[co][ci][k] = sum_p gout[co](p) in[ci](p + tap), gb[co] = sum_p gout[co](p)
-template <int CI, int CO>
-__global__ void k_conv_bwd_w(const float* __restrict__ gout, const __nv_bfloat16* __restrict__ in, Img im,
-                             double* __restrict__ partials) {
-  constexpr int NWG = CO * CI * 9 + CO;
-  const int64_t n = (int64_t)im.nx * im.ny;
-  const int64_t p0 = (int64_t)blockIdx.x * kTile;
-  const int64_t p1 = p0 + kTile < n ? p0 + kTile : n;
-  for (int wi = threadIdx.x; wi < NWG; wi += blockDim.x) {
-    double acc = 0.0;
-    if (wi < CO * CI * 9) {
-      const int co = wi / (CI * 9), ci = (wi / 9) % CI, k = wi % 9;
-      const int dy = k / 3 - 1, dx = k % 3 - 1;
-      float part = 0.f;
-      int cnt = 0;
-      for (int64_t p = p0; p < p1; ++p) {
-        const int y = (int)(p / im.nx) + dy, x = (int)(p % im.nx) + dx;
-        if (y < 0 || y >= im.ny || x < 0 || x >= im.nx) continue;
-        part = fmaf(gout[(int64_t)co * n + p], bf(in[(int64_t)ci * n + (int64_t)y * im.nx + x]), part);
-        if (++cnt == 64) {
-          acc += part;
-          part = 0.f;
-          cnt = 0;
-        }
-      }
-      acc += part;
-    } else {
-      const int co = wi - CO * CI * 9;
-      for (int64_t p = p0; p < p1; ++p) acc += gout[(int64_t)co * n + p];
-    }
-    partials[(size_t)blockIdx.x * NWG + wi] = acc;
-  }
-}
-
-// grad[off + k] += sum over tiles of partials[.][k]
-__global__ void k_wgrad_sum(const double* __restrict__ partials, int ntiles, int nwg, double* __restrict__ grad) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nwg; k += gridDim.x * blockDim.x) {
-    double t = 0.0;
-    for (int b = 0; b < ntiles; ++b) t += partials[(size_t)b * nwg + k];
-    grad[k] += t;
-  }
-}
-
-// gy = coef * (r_scaled - A y) from Ay (double) ; also partials y.Ay, y.r_scaled
-__global__ void k_energy_grad(const float* __restrict__ y, const double* __restrict__ Ay, const __nv_bfloat16* __restrict__ x0,
-                              const double* __restrict__ coef, float* __restrict__ gy, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    gy[i] = (float)(coef[0] * ((double)bf(x0[i]) - Ay[i]));
-}
-
-// Adam on the fp32 master parameters; the bf16 copy is what the kernels read
-__global__ void k_adam(float* __restrict__ th, const double* __restrict__ g, float* __restrict__ m1, float* __restrict__ m2,
-                       __nv_bfloat16* __restrict__ thq, int nw, float lr, float b1, float b2, float eps, int t) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nw) return;
-  const float gk = (float)g[k];
-  m1[k] = b1 * m1[k] + (1.f - b1) * gk;
-  m2[k] = b2 * m2[k] + (1.f - b2) * gk * gk;
-  const float mh = m1[k] / (1.f - powf(b1, (float)t)), vh = m2[k] / (1.f - powf(b2, (float)t));
-  th[k] -= lr * mh / (sqrtf(vh) + eps);
-  thq[k] = __float2bfloat16(th[k]);
-}
-
-__global__ void k_cast_params(const float* __restrict__ th, __nv_bfloat16* __restrict__ thq, int nw) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nw) thq[k] = __float2bfloat16(th[k]);
-}
+// ---- preconditioners on the operator's grid (IC(0), truncated Neumann application, network) ---
+#include "ekprec.cuh"
 
 // 1 / diag(-A)
 __global__ void k_mdinv(Csr A, double* __restrict__ d) {
@@ -523,27 +342,45 @@ __global__ void k_mdinv(Csr A, double* __restrict__ d) {
 
 int grid_for(int64_t n) { return (int)std::min<int64_t>((n + kT - 1) / kT, kGrid); }
 
+constexpr int kPairCap = 4;     // training pairs (columns of the first inner solves)
+constexpr int kTrainBlocks = 2 + 2 * (kQ + 2) + 7;  // n x kPairCap blocks of the training pass
+constexpr int kL2WGrid = 152;   // CTAs of the tensor-core weight-gradient kernel
+
 }  // namespace
 
 namespace {
 
 struct EkLayout {
   size_t total = 0, basis = 0, W = 0, AV = 0, C = 0, mdinv = 0, vec = 0, partials = 0, small = 0, log = 0, hist = 0,
-         flags = 0, chk = 0, check = 0, check_bytes = 0, factor = 0, factor_bytes = 0, csr = 0, pairs = 0, cnn = 0;
+         flags = 0, chk = 0, check = 0, check_bytes = 0, factor = 0, factor_bytes = 0, csr = 0, pairs = 0, prec = 0;
   int pair_cap = 0;
 };
 
-size_t cnn_bytes(int64_t n) {
+int64_t wpart_rows_bytes(int64_t n) {
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t a = ntiles * std::max(kNW1, kNW3);
+  const int64_t b = (int64_t)kL2WGrid * kWarpsW * kNW2;
+  return (int64_t)sizeof(double) * std::max(a, b);
+}
+
+size_t prec_bytes(int64_t n) {
   size_t b = 0;
   auto add = [&](size_t x) { b += lyap_align256((int64_t)x); };
-  add(sizeof(float) * kNW * 3);                  // th, m1, m2
-  add(sizeof(__nv_bfloat16) * kNW);              // thq
-  add(sizeof(__nv_bfloat16) * n * (1 + 2 * kCh)); // x0, a1, a2
-  add(sizeof(float) * n * (1 + 2 * kCh + 1));    // y32, g1, g2, gy
-  add(sizeof(double) * kNW);                     // grad
-  add(sizeof(double) * ((n + kTile - 1) / kTile) * (kCh * kCh * 9 + kCh)); // wpart
-  add(sizeof(double) * n);                        // Ay
-  add(sizeof(double) * 8);                        // coef
+  add(sizeof(double) * n * 5);                    // stencil
+  add(sizeof(double) * n);                        // pivots
+  add(sizeof(double) * n * 6);                    // IC(0) and learned values
+  add(sizeof(float) * n * kNin);                  // features
+  add(sizeof(__nv_bfloat16) * n * kCh * 4);       // a1, a2, g1, g2
+  add(sizeof(float) * n * kNout * 2);             // y, gy
+  add(sizeof(double) * n * 3);                    // value gradients
+  add(sizeof(double) * n * kPairCap * kTrainBlocks);  // training blocks
+  add(sizeof(double) * n * 4 * 3);                // application scratch (s <= 4)
+  add(sizeof(float) * kNW * 4);                   // th, m1, m2, initial th
+  add(sizeof(__nv_bfloat16) * kNW);               // thq
+  add(sizeof(double) * kNW);                      // grad
+  add((size_t)wpart_rows_bytes(n));               // weight-gradient partials
+  add(sizeof(double) * 32);                       // loss coefficients
+  add(256);                                       // flags
   return b;
 }
 
@@ -573,9 +410,9 @@ EkLayout ek_layout(const lyap_csr* A, int s, int maxit, int grid_image) {
   L.check = take(L.check_bytes);
   L.factor_bytes = factor_ws_bytes(S, nmax, 0);
   L.factor = take(L.factor_bytes);
-  L.pair_cap = 4 * s;
+  L.pair_cap = kPairCap;
   L.pairs = take(sizeof(double) * n * L.pair_cap * 2);
-  L.cnn = grid_image ? take(cnn_bytes(n)) : 0;
+  L.prec = grid_image ? take(prec_bytes(n)) : 0;
   L.total = off;
   return L;
 }
@@ -594,43 +431,10 @@ __global__ void k_dot2(const double* __restrict__ u, const double* __restrict__ 
   cta_partials<2>(acc, partials);
 }
 
-// A y for the network's fp32 output y
-__global__ void k_spmv_f(Csr A, const float* __restrict__ y, double* __restrict__ Ay) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
-    double t = 0.0;
-    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) t = fma(A.val[e], (double)y[A.col[e]], t);
-    Ay[i] = t;
-  }
-}
-
-// y.Ay and y.b -> partials
-__global__ void k_dot_y(const float* __restrict__ y, const double* __restrict__ Ay, const double* __restrict__ b, int64_t n,
-                        double* __restrict__ partials) {
-  double acc[2] = {0.0, 0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    acc[0] = fma((double)y[i], Ay[i], acc[0]);
-    acc[1] = fma((double)y[i], b[i], acc[1]);
-  }
-  cta_partials<2>(acc, partials);
-}
-
-// per pair: coef[0] = b.b, coef[1] = b.x (reduced), coef[2] = y.Ay, coef[3] = y.b (reduced).
-// With rhat = b/||b||, xhat = x/||b||: ex = xhat^T (-A) xhat = -xhat.rhat, the loss term
-// (y - xhat)^T (-A) (y - xhat) / ex = (-y.Ay + 2 y.rhat + ex) / ex, gradient coefficient 2/(ex K)
-__global__ void k_energy_coef(double* __restrict__ coef, int K) {
-  if (threadIdx.x) return;
-  const double nb = sqrt(coef[0]);
-  const double ex = -coef[1] / coef[0];
-  const double L = (-coef[2] + 2.0 * coef[3] / nb + ex) / ex;
-  coef[4] = 2.0 / (ex * K);
-  coef[5] += L / K;
-  coef[6] = 1.0 / nb;
-}
-
-__global__ void k_energy_gy(const double* __restrict__ Ay, const double* __restrict__ b, const double* __restrict__ coef,
-                            float* __restrict__ gy, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    gy[i] = (float)(coef[4] * (b[i] * coef[6] - Ay[i]));
+// Y -= X (n * c values)
+__global__ void k_sub(double* __restrict__ Y, const double* __restrict__ X, int64_t m) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+    Y[t] -= X[t];
 }
 
 __global__ void k_init_ek(double* __restrict__ hist, int* __restrict__ flags, int* __restrict__ chk_err, int maxit) {
@@ -649,6 +453,25 @@ __global__ void k_init_ek(double* __restrict__ hist, int* __restrict__ flags, in
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// preconditioner state of a context on an nx x ny grid
+struct EkPrec {
+  Grid g{0, 0};
+  int status = -1;               // 0: IC(0) exists; otherwise why not (1 pattern, 2 diagonal, 4 pivot)
+  double *sten = nullptr, *piv = nullptr;
+  double *d0 = nullptr, *lw0 = nullptr, *ls0 = nullptr;  // IC(0)
+  double *d1 = nullptr, *lw1 = nullptr, *ls1 = nullptr;  // the network's values
+  float* feats = nullptr;
+  __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *g1 = nullptr, *g2 = nullptr;
+  float *y = nullptr, *gy = nullptr;
+  double *gd = nullptr, *gw = nullptr, *gs = nullptr;
+  double* train = nullptr;       // kTrainBlocks blocks of n x kPairCap
+  double* app = nullptr;         // 3 blocks of n x 4: the application's Horner scratch
+  float *th = nullptr, *m1 = nullptr, *m2 = nullptr, *th_init = nullptr;
+  __nv_bfloat16* thq = nullptr;
+  double *grad = nullptr, *wpart = nullptr, *coef = nullptr;
+  int* bad = nullptr;
+};
+
 struct lyap_ek {
   int s = 1, S = 2, maxit = 0;
   int64_t n = 0;
@@ -664,11 +487,8 @@ struct lyap_ek {
   double* log = nullptr;
   double *pair_b = nullptr, *pair_x = nullptr;
   int npairs = 0;
-  // CNN parameters (fp32 master, Adam moments, bf16 copy) and activations
-  float *th = nullptr, *m1 = nullptr, *m2 = nullptr, *y32 = nullptr, *g1 = nullptr, *g2 = nullptr, *gy = nullptr;
-  __nv_bfloat16 *thq = nullptr, *x0 = nullptr, *a1 = nullptr, *a2 = nullptr;
-  double *grad = nullptr, *wpart = nullptr, *Ay = nullptr, *coef = nullptr;
-  int trained = 0, adam_t = 0, last_jacobi_its = 0, fallbacks = 0;
+  EkPrec pc;
+  int trained = 0, adam_t = 0, last_jacobi_its = 0, last_ic0_its = 0, fallbacks = 0;
   lyap_handle hk;  // the check and factor kernels' view: block size S, the log below
   int m = 0, done = 0;
   std::vector<int> inner_its, inner_kind;
@@ -750,87 +570,236 @@ int cholqr2(lyap_ek* e, double* Wm, std::vector<double>& gamma, cudaStream_t st)
   return LYAP_OK;
 }
 
-// ---- the network ------------------------------------------------------------------------------
-// y = N(rsrc_c / ||rsrc_c||) into y32 (activations kept for the backward pass); rr = ||rsrc_c||^2
-void cnn_forward(lyap_ek* e, const double* rsrc, int ldr, int c, const double* rr, cudaStream_t st) {
-  const int64_t n = e->n;
-  Img im{e->nx, e->ny};
-  const int g = (int)std::min<int64_t>((n + kT - 1) / kT, 4096);
-  k_cnn_in<<<g, kT, 0, st>>>(rsrc, ldr, c, rr, e->x0, n);
-  k_conv<1, kCh, true><<<g, kT, 0, st>>>(e->x0, e->thq + oW1, e->th + oB1, e->a1, nullptr, im);
-  k_conv<kCh, kCh, true><<<g, kT, 0, st>>>(e->a1, e->thq + oW2, e->th + oB2, e->a2, nullptr, im);
-  k_conv<kCh, 1, false><<<g, kT, 0, st>>>(e->a2, e->thq + oW3, e->th + oB3, nullptr, e->y32, im);
+// ---- the preconditioner's application, Z = P_q R on C columns -------------------------------
+Vals vals_of(const EkPrec& pc, int kind) {
+  return kind == 2 ? Vals{pc.d1, pc.lw1, pc.ls1} : Vals{pc.d0, pc.lw0, pc.ls0};
 }
 
-// adds the energy-loss gradient of pair k (of K) to e->grad and its loss term to coef[5]
-void cnn_pair_grad(lyap_ek* e, const double* b, const double* x, int K, cudaStream_t st) {
-  const int64_t n = e->n;
-  Img im{e->nx, e->ny};
-  const int g = (int)std::min<int64_t>((n + kT - 1) / kT, 4096);
-  k_dot2<<<kGrid, kT, 0, st>>>(b, b, x, n, e->partials);
-  k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, 2, e->coef);
-  cnn_forward(e, b, 1, 0, e->coef, st);
-  k_add_jacobi<<<g, kT, 0, st>>>(e->y32, e->mdinv, b, e->coef, n);
-  k_spmv_f<<<g, kT, 0, st>>>(e->A, e->y32, e->Ay);
-  k_dot_y<<<kGrid, kT, 0, st>>>(e->y32, e->Ay, b, n, e->partials);
-  k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, 2, e->coef + 2);
-  k_energy_coef<<<1, 32, 0, st>>>(e->coef, K);
-  k_energy_gy<<<g, kT, 0, st>>>(e->Ay, b, e->coef, e->gy, n);
-  const int nt = (int)((n + kTile - 1) / kTile);
-  // layer 3: data gradient into a2's channels (masked by a2 > 0), weight gradient
-  k_conv_bwd_data<kCh, 1><<<g, kT, 0, st>>>(e->gy, e->thq + oW3, e->a2, e->g2, im);
-  k_conv_bwd_w<kCh, 1><<<nt, kT, 0, st>>>(e->gy, e->a2, im, e->wpart);
-  k_wgrad_sum<<<(kCh * 9 + 1 + 127) / 128, 128, 0, st>>>(e->wpart, nt, kCh * 9 + 1, e->grad + oW3);
-  // layer 2
-  k_conv_bwd_data<kCh, kCh><<<g, kT, 0, st>>>(e->g2, e->thq + oW2, e->a1, e->g1, im);
-  k_conv_bwd_w<kCh, kCh><<<nt, kT, 0, st>>>(e->g2, e->a1, im, e->wpart);
-  k_wgrad_sum<<<(kCh * kCh * 9 + kCh + 127) / 128, 128, 0, st>>>(e->wpart, nt, kCh * kCh * 9 + kCh, e->grad + oW2);
-  // layer 1 (its input needs no gradient)
-  k_conv_bwd_w<1, kCh><<<nt, kT, 0, st>>>(e->g1, e->x0, im, e->wpart);
-  k_wgrad_sum<<<(kCh * 9 + kCh + 127) / 128, 128, 0, st>>>(e->wpart, nt, kCh * 9 + kCh, e->grad + oW1);
-}
-
-// loss and gradient over the stored pairs (grad and coef[5] reset first)
-void cnn_grad_all(lyap_ek* e, cudaStream_t st) {
-  cudaMemsetAsync(e->grad, 0, sizeof(double) * kNW, st);
-  cudaMemsetAsync(e->coef + 5, 0, sizeof(double), st);
-  for (int k = 0; k < e->npairs; ++k)
-    cnn_pair_grad(e, e->pair_b + (size_t)k * e->n, e->pair_x + (size_t)k * e->n, e->npairs, st);
-}
-
-int cnn_train(lyap_ek* e, int iters, float lr, cudaStream_t st) {
-  if (e->npairs == 0) return LYAP_ERR_ARG;
-  for (int it = 0; it < iters; ++it) {
-    cnn_grad_all(e, st);
-    if (it == 0) {
-      LYAP_CUDA_TRY(cudaMemcpyAsync(&e->loss0, e->coef + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
-    }
-    ++e->adam_t;
-    k_adam<<<(kNW + 255) / 256, 256, 0, st>>>(e->th, e->grad, e->m1, e->m2, e->thq, kNW, lr, 0.9f, 0.999f, 1e-8f, e->adam_t);
+template <int C>
+void apply_P_t(const EkPrec& pc, const Vals& v, int64_t n, const double* R, int ldr, double* Z, int ldz, cudaStream_t st) {
+  const int gr = grid_for(n) * 4;
+  double* U = pc.app;
+  double* Ya = pc.app + n * 4;
+  double* Yb = pc.app + n * 8;
+  k_h_first<C><<<gr, kT, 0, st>>>(R, ldr, v.d, U, Ya, n);
+  double *cur = Ya, *nxt = Yb;
+  for (int j = 0; j < kQ; ++j) {
+    k_h_fwd<C><<<gr, kT, 0, st>>>(U, cur, v, pc.g, nxt);
+    std::swap(cur, nxt);
   }
-  cnn_grad_all(e, st);
-  LYAP_CUDA_TRY(cudaMemcpyAsync(&e->loss1, e->coef + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+  // cur = B_q R; then B_q^T by Horner steps w <- y - N^T D^{-1} w, ping-pong in the free buffers
+  const double* y = cur;
+  double* wa = cur == Ya ? Yb : Ya;
+  double* wb = U;
+  const double* w0 = y;
+  for (int j = 0; j < kQ; ++j) {
+    double* out = (j % 2 == 0) ? wa : wb;
+    k_h_bwd<C><<<gr, kT, 0, st>>>(y, w0, v, pc.g, out);
+    w0 = out;
+  }
+  k_h_last<C><<<gr, kT, 0, st>>>(w0, v.d, Z, ldz, n);
+}
+
+void apply_P(const EkPrec& pc, int kind, int C, int64_t n, const double* R, int ldr, double* Z, int ldz, cudaStream_t st) {
+  const Vals v = vals_of(pc, kind);
+  switch (C) {
+    case 1: apply_P_t<1>(pc, v, n, R, ldr, Z, ldz, st); break;
+    case 2: apply_P_t<2>(pc, v, n, R, ldr, Z, ldz, st); break;
+    case 3: apply_P_t<3>(pc, v, n, R, ldr, Z, ldz, st); break;
+    case 4: apply_P_t<4>(pc, v, n, R, ldr, Z, ldz, st); break;
+  }
+}
+
+// ---- the network: forward into the learned values, loss and gradient over K pairs ------------
+void net_forward(lyap_ek* e, cudaStream_t st) {
+  EkPrec& pc = e->pc;
+  const int64_t n = e->n;
+  const int gp = (int)std::min<int64_t>((n + kT - 1) / kT, 4096);
+  const int gm = (int)std::min<int64_t>(((n + 15) / 16 + kWarpsW - 1) / kWarpsW, 4096);
+  k_l1_fwd<<<gp, kT, 0, st>>>(pc.feats, pc.thq + oW1, pc.th + oB1, pc.g, pc.a1);
+  k_l2_fwd<<<gm, 256, 0, st>>>(pc.a1, pc.thq + oW2, pc.th + oB2, pc.g, pc.a2);
+  k_l3_fwd<<<gp, kT, 0, st>>>(pc.a2, pc.thq + oW3, pc.th + oB3, pc.g, pc.y);
+  k_net_vals<<<grid_for(n) * 4, kT, 0, st>>>(pc.y, vals_of(pc, 1), n, pc.d1, pc.lw1, pc.ls1);
+}
+
+// training blocks (n x K each, K <= kPairCap): R, X, Ur, Yr[0..q], Ug, Yg[0..q], E, ME, G, T1, T2, lamA, lamB
+struct TrainBufs {
+  double *R, *X, *Ur, *Yr[kQ + 1], *Ug, *Yg[kQ + 1], *E, *ME, *G, *T1, *T2, *la, *lb;
+};
+
+TrainBufs train_bufs(const lyap_ek* e) {
+  TrainBufs b;
+  double* p = e->pc.train;
+  const size_t blk = (size_t)e->n * kPairCap;
+  int k = 0;
+  auto next = [&]() { return p + blk * (k++); };
+  b.R = next();
+  b.X = next();
+  b.Ur = next();
+  for (int j = 0; j <= kQ; ++j) b.Yr[j] = next();
+  b.Ug = next();
+  for (int j = 0; j <= kQ; ++j) b.Yg[j] = next();
+  b.E = next();
+  b.ME = next();
+  b.G = next();
+  b.T1 = next();
+  b.T2 = next();
+  b.la = next();
+  b.lb = next();
+  return b;
+}
+
+template <int C>
+void horner_fwd_store(const EkPrec& pc, const Vals& v, int64_t n, const double* R, double* U, double* const* Y,
+                      cudaStream_t st) {
+  const int gr = grid_for(n) * 4;
+  k_h_first<C><<<gr, kT, 0, st>>>(R, C, v.d, U, Y[0], n);
+  for (int j = 0; j < kQ; ++j) k_h_fwd<C><<<gr, kT, 0, st>>>(U, Y[j], v, pc.g, Y[j + 1]);
+}
+
+// lambda_q = Lq; forward iterates Y[0..q] of the other argument; gradient into gd, gw, gs
+template <int C>
+void reverse_pass(const EkPrec& pc, const Vals& v, int64_t n, const double* Lq, double* const* Y, double* la, double* lb,
+                  cudaStream_t st) {
+  const int gr = grid_for(n) * 4;
+  const double* lam = Lq;
+  double* outs[2] = {la, lb};
+  for (int j = kQ - 1; j >= 0; --j) {
+    double* out = outs[j % 2];
+    k_h_rev<C><<<gr, kT, 0, st>>>(lam, Y[j], Y[j + 1], v, pc.g, out, pc.gd, pc.gw, pc.gs);
+    lam = out;
+  }
+  k_h_rev_last<C><<<gr, kT, 0, st>>>(lam, Y[0], v.d, n, pc.gd);
+}
+
+// the energy loss of the current network over K pairs in tb.R, tb.X (M X = R, interleaved) and its
+// gradient into pc.grad; the loss goes to pc.coef[0]; pc.coef[8 .. 8 + K) must hold x_k^T M x_k
+template <int C>
+int net_loss_grad_t(lyap_ek* e, const TrainBufs& tb, cudaStream_t st) {
+  EkPrec& pc = e->pc;
+  const int64_t n = e->n;
+  const int gr = grid_for(n) * 4;
+  LYAP_CUDA_TRY(cudaMemsetAsync(pc.grad, 0, sizeof(double) * kNW, st));
+  net_forward(e, st);
+  const Vals v = vals_of(pc, 2);
+  // U = B R (iterates kept), E = B^T U - X
+  horner_fwd_store<C>(pc, v, n, tb.R, tb.Ur, tb.Yr, st);
+  const double* y = tb.Yr[kQ];
+  const double* w0 = y;
+  for (int j = 0; j < kQ; ++j) {
+    double* out = (j % 2 == 0) ? tb.T1 : tb.T2;
+    k_h_bwd<C><<<gr, kT, 0, st>>>(y, w0, v, pc.g, out);
+    w0 = out;
+  }
+  k_h_last<C><<<gr, kT, 0, st>>>(w0, v.d, tb.E, C, n);
+  k_sub<<<gr, kT, 0, st>>>(tb.E, tb.X, n * C);
+  // ME = M E (M = -A); loss terms and G = 2 M E / (K x^T M x)
+  spmm(e->A, C, tb.E, C, tb.ME, C, -1.0, st);
+  k_coldots<C><<<kGrid, kT, 0, st>>>(tb.E, tb.ME, n, e->partials);
+  k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, C, pc.coef + 16);
+  k_energy_terms<<<1, 32, 0, st>>>(pc.coef + 16, pc.coef + 8, C, pc.coef);
+  k_scale_cols<<<gr, kT, 0, st>>>(tb.ME, pc.coef + 1, 0.0, C, n, tb.G);
+  // B G (iterates kept); gradient of sum_k [(B r_k)^T B' g_k + (B g_k)^T B' r_k]
+  horner_fwd_store<C>(pc, v, n, tb.G, tb.Ug, tb.Yg, st);
+  LYAP_CUDA_TRY(cudaMemsetAsync(pc.gd, 0, sizeof(double) * n * 3, st));
+  reverse_pass<C>(pc, v, n, tb.Yr[kQ], tb.Yg, tb.la, tb.lb, st);
+  reverse_pass<C>(pc, v, n, tb.Yg[kQ], tb.Yr, tb.la, tb.lb, st);
+  k_net_gy<<<gr, kT, 0, st>>>(pc.gd, pc.gw, pc.gs, pc.d1, vals_of(pc, 1), n, pc.gy);
+  // back through the convolutions
+  const int gp = (int)std::min<int64_t>((n + kT - 1) / kT, 4096);
+  const int gm = (int)std::min<int64_t>(((n + 15) / 16 + kWarpsW - 1) / kWarpsW, 4096);
+  const int nt = (int)((n + kTile - 1) / kTile);
+  k_l3_bwd_data<<<gp, kT, 0, st>>>(pc.gy, pc.thq + oW3, pc.a2, pc.g, pc.g2);
+  k_l3_bwd_w<<<nt, kT, 0, st>>>(pc.gy, pc.a2, pc.g, pc.wpart);
+  k_rows_sum<<<(kNW3 + 127) / 128, 128, 0, st>>>(pc.wpart, nt, kNW3, pc.grad + oW3);
+  k_l2_bwd_data<<<gm, 256, 0, st>>>(pc.g2, pc.thq + oW2, pc.a1, pc.g, pc.g1);
+  k_l2_bwd_w<<<kL2WGrid, kWarpsW * 32, 0, st>>>(pc.g2, pc.a1, pc.g, pc.wpart);
+  k_rows_sum<<<(kNW2 + 127) / 128, 128, 0, st>>>(pc.wpart, kL2WGrid * kWarpsW, kNW2, pc.grad + oW2);
+  k_l1_bwd_w<<<nt, kT, 0, st>>>(pc.g1, pc.feats, pc.g, pc.wpart);
+  k_rows_sum<<<(kNW1 + 127) / 128, 128, 0, st>>>(pc.wpart, nt, kNW1, pc.grad + oW1);
+  return LYAP_OK;
+}
+
+int net_loss_grad(lyap_ek* e, int K, const TrainBufs& tb, cudaStream_t st) {
+  switch (K) {
+    case 1: return net_loss_grad_t<1>(e, tb, st);
+    case 2: return net_loss_grad_t<2>(e, tb, st);
+    case 3: return net_loss_grad_t<3>(e, tb, st);
+    case 4: return net_loss_grad_t<4>(e, tb, st);
+  }
+  return LYAP_ERR_ARG;
+}
+
+// x_k^T M x_k of the pairs into pc.coef[8 .. 8 + K)
+int pair_norms(lyap_ek* e, int K, const TrainBufs& tb, cudaStream_t st) {
+  spmm(e->A, K, tb.X, K, tb.ME, K, -1.0, st);
+  switch (K) {
+    case 1: k_coldots<1><<<kGrid, kT, 0, st>>>(tb.X, tb.ME, e->n, e->partials); break;
+    case 2: k_coldots<2><<<kGrid, kT, 0, st>>>(tb.X, tb.ME, e->n, e->partials); break;
+    case 3: k_coldots<3><<<kGrid, kT, 0, st>>>(tb.X, tb.ME, e->n, e->partials); break;
+    case 4: k_coldots<4><<<kGrid, kT, 0, st>>>(tb.X, tb.ME, e->n, e->partials); break;
+    default: return LYAP_ERR_ARG;
+  }
+  k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, K, e->pc.coef + 8);
+  return LYAP_OK;
+}
+
+// pairs (b_k, x_k) with A x_k = b_k, column-major n x K each, into tb.R = B and tb.X = -X (M = -A)
+void load_pairs(lyap_ek* e, int K, const double* B, const double* X, const TrainBufs& tb, cudaStream_t st) {
+  const int64_t n = e->n;
+  const int g = (int)std::min<int64_t>((n + kT - 1) / kT, 8192);
+  for (int c = 0; c < K; ++c) {
+    k_copy_cols<<<g, kT, 0, st>>>(B + (size_t)c * n, 1, tb.R, K, c, 1, n, 1.0);
+    k_copy_cols<<<g, kT, 0, st>>>(X + (size_t)c * n, 1, tb.X, K, c, 1, n, -1.0);
+  }
+}
+
+void reset_params(lyap_ek* e, cudaStream_t st) {
+  EkPrec& pc = e->pc;
+  cudaMemcpyAsync(pc.th, pc.th_init, sizeof(float) * kNW, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(pc.m1, 0, sizeof(float) * 2 * kNW, st);
+  k_cast_params<<<(kNW + 255) / 256, 256, 0, st>>>(pc.th, pc.thq, kNW);
+  e->adam_t = 0;
+}
+
+// Adam steps on the stored pairs; the trained network is kept only if it lowered the loss below
+// the initial one, which is IC(0)'s (the last layer starts at zero)
+int net_train(lyap_ek* e, int iters, float lr, cudaStream_t st) {
+  EkPrec& pc = e->pc;
+  const int K = e->npairs;
+  if (K < 1) return LYAP_ERR_ARG;
+  const TrainBufs tb = train_bufs(e);
+  load_pairs(e, K, e->pair_b, e->pair_x, tb, st);
+  int rc = pair_norms(e, K, tb, st);
+  if (rc != LYAP_OK) return rc;
+  for (int it = 0; it <= iters; ++it) {
+    rc = net_loss_grad(e, K, tb, st);
+    if (rc != LYAP_OK) return rc;
+    if (it == 0) LYAP_CUDA_TRY(cudaMemcpyAsync(&e->loss0, pc.coef, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (it == iters) break;
+    ++e->adam_t;
+    k_adam<<<(kNW + 255) / 256, 256, 0, st>>>(pc.th, pc.grad, pc.m1, pc.m2, pc.thq, kNW, lr, 0.9f, 0.999f, 1e-8f,
+                                              e->adam_t);
+  }
+  LYAP_CUDA_TRY(cudaMemcpyAsync(&e->loss1, pc.coef, sizeof(double), cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
-  // a network whose training diverged is not used (the solves stay with Jacobi)
-  e->trained = std::isfinite(e->loss1) ? 1 : -1;
-  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
+  LYAP_CUDA_TRY(cudaGetLastError());
+  e->trained = (std::isfinite(e->loss1) && e->loss1 < e->loss0) ? 1 : -1;
+  return LYAP_OK;
 }
 
 // ---- preconditioned conjugate gradients for A X = B (s columns), on M = -A ------------------
+// kind 0: Jacobi; 1: IC(0) by the truncated Neumann series; 2: the network's values, same application
 template <int s>
-int pcg_t(lyap_ek* e, const double* B, int ldb, int use_cnn, int* its, cudaStream_t st) {
+int pcg_t(lyap_ek* e, const double* B, int ldb, int kind, int* its, cudaStream_t st) {
   const int64_t n = e->n;
   const double tol2 = e->inner_tol * e->inner_tol;
   k_cg_start<s><<<kGrid, kT, 0, st>>>(B, ldb, e->x, e->r, n, e->partials);
   k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, s, e->small);
   k_cg_conv<<<1, 32, 0, st>>>(e->small, e->sc, s, tol2, 1);
   auto precond = [&](int first) {
-    if (use_cnn) {
-      for (int c = 0; c < s; ++c) {
-        cnn_forward(e, e->r, s, c, e->sc + c * kSc + 3, st);
-        const int g = (int)std::min<int64_t>((n + kT - 1) / kT, 4096);
-        k_cnn_out<<<g, kT, 0, st>>>(e->y32, e->sc + c * kSc + 3, e->mdinv, e->r, e->z, s, c, n);
-      }
+    if (kind != 0) {
+      apply_P(e->pc, kind, s, n, e->r, s, e->z, s, st);
       k_cg_zdots<s><<<kGrid, kT, 0, st>>>(e->r, e->q, e->sc, e->z, n, first, e->partials);
     } else {
       k_cg_jacobi<s><<<kGrid, kT, 0, st>>>(e->mdinv, e->r, e->q, e->sc, e->z, n, first, e->partials);
@@ -866,34 +835,35 @@ int pcg_t(lyap_ek* e, const double* B, int ldb, int use_cnn, int* its, cudaStrea
   return it >= e->inner_maxit ? LYAP_NOT_CONVERGED : LYAP_OK;
 }
 
-int pcg_once(lyap_ek* e, const double* B, int ldb, int use_cnn, int* its, cudaStream_t st) {
+int pcg_once(lyap_ek* e, const double* B, int ldb, int kind, int* its, cudaStream_t st) {
   switch (e->s) {
-    case 1: return pcg_t<1>(e, B, ldb, use_cnn, its, st);
-    case 2: return pcg_t<2>(e, B, ldb, use_cnn, its, st);
-    case 4: return pcg_t<4>(e, B, ldb, use_cnn, its, st);
+    case 1: return pcg_t<1>(e, B, ldb, kind, its, st);
+    case 2: return pcg_t<2>(e, B, ldb, kind, its, st);
+    case 4: return pcg_t<4>(e, B, ldb, kind, its, st);
   }
   return LYAP_ERR_ARG;
 }
 
-// The network's solve is accepted when it reaches the inner tolerance within 3x the iterations of
-// the last Jacobi solve; otherwise (or if it went non-finite: a nonlinear preconditioner need not
-// keep z.r > 0) the solve is redone with Jacobi, which judges and backs up the network.
-// *used_cnn tells which preconditioner produced the solution.
-int pcg(lyap_ek* e, const double* B, int ldb, int use_cnn, int* its, int* used_cnn, cudaStream_t st) {
-  *used_cnn = 0;
-  if (use_cnn) {
+// The network's solve is accepted when it reaches the inner tolerance within twice the iterations
+// of the last IC(0) solve; otherwise (or when it went non-finite) the solve is redone with IC(0),
+// which judges and backs up the network.  *used tells which preconditioner produced the solution.
+int pcg(lyap_ek* e, const double* B, int ldb, int kind, int* its, int* used, cudaStream_t st) {
+  *used = kind;
+  if (kind == 2) {
     const int cap = e->inner_maxit;
-    e->inner_maxit = std::max(200, 3 * e->last_jacobi_its);
-    int rc = pcg_once(e, B, ldb, 1, its, st);
+    e->inner_maxit = std::min(cap, std::max(100, 2 * e->last_ic0_its));
+    const int rc = pcg_once(e, B, ldb, 2, its, st);
     e->inner_maxit = cap;
-    if (rc == LYAP_OK) {
-      *used_cnn = 1;
-      return rc;
-    }
+    if (rc == LYAP_OK) return rc;
     ++e->fallbacks;
+    kind = 1;
+    *used = 1;
   }
-  int rc = pcg_once(e, B, ldb, 0, its, st);
-  if (rc == LYAP_OK || rc == LYAP_NOT_CONVERGED) e->last_jacobi_its = *its;
+  const int rc = pcg_once(e, B, ldb, kind, its, st);
+  if (rc == LYAP_OK || rc == LYAP_NOT_CONVERGED) {
+    if (kind == 1) e->last_ic0_its = *its;
+    if (kind == 0) e->last_jacobi_its = *its;
+  }
   return rc;
 }
 
@@ -911,8 +881,9 @@ void take_solution(lyap_ek* e, const double* B, int ldb, double* dst, int ldd, i
 }
 
 void init_params_host(std::vector<float>& th) {
-  // the oracle's initialisation law: normal(0, 0.1) for w1, normal(0, 0.1/sqrt(C)) for w2, w3,
-  // normal(0, 0.01) for b1, b2, zero b3 (a fixed-seed generator of this library)
+  // the initialisation law of the network: w1 ~ normal(0, 0.1 / sqrt(5)), w2 ~ normal(0, 0.1 / 4),
+  // zero biases, zero last layer (the preconditioner starts as IC(0) exactly); a fixed-seed
+  // generator of this library (64-bit LCG, Box-Muller)
   th.assign(kNW, 0.f);
   unsigned long long st = 0x2545F4914F6CDD1DULL;
   auto uni = [&]() {
@@ -920,11 +891,68 @@ void init_params_host(std::vector<float>& th) {
     return ((st >> 11) + 0.5) * (1.0 / 9007199254740992.0);
   };
   auto nrm = [&]() { return sqrt(-2.0 * log(uni())) * cos(6.283185307179586 * uni()); };
-  for (int k = 0; k < kCh * 9; ++k) th[oW1 + k] = (float)(0.1 * nrm());
-  for (int k = 0; k < kCh; ++k) th[oB1 + k] = (float)(0.01 * nrm());
+  for (int k = 0; k < kCh * kNin * 9; ++k) th[oW1 + k] = (float)(0.1 / sqrt((double)kNin) * nrm());
   for (int k = 0; k < kCh * kCh * 9; ++k) th[oW2 + k] = (float)(0.1 / 4.0 * nrm());
-  for (int k = 0; k < kCh; ++k) th[oB2 + k] = (float)(0.01 * nrm());
-  // the last layer starts at zero: the preconditioner starts as Jacobi scaling exactly
+}
+
+// stencil, IC(0) and the network's initial state on the grid; pc.status tells whether IC(0) exists
+int prec_setup(lyap_ek* e, cudaStream_t st) {
+  EkPrec& pc = e->pc;
+  const int64_t n = e->n;
+  char* c = e->ws + e->L.prec;
+  auto take = [&](size_t bytes) { char* r2 = c; c += lyap_align256((int64_t)bytes); return r2; };
+  pc.g = Grid{e->nx, e->ny};
+  pc.sten = reinterpret_cast<double*>(take(sizeof(double) * n * 5));
+  pc.piv = reinterpret_cast<double*>(take(sizeof(double) * n));
+  pc.d0 = reinterpret_cast<double*>(take(sizeof(double) * n * 6));
+  pc.lw0 = pc.d0 + n;
+  pc.ls0 = pc.d0 + 2 * n;
+  pc.d1 = pc.d0 + 3 * n;
+  pc.lw1 = pc.d0 + 4 * n;
+  pc.ls1 = pc.d0 + 5 * n;
+  pc.feats = reinterpret_cast<float*>(take(sizeof(float) * n * kNin));
+  pc.a1 = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * n * kCh * 4));
+  pc.a2 = pc.a1 + n * kCh;
+  pc.g1 = pc.a1 + 2 * n * kCh;
+  pc.g2 = pc.a1 + 3 * n * kCh;
+  pc.y = reinterpret_cast<float*>(take(sizeof(float) * n * kNout * 2));
+  pc.gy = pc.y + n * kNout;
+  pc.gd = reinterpret_cast<double*>(take(sizeof(double) * n * 3));
+  pc.gw = pc.gd + n;
+  pc.gs = pc.gd + 2 * n;
+  pc.train = reinterpret_cast<double*>(take(sizeof(double) * n * kPairCap * kTrainBlocks));
+  pc.app = reinterpret_cast<double*>(take(sizeof(double) * n * 4 * 3));
+  pc.th = reinterpret_cast<float*>(take(sizeof(float) * kNW * 4));
+  pc.m1 = pc.th + kNW;
+  pc.m2 = pc.th + 2 * kNW;
+  pc.th_init = pc.th + 3 * kNW;
+  pc.thq = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * kNW));
+  pc.grad = reinterpret_cast<double*>(take(sizeof(double) * kNW));
+  pc.wpart = reinterpret_cast<double*>(take((size_t)wpart_rows_bytes(n)));
+  pc.coef = reinterpret_cast<double*>(take(sizeof(double) * 32));
+  pc.bad = reinterpret_cast<int*>(take(256));
+  LYAP_CUDA_TRY(cudaMemsetAsync(pc.bad, 0, sizeof(int), st));
+  k_stencil<<<grid_for(n) * 4, kT, 0, st>>>(e->A, pc.g, pc.sten, pc.feats, pc.bad);
+  int bad = 0;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(&bad, pc.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (bad == 0 && e->nx <= 1024) {
+    const int threads = (e->nx + 31) / 32 * 32;
+    k_ic0_wave<<<1, threads, 0, st>>>(pc.sten, pc.g, pc.piv, pc.bad);
+    k_ic0_vals<<<grid_for(n) * 4, kT, 0, st>>>(pc.sten, pc.piv, pc.g, pc.d0, pc.lw0, pc.ls0);
+    LYAP_CUDA_TRY(cudaMemcpyAsync(&bad, pc.bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  } else if (bad == 0) {
+    bad = 8;  // grids wider than one CTA: no IC(0)
+  }
+  pc.status = bad;
+  std::vector<float> th;
+  init_params_host(th);
+  LYAP_CUDA_TRY(cudaMemcpyAsync(pc.th_init, th.data(), sizeof(float) * kNW, cudaMemcpyHostToDevice, st));
+  reset_params(e, st);
+  if (pc.status == 0) net_forward(e, st);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
 }
 
 }  // namespace
@@ -936,7 +964,7 @@ int lyap_ek_workspace_size(const lyap_csr* A, int s, int maxit, int nx, int ny, 
   int rc = validate_csr(A);
   if (rc != LYAP_OK) return rc;
   if (A->val_dtype != LYAP_F64) return LYAP_ERR_ARG;
-  if ((nx || ny) && (int64_t)nx * ny != A->n) return LYAP_ERR_ARG;
+  if (nx < 0 || ny < 0 || ((nx || ny) && (int64_t)nx * ny != A->n)) return LYAP_ERR_ARG;
   *bytes = ek_layout(A, s, maxit, nx > 0).total;
   return LYAP_OK;
 }
@@ -1026,29 +1054,8 @@ int lyap_ek_create(const lyap_csr* A, const double* C, int c_mem, int s, double 
     return fail(LYAP_ERR_CUDA);
   k_mdinv<<<grid_for(n) * 4, kT, 0, st>>>(e->A, e->mdinv);
   if (nx > 0) {
-    char* c = w + e->L.cnn;
-    auto take = [&](size_t bytes) { char* r2 = c; c += lyap_align256((int64_t)bytes); return r2; };
-    e->th = reinterpret_cast<float*>(take(sizeof(float) * kNW * 3));
-    e->m1 = e->th + kNW;
-    e->m2 = e->th + 2 * kNW;
-    e->thq = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * kNW));
-    e->x0 = reinterpret_cast<__nv_bfloat16*>(take(sizeof(__nv_bfloat16) * n * (1 + 2 * kCh)));
-    e->a1 = e->x0 + n;
-    e->a2 = e->a1 + n * kCh;
-    e->y32 = reinterpret_cast<float*>(take(sizeof(float) * n * (2 + 2 * kCh)));
-    e->g1 = e->y32 + n;
-    e->g2 = e->g1 + n * kCh;
-    e->gy = e->g2 + n * kCh;
-    e->grad = reinterpret_cast<double*>(take(sizeof(double) * kNW));
-    e->wpart = reinterpret_cast<double*>(take(sizeof(double) * ((n + kTile - 1) / kTile) * (kCh * kCh * 9 + kCh)));
-    e->Ay = reinterpret_cast<double*>(take(sizeof(double) * n));
-    e->coef = reinterpret_cast<double*>(take(sizeof(double) * 8));
-    std::vector<float> th;
-    init_params_host(th);
-    if (cudaMemcpyAsync(e->th, th.data(), sizeof(float) * kNW, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return fail(LYAP_ERR_CUDA);
-    cudaMemsetAsync(e->m1, 0, sizeof(float) * 2 * kNW, st);
-    k_cast_params<<<(kNW + 255) / 256, 256, 0, st>>>(e->th, e->thq, kNW);
+    rc = prec_setup(e, st);
+    if (rc != LYAP_OK) return fail(rc);
   }
   // the check and factor view
   lyap_handle& hk = e->hk;
@@ -1082,10 +1089,14 @@ int lyap_ek_create(const lyap_csr* A, const double* C, int c_mem, int s, double 
   return LYAP_OK;
 }
 
-// precond: 0 Jacobi, 1 the network (the first train_steps inner solves use Jacobi and provide
-// its training pairs, then train_iters Adam steps, learning rate lr)
-int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, float lr, void* stream) {
-  if (!e || (precond != 0 && precond != 1) || (precond == 1 && e->nx == 0)) return LYAP_ERR_ARG;
+int lyap_ek_precond_status(lyap_ek* e) { return e ? (e->nx > 0 ? e->pc.status : -1) : -1; }
+
+// precond: 0 Jacobi, 1 IC(0), 2 the network (the first train_solves inner solves use IC(0) and
+// provide its training pairs, then train_iters Adam steps with learning rate lr)
+int lyap_ek_solve(lyap_ek* e, int precond, int train_solves, int train_iters, float lr, void* stream) {
+  if (!e || precond < 0 || precond > 2) return LYAP_ERR_ARG;
+  if (precond > 0 && (e->nx == 0 || e->pc.status != 0)) return LYAP_ERR_ARG;
+  if (precond == 2 && (train_solves < 1 || train_iters < 0 || !(lr > 0.f))) return LYAP_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = e->n;
   const int s = e->s, S = e->S;
@@ -1096,8 +1107,12 @@ int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, flo
   e->inner_its.clear();
   e->inner_kind.clear();
   e->npairs = 0;
+  e->trained = 0;
+  e->loss0 = e->loss1 = -1.0;
+  e->last_ic0_its = 0;
   hk.solved = 0;
   hk.factored = 0;
+  if (precond == 2) reset_params(e, st);
   float t_train = 0.f;
   // beta = ||C||_F
   k_dot2<<<kGrid, kT, 0, st>>>(e->C, e->C, e->C, n * s, e->partials);
@@ -1106,19 +1121,20 @@ int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, flo
   LYAP_CUDA_TRY(cudaMemcpyAsync(bb, e->small, sizeof(bb), cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
   const double beta = sqrt(bb[0]);
-  auto use_cnn = [&]() { return precond == 1 && e->trained == 1; };
-  auto collect = [&]() { return precond == 1 && e->trained == 0; };
+  auto kind_now = [&]() { return precond == 2 ? (e->trained == 1 ? 2 : 1) : precond; };
+  auto collect = [&]() { return precond == 2 && e->trained == 0 && (int)e->inner_its.size() < train_solves; };
   // [C, A^{-1} C] = V_1 gamma
   double* V1 = e->basis;
   const int gcp = (int)std::min<int64_t>((n * S + kT - 1) / kT, 8192);
   k_copy_cols<<<gcp, kT, 0, st>>>(e->C, s, V1, S, 0, s, n, 1.0);
   int its = 0, used = 0;
   e->fallbacks = 0;
-  int rc = pcg(e, e->C, s, use_cnn(), &its, &used, st);
+  const bool keep0 = collect();
+  int rc = pcg(e, e->C, s, kind_now(), &its, &used, st);
   if (rc == LYAP_ERR_NONFINITE) return rc;
   e->inner_its.push_back(its);
   e->inner_kind.push_back(used);
-  take_solution(e, e->C, s, V1, S, s, collect(), st);
+  take_solution(e, e->C, s, V1, S, s, keep0, st);
   std::vector<double> gamma;
   rc = cholqr2(e, V1, gamma, st);
   if (rc != LYAP_OK) return rc;
@@ -1133,9 +1149,9 @@ int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, flo
   }
   int result = LYAP_NOT_CONVERGED, m_final = e->maxit, done = 0;
   for (int j = 1; j <= e->maxit; ++j) {
-    if (precond == 1 && e->trained == 0 && (int)e->inner_its.size() >= train_steps) {
+    if (precond == 2 && e->trained == 0 && (int)e->inner_its.size() >= train_solves) {
       cudaEventRecord(e->ev[2], st);
-      rc = cnn_train(e, train_iters, lr, st);
+      rc = net_train(e, train_iters, lr, st);
       if (rc != LYAP_OK) return rc;
       cudaEventRecord(e->ev[3], st);
       LYAP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1145,11 +1161,12 @@ int lyap_ek_solve(lyap_ek* e, int precond, int train_steps, int train_iters, flo
     double* Vn = e->basis + (size_t)j * n * S;
     spmm(e->A, S, Vj, S, e->AV, S, 1.0, st);
     k_copy_cols<<<gcp, kT, 0, st>>>(e->AV, S, Vn, S, 0, s, n, 1.0);
-    rc = pcg(e, Vj + s, S, use_cnn(), &its, &used, st);
+    const bool keep = collect();
+    rc = pcg(e, Vj + s, S, kind_now(), &its, &used, st);
     if (rc == LYAP_ERR_NONFINITE) return rc;
     e->inner_its.push_back(its);
     e->inner_kind.push_back(used);
-    take_solution(e, Vj + s, S, Vn, S, s, collect(), st);
+    take_solution(e, Vj + s, S, Vn, S, s, keep, st);
     // block Gram-Schmidt against every stored block, twice, then CholQR2
     for (int pass = 0; pass < 2; ++pass) {
       project(e, e->basis, j, Vn, st);
@@ -1198,35 +1215,72 @@ int lyap_ek_factor(lyap_ek* e, double* Z, int64_t ldz, int tcap, int* t_out, voi
   return run_factor_basis(&e->hk, e->basis, e->n, Z, ldz, tcap, t_out, static_cast<cudaStream_t>(stream));
 }
 
-// out[0] solve ms, [1] training ms, [2] loss before training, [3] loss after, [4] inner solves,
-// [5] network solves redone with Jacobi, then the inner iteration counts (negative: solved with
-// the network) up to cap
+// out[0] solve ms, [1] training ms, [2] loss before training, [3] after, [4] inner solves ns,
+// [5] network solves redone with IC(0), [6] 1 when the trained network was accepted, then the ns
+// iteration counts and the ns preconditioner kinds (0 Jacobi, 1 IC(0), 2 network) up to cap
 int lyap_ek_stats(lyap_ek* e, double* out, int cap) {
   if (!e || !out) return LYAP_ERR_ARG;
-  const double head[6] = {e->times[0], e->times[1], e->loss0, e->loss1, (double)e->inner_its.size(), (double)e->fallbacks};
+  const int ns = (int)e->inner_its.size();
+  const double head[7] = {e->times[0], e->times[1], e->loss0, e->loss1, (double)ns, (double)e->fallbacks,
+                          e->trained == 1 ? 1.0 : 0.0};
   int k = 0;
-  for (; k < 6 && k < cap; ++k) out[k] = head[k];
-  for (size_t i = 0; i < e->inner_its.size() && k < cap; ++i, ++k)
-    out[k] = e->inner_kind[i] ? -(double)e->inner_its[i] : (double)e->inner_its[i];
+  for (; k < 7 && k < cap; ++k) out[k] = head[k];
+  for (int i = 0; i < ns && k < cap; ++i, ++k) out[k] = (double)e->inner_its[i];
+  for (int i = 0; i < ns && k < cap; ++i, ++k) out[k] = (double)e->inner_kind[i];
   return LYAP_OK;
 }
 
-// loss and gradient of the network over caller-given pairs (device, n x K column-major each,
-// A x_k = b_k) with the caller's parameters (host, the layout of the parameter vector);
-// for testing the training kernels against an independent implementation
-int lyap_ek_cnn_grad(lyap_ek* e, const float* params, int K, const double* B, const double* X, double* loss,
+// energy-norm loss and gradient of the network for caller parameters over caller pairs
+int lyap_ek_net_grad(lyap_ek* e, const float* params, int K, const double* B, const double* X, double* loss,
                      double* grad, void* stream) {
-  if (!e || !params || K < 1 || !B || !X || !loss || !grad || e->nx == 0) return LYAP_ERR_ARG;
+  if (!e || !params || K < 1 || K > kPairCap || !B || !X || !loss || !grad || e->nx == 0 || e->pc.status != 0)
+    return LYAP_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  LYAP_CUDA_TRY(cudaMemcpyAsync(e->th, params, sizeof(float) * kNW, cudaMemcpyHostToDevice, st));
-  k_cast_params<<<(kNW + 255) / 256, 256, 0, st>>>(e->th, e->thq, kNW);
-  cudaMemsetAsync(e->grad, 0, sizeof(double) * kNW, st);
-  cudaMemsetAsync(e->coef + 5, 0, sizeof(double), st);
-  for (int k = 0; k < K; ++k) cnn_pair_grad(e, B + (size_t)k * e->n, X + (size_t)k * e->n, K, st);
-  LYAP_CUDA_TRY(cudaMemcpyAsync(grad, e->grad, sizeof(double) * kNW, cudaMemcpyDeviceToHost, st));
-  LYAP_CUDA_TRY(cudaMemcpyAsync(loss, e->coef + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+  EkPrec& pc = e->pc;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(pc.th, params, sizeof(float) * kNW, cudaMemcpyHostToDevice, st));
+  k_cast_params<<<(kNW + 255) / 256, 256, 0, st>>>(pc.th, pc.thq, kNW);
+  const TrainBufs tb = train_bufs(e);
+  load_pairs(e, K, B, X, tb, st);
+  int rc = pair_norms(e, K, tb, st);
+  if (rc == LYAP_OK) rc = net_loss_grad(e, K, tb, st);
+  if (rc != LYAP_OK) return rc;
+  LYAP_CUDA_TRY(cudaMemcpyAsync(grad, pc.grad, sizeof(double) * kNW, cudaMemcpyDeviceToHost, st));
+  LYAP_CUDA_TRY(cudaMemcpyAsync(loss, pc.coef, sizeof(double), cudaMemcpyDeviceToHost, st));
   LYAP_CUDA_TRY(cudaStreamSynchronize(st));
   return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
+}
+
+// Z = P_q R for K columns (device, column-major n x K each) with the IC(0) values (kind 1) or the
+// network's (kind 2; params: host parameters to evaluate it with, or NULL for the current ones)
+int lyap_ek_precond_apply(lyap_ek* e, int kind, const float* params, int K, const double* R, double* Z, void* stream) {
+  if (!e || (kind != 1 && kind != 2) || K < 1 || K > 4 || !R || !Z || e->nx == 0 || e->pc.status != 0)
+    return LYAP_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  EkPrec& pc = e->pc;
+  if (kind == 2 && params) {
+    LYAP_CUDA_TRY(cudaMemcpyAsync(pc.th, params, sizeof(float) * kNW, cudaMemcpyHostToDevice, st));
+    k_cast_params<<<(kNW + 255) / 256, 256, 0, st>>>(pc.th, pc.thq, kNW);
+    net_forward(e, st);
+  }
+  const int64_t n = e->n;
+  const TrainBufs tb = train_bufs(e);
+  const int g = (int)std::min<int64_t>((n + kT - 1) / kT, 8192);
+  for (int c = 0; c < K; ++c) k_copy_cols<<<g, kT, 0, st>>>(R + (size_t)c * n, 1, tb.R, K, c, 1, n, 1.0);
+  apply_P(pc, kind, K, n, tb.R, K, tb.X, K, st);
+  for (int c = 0; c < K; ++c) k_copy_cols<<<g, kT, 0, st>>>(tb.X + c, K, Z + (size_t)c * n, 1, 0, 1, n, 1.0);
+  LYAP_CUDA_TRY(cudaStreamSynchronize(st));
+  return cudaGetLastError() == cudaSuccess ? LYAP_OK : LYAP_ERR_CUDA;
+}
+
+// the factor values (d, lw, ls; host arrays of n) of IC(0) (kind 1) or of the network (kind 2)
+int lyap_ek_precond_values(lyap_ek* e, int kind, double* d, double* lw, double* ls) {
+  if (!e || (kind != 1 && kind != 2) || !d || !lw || !ls || e->nx == 0 || e->pc.status != 0) return LYAP_ERR_ARG;
+  const Vals v = vals_of(e->pc, kind);
+  const size_t b = sizeof(double) * e->n;
+  LYAP_CUDA_TRY(cudaMemcpy(d, v.d, b, cudaMemcpyDeviceToHost));
+  LYAP_CUDA_TRY(cudaMemcpy(lw, v.lw, b, cudaMemcpyDeviceToHost));
+  LYAP_CUDA_TRY(cudaMemcpy(ls, v.ls, b, cudaMemcpyDeviceToHost));
+  return LYAP_OK;
 }
 
 int lyap_ek_param_count(void) { return kNW; }

@@ -241,8 +241,11 @@ class Batch:
 
 
 class ExtendedKrylov:
-    """Extended Krylov projection (lyap_ek_*): inner solves by conjugate gradients with Jacobi or
-    the learned convolutional preconditioner on the nx x ny grid ``grid`` (x fastest)."""
+    """Extended Krylov projection (lyap_ek_*): inner solves by conjugate gradients preconditioned by
+    Jacobi scaling, IC(0) applied by a truncated Neumann series, or the learned factor values, on
+    the nx x ny grid ``grid`` (x fastest) of a 5-point operator."""
+
+    PRECOND = {"jacobi": 0, "ic0": 1, "learned": 2}
 
     def __init__(self, A, C, *, tol=1e-8, maxit=60, inner_tol=1e-10, grid=None, device="cuda:0"):
         import torch
@@ -269,8 +272,12 @@ class ExtendedKrylov:
                                   self.ws.data_ptr(), self.ws_bytes, self.stream)
         self.m = 0
 
-    def solve(self, precond="jacobi", train_steps=2, train_iters=200, lr=2e-3) -> int:
-        st = L.lyap_ek_solve(self.h, 1 if precond == "cnn" else 0, train_steps, train_iters, lr, self.stream)
+    def precond_status(self) -> int:
+        """0 when IC(0) exists on the grid (the IC(0) and learned preconditioners are available)."""
+        return L.lyap_ek_precond_status(self.h)
+
+    def solve(self, precond="jacobi", train_solves=1, train_iters=150, lr=3e-3) -> int:
+        st = L.lyap_ek_solve(self.h, self.PRECOND[precond], train_solves, train_iters, lr, self.stream)
         _, self.m = L.lyap_ek_residual_norm(self.h, 0)
         return st
 
@@ -286,17 +293,33 @@ class ExtendedKrylov:
         return Z[:, :tk]
 
     def stats(self):
-        v = L.lyap_ek_stats(self.h)
-        k = int(v[4])
-        inner = v[6:6 + k]
+        v = L.lyap_ek_stats(self.h, 7 + 2 * (self.maxit + 1))
+        ns = int(v[4])
+        its = [int(x) for x in v[7:7 + ns]]
+        kinds = [int(x) for x in v[7 + ns:7 + 2 * ns]]
         return {"solve_ms": v[0], "train_ms": v[1], "loss_before": v[2], "loss_after": v[3], "fallbacks": int(v[5]),
-                "inner_jacobi": [int(x) for x in inner if x > 0], "inner_cnn": [int(-x) for x in inner if x < 0]}
+                "network_accepted": bool(v[6]), "inner_iterations": its, "inner_kinds": kinds}
 
-    def cnn_grad(self, params, B, X):
+    def _cols(self, Bm):
         t = self.torch
-        Bd = t.from_numpy(np.asfortranarray(B, dtype=np.float64).T.copy()).to(self.device)  # K x n: column k contiguous
-        Xd = t.from_numpy(np.asfortranarray(X, dtype=np.float64).T.copy()).to(self.device)
-        return L.lyap_ek_cnn_grad(self.h, params, B.shape[1], Bd.data_ptr(), Xd.data_ptr(), self.stream)
+        return t.from_numpy(np.asfortranarray(Bm, dtype=np.float64).T.copy()).to(self.device)  # K x n: column k contiguous
+
+    def net_grad(self, params, B, X):
+        """Energy loss and gradient of the network with parameters ``params`` over the pairs
+        A X = B (n x K each, K <= 4)."""
+        Bd, Xd = self._cols(B), self._cols(X)
+        return L.lyap_ek_net_grad(self.h, params, B.shape[1], Bd.data_ptr(), Xd.data_ptr(), self.stream)
+
+    def precond_apply(self, kind, R, params=None):
+        """P R on the device (kind "ic0" or "learned"; the learned values from ``params`` when given)."""
+        Rd = self._cols(R)
+        Zd = self.torch.empty_like(Rd)
+        L.lyap_ek_precond_apply(self.h, self.PRECOND[kind], params, R.shape[1], Rd.data_ptr(), Zd.data_ptr(), self.stream)
+        self.torch.cuda.synchronize(self.device)
+        return Zd.cpu().numpy().T.copy()
+
+    def precond_values(self, kind):
+        return L.lyap_ek_precond_values(self.h, self.PRECOND[kind], self.n)
 
     def close(self):
         if getattr(self, "h", None):
