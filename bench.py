@@ -66,10 +66,11 @@ def parse():
                          "returned factor has an explicit relative residual <= tol")
     ap.add_argument("--profile-precision", choices=["f64", "mixed", "f32x2"], default="f32x2",
                     help="bulk precision of the --profile-case solve")
-    ap.add_argument("--profile-case", choices=["lanczos", "check", "sylv-check"], default=None,
+    ap.add_argument("--profile-case", choices=["lanczos", "check", "sylv-check", "net"], default=None,
                     help="run a short solve of the workload for a profiler and exit: 'lanczos' runs 6 block "
                          "Lanczos steps, 'check' 64 steps with their convergence checks (tol 0), 'sylv-check' "
-                         "800 steps of the Sylvester workload with their checks (tol 0)")
+                         "800 steps of the Sylvester workload with their checks (tol 0), 'net' two loss-and-"
+                         "gradient evaluations of the inner-solve network on the --ek-grid operator")
     return ap.parse_args()
 
 
@@ -222,8 +223,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-SWEEP_PROFILE = os.path.join(ROOT, "profiles", "lanczos_sweeps_lap3d100_s4.md")
-SWEEP_SOURCES = [os.path.join(ROOT, "paper_1602_05033_gb300", "csrc", f) for f in ("lanczos.cu", "common.cuh")]
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "lanczos_sweeps_lap3d100_s4_f32x2.md")
+SWEEP_PATH = "f32x2"  # the bulk path whose sweeps that summary measured
+SWEEP_SOURCES = [os.path.join(ROOT, "paper_1602_05033_gb300", "csrc", f) for f in ("step.cu", "common.cuh", "ff.cuh")]
 
 
 def sweep_traffic():
@@ -603,7 +605,7 @@ def ours(args):
         "roofline": {"kernel": "block Lanczos step (SpMM with the projection and Gram sums; then the row "
                                "update to V_(j+1)), " + head,
                      "bound": "hbm", "achieved": hr["lanczos_GBps"], "peak": peak, "unit": "GB/s",
-                     "frac": hr["lanczos_frac"], "traffic": sweep_traffic() if head == "mixed" else None,
+                     "frac": hr["lanczos_frac"], "traffic": sweep_traffic() if head == SWEEP_PATH else None,
                      "bytes_per_unit": hr["bytes_per_step"], "peak_source": peak_src},
         "gpu_launches": hr["gpu_launches"],
         "clocks": clk,
@@ -674,6 +676,12 @@ def e2e_arm(args, P, precision, dev):
             "d2h_bytes_per_step": int(d2h), "steps": len(times)}
 
 
+def e_param_count():
+    from paper_1602_05033_gb300 import _lib as L
+
+    return L.lyap_ek_param_count()
+
+
 def profile_case(args):
     """A short, fixed piece of the workload for ncu captures (small device footprint)."""
     import torch
@@ -681,6 +689,22 @@ def profile_case(args):
     import workloads as wl
     from paper_1602_05033_gb300 import Solver
 
+    if args.profile_case == "net":
+        from paper_1602_05033_gb300 import ExtendedKrylov
+
+        k = args.ek_grid
+        A = wl.var_coeff_diffusion(np.exp(1.5 * wl.gaussian_field(k, 2, seed=1000, corr_len=32.0 * k / 1024)))
+        rng = np.random.default_rng(0)
+        X = rng.standard_normal((A.shape[0], 2))
+        e = ExtendedKrylov(A, X[:, :1], maxit=2, grid=(k, k))
+        params = np.zeros(e_param_count(), dtype=np.float32)
+        params[:] = 0.05 * rng.standard_normal(params.size)
+        for _ in range(2):
+            loss, _ = e.net_grad(params, A @ X, X)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "net", "grid": k, "loss": loss}))
+        e.close()
+        return 0
     if args.profile_case == "sylv-check":
         P = wl.config_c3(0)
         sol = Solver(P.A, P.C1, B=P.B, C2=P.C2, tol=0.0, maxit=800, precision="mixed", val_dtype="f32")

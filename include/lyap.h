@@ -354,6 +354,10 @@ int lyap_ek_precond_apply(lyap_ek* e, int kind, const float* params, int K, cons
 /* The factor values d (diagonal), lw (west), ls (south) of kind 1 or 2 into host arrays of n. */
 int lyap_ek_precond_values(lyap_ek* e, int kind, double* d, double* lw, double* ls);
 int lyap_ek_param_count(void);
+/* T_m of the extended space (block size 2s) in the band layout of lyap_projected_matrix, with
+ * gamma (gamma_1 padded with zero columns) and tau_{m+1,m}; m up to the steps run, also after a
+ * solve that stopped with an error.  For tests. */
+int lyap_ek_projected_matrix(lyap_ek* e, int m, double* ab, int ldab, double* gamma, double* tau_next);
 int lyap_ek_destroy(lyap_ek* e);
 
 /* Generalised Lyapunov equation A X E + E X A + C C^T = 0 with E symmetric positive definite (the

@@ -64,6 +64,7 @@ EXPORTED = (
     "lyap_ek_precond_values",
     "lyap_ek_precond_status",
     "lyap_ek_param_count",
+    "lyap_ek_projected_matrix",
     "lyap_ek_destroy",
     "lyap_gen_workspace_size",
     "lyap_gen_create",
@@ -165,6 +166,7 @@ def load(path: str | None = None) -> ct.CDLL:
     lib.lyap_ek_precond_values.argtypes = [P, ct.c_int, DP, DP, DP]
     lib.lyap_ek_precond_status.argtypes = [P]
     lib.lyap_ek_param_count.argtypes = []
+    lib.lyap_ek_projected_matrix.argtypes = [P, ct.c_int, P, ct.c_int, P, P]
     lib.lyap_ek_destroy.argtypes = [P]
     lib.lyap_gen_workspace_size.argtypes = [CSRP, CSRP, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)]
     lib.lyap_gen_create.argtypes = [CSRP, CSRP, P, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.c_double, P,
@@ -476,6 +478,20 @@ def lyap_ek_precond_values(h: int, kind: int, n: int):
 
 def lyap_ek_precond_status(h: int) -> int:
     return int(load().lyap_ek_precond_status(ct.c_void_p(h)))
+
+
+def lyap_ek_projected_matrix(h: int, m: int, S: int):
+    """(ab, gamma, tau_next) of the extended space's T_m: ab is (S+1) x (S*m) lower band storage."""
+    import numpy as np
+
+    N = S * m
+    ab = np.zeros((N, S + 1))
+    gam = np.zeros((S, S))
+    tau = np.zeros((S, S))
+    st = load().lyap_ek_projected_matrix(ct.c_void_p(h), int(m), ab.ctypes.data, S + 1, gam.ctypes.data, tau.ctypes.data)
+    if st != LYAP_OK:
+        raise LyapError(st, "lyap_ek_projected_matrix")
+    return ab.T.copy(), gam, tau
 
 
 def lyap_ek_destroy(h: int) -> None:

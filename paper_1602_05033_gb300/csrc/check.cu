@@ -219,7 +219,10 @@ __global__ void __launch_bounds__(256) k_setup_band(CheckArgs g) {
   }
   __syncthreads();
   for (int t = threadIdx.x; t < (s + 1) * N; t += blockDim.x) sl.Tb32[t] = (float)(sl.Tb[t] * sc);
-  for (int t = threadIdx.x; t < N; t += blockDim.x) sl.part[t] = 0.0;  // retry marks of k_invit
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    sl.part[t] = 0.0;  // retry marks of k_invit
+    sl.lam[t] = __longlong_as_double(0x7ff8000000000000LL);  // every eigenvalue must be written
+  }
 }
 
 // Number of eigenvalues of the fp32 band below x: inertia of the unpivoted LDL^T of T - x I, a
@@ -955,15 +958,46 @@ __global__ void k_invit(CheckArgs g, int round) {
   if (retry) {
     if ((i > 0 && sl.est[i] - sl.est[i - 1] <= tolc) || (i + 1 < N && sl.est[i + 1] - sl.est[i] <= tolc)) {
       atomicOr(g.chk_err + m - 1, DERR_EIGEN);
+#ifdef LYAP_DEBUG
+      printf("eig fail retry m=%d N=%d i=%d est=%.17g tolc=%.4g\n", m, N, i, sl.est[i], tolc);
+#endif
       return;
     }
   } else {
-    // groups: consecutive estimates closer than the larger of their two tolerances
-    if (i > 0 && sl.est[i] - sl.est[i - 1] <= fmax(tolc, sl.etol[i - 1])) return;  // not a leader
-    while (i + c < N && sl.est[i + c] - sl.est[i + c - 1] <= fmax(sl.etol[i + c], sl.etol[i + c - 1])) ++c;
-    if (c > kMaxCluster) {
+    // groups: consecutive estimates closer than the larger of their two tolerances.  A chain of
+    // more than kMaxCluster such estimates (the tolerance floor chains eigenvalues that are tiny
+    // against ||T|| but well apart, as the extended Krylov T_m has) is cut into groups of at most
+    // kMaxCluster, each cut at the widest gap of its window so that the subspace iterations on
+    // either side see well separated shifts; a cut narrower than four times the accuracy of the
+    // refined estimates is an error.
+    auto linked = [&](int a) { return sl.est[a] - sl.est[a - 1] <= fmax(sl.etol[a], sl.etol[a - 1]); };
+    auto gap = [&](int a) { return sl.est[a] - sl.est[a - 1]; };
+    int s0 = i;
+    while (s0 > 0 && linked(s0)) --s0;
+    int st = s0;
+    for (;;) {  // the same partition of the chain in every thread
+      int L = 1;
+      while (st + L < N && L <= kMaxCluster && linked(st + L)) ++L;
+      int len = L;
+      if (L > kMaxCluster) {
+        int best = st + 1;
+        for (int p = st + 2; p <= st + kMaxCluster; ++p)
+          if (gap(p) > gap(best)) best = p;
+        len = best - st;
+      }
+      if (i < st + len) {
+        c = len;
+        break;
+      }
+      st += len;
+    }
+    if (i != st) return;  // not a leader
+    const double cut_min = 4.0 * kRefineRes * tnorm + 8.0 * sqrt((double)N) * DBL_EPSILON * tnorm;
+    if (st > s0 && !(gap(st) > cut_min)) {
       atomicOr(g.chk_err + m - 1, DERR_EIGEN);
-      c = kMaxCluster;
+#ifdef LYAP_DEBUG
+      printf("eig fail cut m=%d N=%d i=%d est=%.17g prev=%.17g\n", m, N, i, sl.est[i], sl.est[i - 1]);
+#endif
     }
   }
   if (c == 1) {
@@ -1026,6 +1060,11 @@ __global__ void k_invit(CheckArgs g, int round) {
     rayleigh(sl.Tb, S, N, sl.X, ld, i, &rq, &res);
     }
     sl.lam[i] = rq;
+#ifdef LYAP_DEBUG
+    if (!(rq < 0.0))
+      printf("invit lam>=0 m=%d N=%d i=%d est=%.17g rq=%.17g res=%.3e refined=%d retry=%d tolc=%.4g tnorm=%.4g\n", m, N,
+             i, est, rq, res, (int)refined, (int)retry, tolc, tnorm);
+#endif
     // the windows est +- tolc/2 of different groups are disjoint, so this also excludes
     // two singletons converging to the same eigenpair
     if (!(res <= kResTol * tnorm) || !isfinite(rq) || fabs(rq - est) > 0.5 * tolc) {
@@ -1053,6 +1092,12 @@ __global__ void k_invit(CheckArgs g, int round) {
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -1230,7 +1275,6 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
           const int st = qs[q];
           if ((st & kFin) || (it == 1 && (st & kPolish))) continue;
           const int c = qc[q];
-          const bool low = round < ((st & kF64) ? 0 : kRounds32);
           double* xc = sl.Xc + (size_t)qi[q] * ld;
           bool ovf = false;
           for (int pass = 0; pass < 2; ++pass)
@@ -1247,10 +1291,28 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
               double n2 = 0.0;
               for (int k = lane; k < N; k += 32) n2 = fma(xv[k], xv[k], n2);
               n2 = warp_sum(n2);
-              const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+              if (!(n2 > 0.0) || !isfinite(n2)) {
+                // the squared norm under- or overflowed: scale by the largest entry first
+                double amax = 0.0;
+                for (int k = lane; k < N; k += 32) amax = fmax(amax, fabs(xv[k]));
+                amax = warp_max(amax);
+                if (amax > 0.0 && isfinite(amax)) {
+                  const double ia = 1.0 / amax;
+                  n2 = 0.0;
+                  for (int k = lane; k < N; k += 32) {
+                    xv[k] *= ia;
+                    n2 = fma(xv[k], xv[k], n2);
+                  }
+                  n2 = warp_sum(n2);
+                }
+              }
+              const bool good = n2 > 0.0 && isfinite(n2);
+              const double inv = good ? 1.0 / sqrt(n2) : 0.0;
               for (int k = lane; k < N; k += 32) xv[k] *= inv;
               __syncwarp();
-              if (!isfinite(n2) && low) ovf = true;
+              // a vector lost to overflow or cancellation restarts the group from fresh vectors in
+              // fp64 (in any round: a zero vector would otherwise stay zero and pass every test)
+              if (!good) ovf = true;
             }
           if (ovf) {
             __syncwarp();
@@ -1355,8 +1417,11 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
       const int i = qi[q], c = qc[q];
       for (int v = 0; v < c; ++v) {
         const double* xv = sl.Xc + (size_t)(i + v) * ld;
-        const double num = warp_sum(lane_xTy<S>(sl.Tb, N, xv, xv, lane));
-        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xv, num, lane));
+        double x2 = 0.0;
+        for (int k = lane; k < N; k += 32) x2 = fma(xv[k], xv[k], x2);
+        x2 = warp_sum(x2);
+        const double num = warp_sum(lane_xTy<S>(sl.Tb, N, xv, xv, lane)) / x2;
+        const double r2 = warp_sum(lane_res2<S>(sl.Tb, N, xv, num, lane)) / x2;
         if (lane < S) {
           sl.X[(size_t)lane * ld + i + v] = xv[lane];
           sl.X[(size_t)(N - S + lane) * ld + i + v] = xv[N - S + lane];
@@ -1365,12 +1430,14 @@ __global__ void __launch_bounds__(128, 1) k_invit_clusters(CheckArgs g) {
           sl.lam[i + v] = num;
           const bool inside =
               num >= sl.est[i] - 0.5 * sl.etol[i] && num <= sl.est[i + c - 1] + 0.5 * sl.etol[i + c - 1];
-          if (!(sqrt(r2) <= kResTol * tnorm) || !isfinite(num) || !inside) {
+          // the vectors leave the rounds normalised: anything else is a lost vector
+          const bool unit = fabs(x2 - 1.0) <= 1e-6;
+          if (!(sqrt(r2) <= kResTol * tnorm) || !isfinite(num) || !inside || !unit) {
             atomicOr(g.chk_err + m - 1, DERR_EIGEN);
 #ifdef LYAP_DEBUG
             printf("eig fail m=%d N=%d i=%d c=%d v=%d rq=%.17g res=%.3e tnorm=%.3e est[i]=%.17g est[i+c-1]=%.17g "
-                   "etol=%.4g state=%d\n",
-                   m, N, i, c, v, num, sqrt(r2), tnorm, sl.est[i], sl.est[i + c - 1], sl.etol[i], qs[q]);
+                   "etol=%.4g state=%d x2=%.6g\n",
+                   m, N, i, c, v, num, sqrt(r2), tnorm, sl.est[i], sl.est[i + c - 1], sl.etol[i], qs[q], x2);
 #endif
           }
         }
@@ -1412,7 +1479,12 @@ __global__ void k_cauchy_lyap(CheckArgs g) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     tot = fma(v, v, tot);
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(g.chk_err + m - 1, DERR_NOTNEGDEF);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) {
+    atomicOr(g.chk_err + m - 1, DERR_NOTNEGDEF);
+#ifdef LYAP_DEBUG
+    printf("not negdef m=%d N=%d i=%d lam_i=%.17g est_i=%.17g etol_i=%.4g\n", m, N, i, li, sl.est[i], sl.etol[i]);
+#endif
+  }
   if (lane == 0) sl.part[i] = tot;
 }
 

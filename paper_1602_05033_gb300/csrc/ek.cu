@@ -1285,6 +1285,11 @@ int lyap_ek_precond_values(lyap_ek* e, int kind, double* d, double* lw, double* 
 
 int lyap_ek_param_count(void) { return kNW; }
 
+int lyap_ek_projected_matrix(lyap_ek* e, int m, double* ab, int ldab, double* gamma, double* tau_next) {
+  if (!e) return LYAP_ERR_ARG;
+  return lyap_projected_matrix(&e->hk, 0, m, ab, ldab, gamma, tau_next);
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------

@@ -211,3 +211,40 @@ def test_learned_preconditioner_gains_over_ic0(pkg):
           f"({it_l / it_i:.3f} of IC(0)); loss {sl['loss_before']:.4f} -> {sl['loss_after']:.4f}")
     assert it_i < it_j
     assert it_l <= 0.95 * it_i
+
+
+def test_check_cuts_long_chains_of_resolved_eigenvalues(pkg):
+    """The extended space resolves the small eigenvalues of a high-contrast operator early: at
+    256^2 (sigma 1.5) T_m holds eigenvalues -19.4 ... -300 with gaps of 10 to 40 against ||T|| of
+    4e7, closer than the fp64 grouping floor (1e-6 ||T||) yet resolved in fp64.  They chain into
+    more members than one subspace iteration takes, and the chain is cut into consecutive groups:
+    every m's history must equal the oracle's Prop. 3.1 evaluated on the GPU's own T_m."""
+    import scipy.linalg as sla
+
+    from oracle import lyap as olyap
+    from paper_1602_05033_gb300 import _lib as L
+
+    k = 256
+    A = _vc2d(k, 1000, corr=8.0)
+    C = wl.rhs(A.shape[0], 2, 0)
+    beta = np.linalg.norm(C)
+    e = pkg.ExtendedKrylov(A, C, tol=1e-8, maxit=18, inner_tol=1e-10, grid=(k, k))
+    st = e.solve("ic0")
+    assert st in (0, 1)
+    h = e.history()
+    longest = 0
+    for m in range(1, len(h) + 1):
+        ab, gam, tau = L.lyap_ek_projected_matrix(e.h, m, 4)
+        lam, Q = sla.eig_banded(ab, lower=True)
+        assert lam.max() < 0
+        ref = olyap.cheap_residual(lam, Q, gam, tau, 4) / beta**2
+        assert abs(h[m - 1] - ref) <= 1e-10 * ref + 1e-14, (m, h[m - 1], ref)
+        close = np.diff(lam) <= 1e-6 * np.abs(lam).max()
+        run = best = 0
+        for c in close:
+            run = run + 1 if c else 0
+            best = max(best, run)
+        longest = max(longest, best + 1)
+    print("longest chain of estimates within the fp64 grouping floor:", longest)
+    assert longest > 16  # the case this test is for
+    e.close()
