@@ -489,6 +489,13 @@ struct lyap_ek {
   int npairs = 0;
   EkPrec pc;
   int trained = 0, adam_t = 0, last_jacobi_its = 0, last_ic0_its = 0, fallbacks = 0;
+  // the conjugate-gradient iterations run on an internal stream; eight of them at a time are
+  // replayed from a CUDA graph per preconditioner kind (state 0: not captured, 1: captured,
+  // -1: capture failed, direct launches)
+  cudaStream_t cgs = nullptr;
+  cudaEvent_t cg_ev[2] = {};
+  cudaGraphExec_t cg_graph[3] = {};
+  int cg_state[3] = {0, 0, 0};
   lyap_handle hk;  // the check and factor kernels' view: block size S, the log below
   int m = 0, done = 0;
   std::vector<int> inner_its, inner_kind;
@@ -791,9 +798,14 @@ int net_train(lyap_ek* e, int iters, float lr, cudaStream_t st) {
 // ---- preconditioned conjugate gradients for A X = B (s columns), on M = -A ------------------
 // kind 0: Jacobi; 1: IC(0) by the truncated Neumann series; 2: the network's values, same application
 template <int s>
-int pcg_t(lyap_ek* e, const double* B, int ldb, int kind, int* its, cudaStream_t st) {
+int pcg_t(lyap_ek* e, const double* B, int ldb, int kind, int* its, cudaStream_t caller) {
   const int64_t n = e->n;
   const double tol2 = e->inner_tol * e->inner_tol;
+  cudaStream_t st = e->cgs ? e->cgs : caller;
+  if (e->cgs) {
+    LYAP_CUDA_TRY(cudaEventRecord(e->cg_ev[0], caller));
+    LYAP_CUDA_TRY(cudaStreamWaitEvent(st, e->cg_ev[0], 0));
+  }
   k_cg_start<s><<<kGrid, kT, 0, st>>>(B, ldb, e->x, e->r, n, e->partials);
   k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, s, e->small);
   k_cg_conv<<<1, 32, 0, st>>>(e->small, e->sc, s, tol2, 1);
@@ -807,20 +819,43 @@ int pcg_t(lyap_ek* e, const double* B, int ldb, int kind, int* its, cudaStream_t
     k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, 2 * s, e->small);
     k_cg_beta<<<1, 32, 0, st>>>(e->small, e->sc, s, first);
   };
+  auto iteration = [&]() {
+    k_cg_matvec<s><<<kGrid, kT, 0, st>>>(e->A, e->p, e->q, e->partials);
+    k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, s, e->small);
+    k_cg_alpha<<<1, 32, 0, st>>>(e->small, e->sc, s);
+    k_cg_update<s><<<kGrid, kT, 0, st>>>(e->x, e->r, e->p, e->q, e->sc, n, e->partials);
+    k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, s, e->small);
+    k_cg_conv<<<1, 32, 0, st>>>(e->small, e->sc, s, tol2, 0);
+    precond(0);
+    k_cg_dir<s><<<kGrid * 4, kT, 0, st>>>(e->z, e->p, e->sc, n);
+  };
+  constexpr int kBlock = 8;  // iterations between the host's convergence reads
+  // the block of kBlock iterations as a graph: every argument is fixed per context and kind
+  if (e->cgs && e->cg_state[kind] == 0) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      for (int k = 0; k < kBlock; ++k) iteration();
+      ok = cudaStreamEndCapture(st, &g) == cudaSuccess && g != nullptr;
+    }
+    ok = ok && cudaGraphInstantiate(&e->cg_graph[kind], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      e->cg_graph[kind] = nullptr;
+      cudaGetLastError();  // a failed capture leaves no sticky error; the block runs as launches
+    }
+    e->cg_state[kind] = ok ? 1 : -1;
+  }
   precond(1);
   LYAP_CUDA_TRY(cudaMemcpyAsync(e->p, e->z, sizeof(double) * n * s, cudaMemcpyDeviceToDevice, st));
   std::vector<double> hsc(kSc * s);
   int it = 0;
   for (; it < e->inner_maxit;) {
-    for (int k = 0; k < 8 && it < e->inner_maxit; ++k, ++it) {
-      k_cg_matvec<s><<<kGrid, kT, 0, st>>>(e->A, e->p, e->q, e->partials);
-      k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, s, e->small);
-      k_cg_alpha<<<1, 32, 0, st>>>(e->small, e->sc, s);
-      k_cg_update<s><<<kGrid, kT, 0, st>>>(e->x, e->r, e->p, e->q, e->sc, n, e->partials);
-      k_sum_partials<<<1, 64, 0, st>>>(e->partials, kGrid, s, e->small);
-      k_cg_conv<<<1, 32, 0, st>>>(e->small, e->sc, s, tol2, 0);
-      precond(0);
-      k_cg_dir<s><<<kGrid * 4, kT, 0, st>>>(e->z, e->p, e->sc, n);
+    if (e->cg_state[kind] == 1 && e->inner_maxit - it >= kBlock) {
+      LYAP_CUDA_TRY(cudaGraphLaunch(e->cg_graph[kind], st));
+      it += kBlock;
+    } else {
+      for (int k = 0; k < kBlock && it < e->inner_maxit; ++k, ++it) iteration();
     }
     LYAP_CUDA_TRY(cudaMemcpyAsync(hsc.data(), e->sc, sizeof(double) * kSc * s, cudaMemcpyDeviceToHost, st));
     LYAP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -828,6 +863,10 @@ int pcg_t(lyap_ek* e, const double* B, int ldb, int kind, int* its, cudaStream_t
     bool any = false;
     for (int c = 0; c < s; ++c) any = any || hsc[c * kSc + 5] != 0.0;
     if (!any) break;
+  }
+  if (e->cgs) {
+    LYAP_CUDA_TRY(cudaEventRecord(e->cg_ev[1], st));
+    LYAP_CUDA_TRY(cudaStreamWaitEvent(caller, e->cg_ev[1], 0));
   }
   *its = it;
   for (int c = 0; c < s; ++c)
@@ -965,6 +1004,7 @@ int lyap_ek_workspace_size(const lyap_csr* A, int s, int maxit, int nx, int ny, 
   if (rc != LYAP_OK) return rc;
   if (A->val_dtype != LYAP_F64) return LYAP_ERR_ARG;
   if (nx < 0 || ny < 0 || ((nx || ny) && (int64_t)nx * ny != A->n)) return LYAP_ERR_ARG;
+  if (nx > 0 && A->n >= INT_MAX) return LYAP_ERR_ARG;  // grid kernels index nodes in 32 bits
   *bytes = ek_layout(A, s, maxit, nx > 0).total;
   return LYAP_OK;
 }
@@ -976,6 +1016,11 @@ namespace {
 void ek_release(lyap_ek* e) {
   for (int i = 0; i < 4; ++i)
     if (e->ev[i]) cudaEventDestroy(e->ev[i]);
+  for (int k = 0; k < 3; ++k)
+    if (e->cg_graph[k]) cudaGraphExecDestroy(e->cg_graph[k]);
+  for (int k = 0; k < 2; ++k)
+    if (e->cg_ev[k]) cudaEventDestroy(e->cg_ev[k]);
+  if (e->cgs) cudaStreamDestroy(e->cgs);
   if (e->hk.ev[0]) cudaEventDestroy(e->hk.ev[0]);
   if (e->hk.ev[1]) cudaEventDestroy(e->hk.ev[1]);
   if (e->hk.hist_host) cudaFreeHost(e->hk.hist_host);
@@ -1082,6 +1127,9 @@ int lyap_ek_create(const lyap_csr* A, const double* C, int c_mem, int s, double 
   if (cudaEventCreate(&hk.ev[0]) != cudaSuccess || cudaEventCreate(&hk.ev[1]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   for (int i = 0; i < 4; ++i)
     if (cudaEventCreate(&e->ev[i]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&e->cgs, cudaStreamNonBlocking) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&e->cg_ev[i], cudaEventDisableTiming) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   if (cudaMallocHost(&hk.hist_host, sizeof(double) * maxit) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   if (cudaMallocHost(&hk.flags_host, sizeof(int) * 8) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(LYAP_ERR_CUDA);
@@ -1514,6 +1562,9 @@ int lyap_gen_create(const lyap_csr* A, const lyap_csr* E, const double* C, int c
   if (cudaEventCreate(&hk.ev[0]) != cudaSuccess || cudaEventCreate(&hk.ev[1]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   for (int i = 0; i < 4; ++i)
     if (cudaEventCreate(&e->ev[i]) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&e->cgs, cudaStreamNonBlocking) != cudaSuccess) return fail(LYAP_ERR_CUDA);
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&e->cg_ev[i], cudaEventDisableTiming) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   if (cudaMallocHost(&hk.hist_host, sizeof(double) * maxit) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   if (cudaMallocHost(&hk.flags_host, sizeof(int) * 8) != cudaSuccess) return fail(LYAP_ERR_CUDA);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(LYAP_ERR_CUDA);

@@ -37,6 +37,9 @@ struct Grid {
 };
 
 __device__ __forceinline__ int64_t gnode(const Grid g, int x, int y) { return (int64_t)y * g.nx + x; }
+// grid coordinates of node p in 32-bit arithmetic (nx * ny < 2^31, checked at sizing)
+__device__ __forceinline__ int grid_x(const Grid g, int64_t p) { return (int)p % g.nx; }
+__device__ __forceinline__ int grid_y(const Grid g, int64_t p) { return (int)p / g.nx; }
 __device__ __forceinline__ bool ginside(const Grid g, int x, int y) { return x >= 0 && x < g.nx && y >= 0 && y < g.ny; }
 
 // ---- the operator's stencil --------------------------------------------------------------
@@ -46,7 +49,7 @@ __device__ __forceinline__ bool ginside(const Grid g, int x, int y) { return x >
 __global__ void k_stencil(Csr A, Grid g, double* __restrict__ sten, float* __restrict__ feats, int* __restrict__ bad) {
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    const int x = grid_x(g, i), y = grid_y(g, i);
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
       const int64_t j = A.col[e];
@@ -117,7 +120,7 @@ __global__ void k_ic0_vals(const double* __restrict__ sten, const double* __rest
                            double* __restrict__ d, double* __restrict__ lw, double* __restrict__ ls) {
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    const int x = grid_x(g, i), y = grid_y(g, i);
     d[i] = sqrt(piv[i]);
     lw[i] = x > 0 ? sten[i * 5 + 1] / sqrt(piv[i - 1]) : 0.0;
     ls[i] = y > 0 ? sten[i * 5 + 3] / sqrt(piv[i - g.nx]) : 0.0;
@@ -150,7 +153,7 @@ __global__ void k_h_fwd(const double* __restrict__ U, const double* __restrict__
                         double* __restrict__ Y1) {
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    const int x = grid_x(g, i), y = grid_y(g, i);
     const double inv = 1.0 / v.d[i];
     const double a = x > 0 ? v.lw[i] : 0.0, b = y > 0 ? v.ls[i] : 0.0;
 #pragma unroll
@@ -169,7 +172,7 @@ __global__ void k_h_bwd(const double* __restrict__ Y, const double* __restrict__
                         double* __restrict__ W1) {
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    const int x = grid_x(g, i), y = grid_y(g, i);
     const bool e = x + 1 < g.nx, nn = y + 1 < g.ny;
     const double a = e ? v.lw[i + 1] / v.d[i + 1] : 0.0;
     const double b = nn ? v.ls[i + g.nx] / v.d[i + g.nx] : 0.0;
@@ -203,7 +206,7 @@ __global__ void k_h_rev(const double* __restrict__ lam1, const double* __restric
                         double* __restrict__ gs) {
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx), y = (int)(i / g.nx);
+    const int x = grid_x(g, i), y = grid_y(g, i);
     const double inv = 1.0 / v.d[i];
     double sd = 0.0, sw = 0.0, ss = 0.0;
     const bool e = x + 1 < g.nx, nn = y + 1 < g.ny;
@@ -320,7 +323,7 @@ __global__ void k_l1_fwd(const float* __restrict__ feats, const __nv_bfloat16* _
   __syncthreads();
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(p % g.nx), y = (int)(p / g.nx);
+    const int x = grid_x(g, p), y = grid_y(g, p);
     float acc[kCh];
 #pragma unroll
     for (int co = 0; co < kCh; ++co) acc[co] = b[co];
@@ -366,7 +369,7 @@ __global__ void k_l3_fwd(const __nv_bfloat16* __restrict__ a2, const __nv_bfloat
   __syncthreads();
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(p % g.nx), y = (int)(p / g.nx);
+    const int x = grid_x(g, p), y = grid_y(g, p);
     float acc[kNout];
 #pragma unroll
     for (int co = 0; co < kNout; ++co) acc[co] = bias[co];
@@ -394,7 +397,7 @@ __global__ void k_l3_bwd_data(const float* __restrict__ gy, const __nv_bfloat16*
   __syncthreads();
   const int64_t n = (int64_t)g.nx * g.ny;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(p % g.nx), y = (int)(p / g.nx);
+    const int x = grid_x(g, p), y = grid_y(g, p);
     float acc[kCh];
 #pragma unroll
     for (int ci = 0; ci < kCh; ++ci) acc[ci] = 0.f;
@@ -435,7 +438,7 @@ __global__ void k_l3_bwd_w(const float* __restrict__ gy, const __nv_bfloat16* __
       const int co = wi / (kCh * 9), ci = (wi / 9) % kCh, k = wi % 9;
       float part = 0.f;
       for (int64_t p = p0; p < p1; ++p) {
-        const int xx = (int)(p % g.nx) + k % 3 - 1, yy = (int)(p / g.nx) + k / 3 - 1;
+        const int xx = grid_x(g, p) + k % 3 - 1, yy = grid_y(g, p) + k / 3 - 1;
         if (!ginside(g, xx, yy)) continue;
         part = fmaf(gy[p * kNout + co], bfv(a2[gnode(g, xx, yy) * kCh + ci]), part);
       }
@@ -459,7 +462,7 @@ __global__ void k_l1_bwd_w(const __nv_bfloat16* __restrict__ g1, const float* __
       const int co = wi / (kNin * 9), ci = (wi / 9) % kNin, k = wi % 9;
       float part = 0.f;
       for (int64_t p = p0; p < p1; ++p) {
-        const int xx = (int)(p % g.nx) + k % 3 - 1, yy = (int)(p / g.nx) + k / 3 - 1;
+        const int xx = grid_x(g, p) + k % 3 - 1, yy = grid_y(g, p) + k / 3 - 1;
         if (!ginside(g, xx, yy)) continue;
         part = fmaf(bfv(g1[p * kCh + co]), feats[(int64_t)ci * n + gnode(g, xx, yy)], part);
       }
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(256) k_l2_fwd(const __nv_bfloat16* __restrict_
   for (int64_t ch = wid; ch < nchunks; ch += nw) {
     const int64_t pA = ch * 16 + gq, pB = pA + 8;
     const bool okA = pA < n, okB = pB < n;
-    const int xA = (int)(pA % g.nx), yA = (int)(pA / g.nx), xB = (int)(pB % g.nx), yB = (int)(pB / g.nx);
+    const int xA = grid_x(g, pA), yA = grid_y(g, pA), xB = grid_x(g, pB), yB = grid_y(g, pB);
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(256) k_l2_bwd_data(const __nv_bfloat16* __rest
   for (int64_t ch = wid; ch < nchunks; ch += nw) {
     const int64_t pA = ch * 16 + gq, pB = pA + 8;
     const bool okA = pA < n, okB = pB < n;
-    const int xA = (int)(pA % g.nx), yA = (int)(pA / g.nx), xB = (int)(pB % g.nx), yB = (int)(pB / g.nx);
+    const int xA = grid_x(g, pA), yA = grid_y(g, pA), xB = grid_x(g, pB), yB = grid_y(g, pB);
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(256) k_l2_bwd_data(const __nv_bfloat16* __rest
 __device__ __forceinline__ uint16_t ld_ch(const uint16_t* __restrict__ a, Grid g, int64_t p, int64_t n, int dx, int dy,
                                           int c) {
   if (p >= n) return 0;
-  const int x = (int)(p % g.nx) + dx, y = (int)(p / g.nx) + dy;
+  const int x = grid_x(g, p) + dx, y = grid_y(g, p) + dy;
   return ginside(g, x, y) ? a[gnode(g, x, y) * kCh + c] : (uint16_t)0;
 }
 
