@@ -130,7 +130,12 @@ def test_ek_planning_rejects_bad_arguments(lib):
     keep = []
     A = _host_csr(wl.laplacian_2d(16), keep)
     assert _lib.lyap_ek_workspace_size(A, 2, 20, 16, 16) > _lib.lyap_ek_workspace_size(A, 2, 10, 16, 16) > 0
-    for s, maxit, nx, ny in [(3, 20, 16, 16), (2, 0, 16, 16), (2, 20, 16, 15)]:
+    # the grid adds the preconditioners' state: stencil, IC(0) and learned values, network
+    # activations and the training blocks (19 blocks of n x 4 values of the Horner passes)
+    n = 256
+    extra = _lib.lyap_ek_workspace_size(A, 2, 20, 16, 16) - _lib.lyap_ek_workspace_size(A, 2, 20, 0, 0)
+    assert extra >= 8 * n * (5 + 1 + 6 + 3 + 19 * 4 + 12) + 2 * n * 16 * 4
+    for s, maxit, nx, ny in [(3, 20, 16, 16), (2, 0, 16, 16), (2, 20, 16, 15), (2, 20, -16, -16)]:
         with pytest.raises(_lib.LyapError) as e:
             _lib.lyap_ek_workspace_size(A, s, maxit, nx, ny)
         assert e.value.status == _lib.LYAP_ERR_ARG
