@@ -1,7 +1,9 @@
-"""FP64 oracle of the convolutional preconditioner used for the inner solves of the extended
-Krylov method: three 3x3 convolutions (1 -> C -> C -> 1 channels, zero padding, ReLU after the
-first two) applied to a residual laid out on the operator's grid, and the gradients of a
-least-squares loss with respect to every weight and bias.
+"""FP64 oracle of 3x3 convolution layers (zero padding) and their backward passes, which the
+inner-solve networks of the extended Krylov method are built from (oracle/learned_factor.py,
+oracle/neumann_ic.py).  The three-layer network here (1 -> C -> C -> 1 channels, ReLU after the
+first two, applied to a residual laid out on the operator's grid) and its least-squares and
+energy-norm losses are the first design of that preconditioner, a correction to Jacobi scaling,
+kept with their pins; the GPU path now learns corrections of the IC(0) factor values instead.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain numpy loops over the nine taps;
 parameters are a dict with w1 (C,1,3,3), b1 (C), w2 (C,C,3,3), b2 (C), w3 (1,C,3,3), b3 (1).

@@ -1,7 +1,8 @@
 // Extended Krylov projection (Sec. 4) with the solves with A done by preconditioned conjugate
-// gradients on the GPU, preconditioned by Jacobi scaling or by a small convolutional network
-// (three 3x3 convolutions, 1 -> 16 -> 16 -> 1 channels, ReLU, bf16 activations with fp32
-// accumulation) trained on solve pairs that the method itself produces.
+// gradients on the GPU, preconditioned by Jacobi scaling, by IC(0) applied through a truncated
+// Neumann series, or by IC(0) values corrected by a small network trained on solve pairs that the
+// method itself produces (ekprec.cuh).  The CG iterations run on an internal stream, eight at a
+// time replayed from a CUDA graph.
 //
 // Basis blocks V_j = [V_j^(1), V_j^(2)] have S = 2s columns; [C, A^{-1} C] = V_1 gamma.  Step j:
 // W = [A V_j^(1), A^{-1} V_j^(2)], block Gram-Schmidt against every stored block (twice), CholQR2
