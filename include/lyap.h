@@ -351,7 +351,8 @@ int lyap_ek_net_grad(lyap_ek* e, const float* params, int K, const double* B, co
  * values (with params, host, when not NULL: then they replace the context's parameters). */
 int lyap_ek_precond_apply(lyap_ek* e, int kind, const float* params, int K, const double* R,
                           double* Z, void* stream);
-/* The factor values d (diagonal), lw (west), ls (south) of kind 1 or 2 into host arrays of n. */
+/* The factor values d (diagonal), lw (west), ls (south) of kind 1 or 2 into host arrays of n.
+ * A blocking copy: call it once the context's work on its stream has finished. */
 int lyap_ek_precond_values(lyap_ek* e, int kind, double* d, double* lw, double* ls);
 int lyap_ek_param_count(void);
 /* T_m of the extended space (block size 2s) in the band layout of lyap_projected_matrix, with
