@@ -163,3 +163,26 @@ def test_create_rejects_bad_arguments_before_any_device_work(lib):
         with pytest.raises(_lib.LyapError) as e:
             _lib.lyap_create(A, c["B"], C.ctypes.data, None, c["c_mem"], c["s"], c["tol"], o, 0, 0, 0)
         assert e.value.status == _lib.LYAP_ERR_ARG, c
+
+
+def test_two_pass_storage_does_not_grow_with_n_times_m(lib):
+    """The memory device of Sec. 3.3: the basis is not stored, so raising maxit adds
+    only m-sized storage (coefficient log, history, check slots of the reduced problem), the same
+    for a 4x larger operator; the n-sized part (three blocks, W, the pass-2 buffer, the operator
+    copy) does not depend on maxit."""
+    from paper_1602_05033_gb300 import _lib
+
+    keep = []
+    small = _host_csr(wl.laplacian_2d(60), keep)    # n = 3600
+    large = _host_csr(wl.laplacian_2d(120), keep)   # n = 14400
+    o = _lib.lyap_default_options()
+    growth = []
+    for A in (small, large):
+        o.maxit = 100
+        a = _lib.lyap_workspace_size(A, None, 4, o)
+        o.maxit = 300
+        b = _lib.lyap_workspace_size(A, None, 4, o)
+        growth.append(b - a)
+    # identical growth for a 4x larger operator: nothing of size n x m is stored (the reduced
+    # problem's check slots, O((s m)^2), are what grows)
+    assert growth[0] == growth[1] > 0
